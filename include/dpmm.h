@@ -1,0 +1,168 @@
+/*
+ * dpmm.h -- C ABI of the GB300 (sm_103a) sweep library for the sub-cluster
+ * split/merge Dirichlet-process mixture sampler (Dinari, Zamir, Fisher III,
+ * Freifeld, arXiv 2204.08988; sampler of Chang & Fisher III, NIPS 2013).
+ *
+ * One context holds one chain: the data X (N points of dimension d), the labels
+ * z (cluster) and zbar (sub-cluster l=0 / r=1), the sufficient statistics of the
+ * K clusters and 2K sub-clusters, and the parameters drawn from them.  A sweep
+ * (dpmm_sweep) is one iteration of Sec. 4.1: (a) weights, (b) sub-weights, (c)
+ * cluster and (d) sub-cluster parameters, (e) labels, (f) sub-labels, the
+ * sufficient statistics, then the split and merge proposals.  Every step runs on
+ * the GPU; there is no CPU fallback: without a usable sm_103a device every call
+ * that needs one returns DPMM_ECUDA.
+ *
+ * Conventions
+ *  - The caller owns every buffer it passes; the library never keeps a caller
+ *    pointer after a call returns.  Host buffers are plain CPU memory; where a
+ *    call takes `on_device`, a non-zero value means the pointer is device memory
+ *    of the context's device.
+ *  - All work is ordered on the stream given to dpmm_set_options (default: the
+ *    legacy default stream).  Calls that return data to the host synchronise that
+ *    stream; dpmm_sweep does not.
+ *  - Every call returns a status; dpmm_last_error gives the text of the last
+ *    failure of that context.  No exception crosses the ABI.
+ *  - Matrices are row-major.  Slot s = 3k + 0 is cluster k, 3k + 1 and 3k + 2
+ *    its sub-clusters l and r.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+ * (entity, sweep index, tag << 24 | block, problem); the layout is fixed, so a
+ * chain is reproducible from (data, prior, options, seed) alone.
+ */
+#ifndef DPMM_H
+#define DPMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpmm_ctx dpmm_ctx; /* opaque, library-owned */
+
+typedef enum {
+    DPMM_OK = 0,
+    DPMM_EINVAL = 1,   /* bad argument (message says which) */
+    DPMM_ENOMEM = 2,   /* device or host allocation failed */
+    DPMM_ECUDA = 3,    /* CUDA runtime/driver error, or no usable sm_103a device */
+    DPMM_ESTATE = 4,   /* call out of order (e.g. sweep before set_data) */
+    DPMM_ENUMERIC = 5, /* NaN score or non-positive-definite scale seen on the device */
+    DPMM_ETIMEOUT = 6  /* a bounded device wait gave up */
+} dpmm_status;
+
+/* Component family and conjugate prior (Sec. 2.2).
+ * DPMM_PRIOR_NIW: Gaussian components, Normal-Inverse-Wishart prior
+ *   NIW(mu, Sigma; kappa0, m0, nu0, Psi0) = N(mu; m0, Sigma/kappa0) W^-1(Sigma; nu0, Psi0),
+ *   kappa0 > 0, nu0 > d - 1, Psi0 symmetric positive definite (d x d), m0 in R^d.
+ * DPMM_PRIOR_DIRICHLET: multinomial components (count vectors), Dirichlet(beta)
+ *   prior, beta_j > 0. */
+typedef enum { DPMM_PRIOR_NIW = 0, DPMM_PRIOR_DIRICHLET = 1 } dpmm_prior_kind;
+
+typedef struct {
+    dpmm_prior_kind kind;
+    double kappa0;       /* NIW */
+    const double* m0;    /* NIW, d values */
+    double nu0;          /* NIW */
+    const double* psi0;  /* NIW, d x d */
+    const double* beta;  /* Dirichlet, d values */
+} dpmm_prior;
+
+/* Element type of the data passed to dpmm_set_data. */
+typedef enum { DPMM_F64 = 0, DPMM_F32 = 1, DPMM_BF16 = 2, DPMM_I32 = 3 } dpmm_dtype;
+
+/* Arithmetic of the label step (e)-(f) and of the statistics.
+ * FP64_PLAIN: everything in FP64 on CUDA cores (the parity path).
+ * FP32: FP32 CUDA cores, FP64 combine of statistics.
+ * TF32 / BF16: the cluster likelihoods as one tensor-core contraction
+ *   (tcgen05, FP32 accumulation), the rest as FP32. */
+typedef enum {
+    DPMM_PREC_FP64_PLAIN = 0,
+    DPMM_PREC_TF32 = 1,
+    DPMM_PREC_BF16 = 2,
+    DPMM_PREC_FP32 = 3
+} dpmm_prec;
+
+/* Create a chain.  alpha > 0 is the DP concentration (Eq. DPLatentVar); d >= 1
+ * the dimension; K_max >= 1 the capacity for clusters (a split that would exceed
+ * it is rejected and counted, Sec. 4.1 "Propose and accept splits").
+ * Errors: DPMM_EINVAL for invalid hyper-parameters (kappa0 <= 0, nu0 <= d - 1,
+ * Psi0 not SPD, beta_j <= 0, alpha <= 0, d < 1, K_max < 1), DPMM_ECUDA without a
+ * usable device.  *out is NULL on error. */
+dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max, dpmm_ctx** out);
+
+/* Options; call before dpmm_set_data.  init_K: clusters at start (Sec. 3.4
+ * examples start from 1); burn_out: sweeps a new cluster must complete before it
+ * may be split (the examples pass 15); cuda_stream: a cudaStream_t or NULL. */
+dpmm_status dpmm_set_options(dpmm_ctx* ctx, dpmm_prec prec, int init_K, int burn_out, void* cuda_stream);
+
+/* Data: N x d row-major of type dt.  The library copies and converts it into its
+ * own device buffer (FP64 for FP64_PLAIN, FP32 for FP32/TF32, BF16 for BF16;
+ * Gaussian data is centred by its mean, an exact reparameterisation undone in
+ * every output).  Resets the chain: the labels are drawn at the next sweep.
+ * Errors: DPMM_EINVAL (N < 1, NULL X, type not allowed for the prior). */
+dpmm_status dpmm_set_data(dpmm_ctx* ctx, const void* X, int64_t N, dpmm_dtype dt, int on_device);
+
+/* Replace the values of the data (same N, d, dtype) and keep the chain's state.
+ * Used for streaming data and for end-to-end timing with host-resident inputs. */
+dpmm_status dpmm_update_data(dpmm_ctx* ctx, const void* X, dpmm_dtype dt, int on_device);
+
+/* Run `iters` sweeps (Sec. 4.1) with Philox key `seed`.  The sweep counter
+ * persists across calls, so two calls of 5 equal one call of 10.  Asynchronous on
+ * the context's stream. */
+dpmm_status dpmm_sweep(dpmm_ctx* ctx, int iters, uint64_t seed);
+
+/* Labels into caller-owned host arrays of length N (z in [0, K), zbar in {0,1}).
+ * Either pointer may be NULL.  Synchronises. */
+dpmm_status dpmm_get_labels(dpmm_ctx* ctx, int32_t* z, uint8_t* zbar);
+
+/* Sufficient statistics (Sec. 4.4) in the data's original coordinates, for the
+ * 3K slots: n[3K], sx[3K x d] (sum of x), sxx[3K x d x d] (sum of x x^T, Gaussian
+ * only; may be NULL) and the cluster weights pi_k[K] of the last sweep (may be
+ * NULL).  Buffers must hold 3*K_max (resp. K_max) entries.  Synchronises. */
+dpmm_status dpmm_get_stats(dpmm_ctx* ctx, int* K, int64_t* n, double* sx, double* sxx, double* weights);
+
+/* Number of clusters and the sweep counter.  Synchronises. */
+dpmm_status dpmm_get_info(dpmm_ctx* ctx, int* K, uint32_t* iter);
+
+/* Last sweep's split/merge accounting: out[0] splits, out[1] merges, out[2] splits
+ * rejected because K would exceed K_max, out[3] clusters emptied by the label step.
+ * Synchronises. */
+dpmm_status dpmm_get_counters(dpmm_ctx* ctx, int out[4]);
+
+const char* dpmm_last_error(const dpmm_ctx* ctx);
+void dpmm_destroy(dpmm_ctx* ctx);
+
+/* ---- test hooks (used by the parity tests; not needed by an ordinary user) ---- */
+
+/* Set the labels (host arrays, length N) and K; the statistics are recomputed. */
+dpmm_status dpmm_set_state(dpmm_ctx* ctx, int K, const int32_t* z, const uint8_t* zbar);
+
+/* Steps a sweep performs: bit 0 parameters (a)-(d), bit 1 labels (e)-(f) and
+ * statistics, bit 2 splits and merges.  Default 7.  With bit 0 clear the label
+ * step uses the parameters last drawn or set by dpmm_set_params. */
+dpmm_status dpmm_set_step_mask(dpmm_ctx* ctx, unsigned mask);
+
+/* Parameters of the 3K slots (host arrays), in the data's original coordinates.
+ * Gaussian: log weight logw[3K], mean mu[3K x d], precision factor W[3K x d x d]
+ * (upper-triangular, Lambda = W W^T) and logdetW[3K] = sum_j log W_jj.
+ * Multinomial: logw[3K] and logtheta[3K x d].  Unused pointers may be NULL on get;
+ * on set they must match the prior's kind.  set overwrites K. */
+dpmm_status dpmm_set_params(dpmm_ctx* ctx, int K, const double* logw, const double* mu, const double* W,
+                            const double* logdetW, const double* logtheta);
+dpmm_status dpmm_get_params(dpmm_ctx* ctx, double* logw, double* mu, double* W, double* logdetW,
+                            double* logtheta);
+
+/* Overwrite the sweep counter (so that a test can replay one sweep index). */
+dpmm_status dpmm_set_iter(dpmm_ctx* ctx, uint32_t iter);
+
+/* Kernel timing: when enabled, every kernel launch of the sweep is bracketed by
+ * CUDA events on the context's stream.  dpmm_get_profile returns, for up to `cap`
+ * kernels, the name, the number of launches and the summed device time (ms)
+ * since the last reset, and the number of kernels known.  Synchronises. */
+dpmm_status dpmm_profile(dpmm_ctx* ctx, int enable);
+dpmm_status dpmm_get_profile(dpmm_ctx* ctx, int cap, const char** names, int* launches, double* ms, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPMM_H */

@@ -1,0 +1,629 @@
+// dpmm_api.cu -- the C ABI (include/dpmm.h): context, data upload, the sweep
+// (Sec. 4.1) as a sequence of stream-ordered kernels, getters and test hooks.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dpmm_internal.cuh"
+
+using namespace dpmm;
+
+namespace dpmm {
+cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate);
+
+void prof_begin(dpmm_ctx* c, const char* name) {
+    if (!c->profiling) return;
+    Profile* p = nullptr;
+    for (auto& q : c->prof)
+        if (q.name == name) p = &q;
+    if (!p) {
+        c->prof.push_back(Profile());
+        p = &c->prof.back();
+        p->name = name;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, c->stream);
+    p->ev.push_back(e);
+}
+
+void prof_end(dpmm_ctx* c, const char* name) {
+    if (!c->profiling) return;
+    for (auto& q : c->prof)
+        if (q.name == name) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            cudaEventRecord(e, c->stream);
+            q.ev.push_back(e);
+            q.launches += 1;
+            return;
+        }
+}
+}  // namespace dpmm
+
+// ------------------------------------------------------------------ helpers
+static dpmm_status fail(dpmm_ctx* c, dpmm_status s, const std::string& m) {
+    if (c) c->err = m;
+    return s;
+}
+
+#define CK(c, x)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (x);                                                                    \
+        if (e_ != cudaSuccess) return fail((c), DPMM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename P>
+static cudaError_t dalloc(P** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc((void**)p, bytes);
+}
+
+static void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// host Cholesky, returns false when A is not positive definite; *logdet = log det A
+static bool host_logdet_spd(const double* A, int d, double* logdet) {
+    std::vector<double> L((size_t)d * d, 0.0);
+    double s2 = 0.0;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * d + j];
+            for (int m = 0; m < j; ++m) s -= L[i * d + m] * L[j * d + m];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i * d + i] = sqrt(s);
+                s2 += log(L[i * d + i]);
+            } else {
+                L[i * d + j] = s / L[j * d + j];
+            }
+        }
+    *logdet = 2.0 * s2;
+    return true;
+}
+
+// ------------------------------------------------------------------ data kernels
+template <typename IN>
+__device__ inline double to_d(IN v) { return (double)v; }
+template <>
+__device__ inline double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <typename IN>
+__global__ void colsum_kernel(const IN* X, int64_t N, int d, int64_t R, double* part) {
+    const int g = blockIdx.x;
+    const int64_t a = (int64_t)g * R, b = min(N, a + R);
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t i = a; i < b; ++i) s += to_d(X[i * d + j]);
+        part[(size_t)g * d + j] = s;
+    }
+}
+
+__global__ void colmean_kernel(const double* part, int G, int d, int64_t N, double* center) {
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part[(size_t)g * d + j];
+        center[j] = s / (double)N;
+    }
+}
+
+template <typename OUT>
+__device__ inline OUT from_d(double v) { return (OUT)v; }
+template <>
+__device__ inline __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+
+template <typename IN, typename OUT>
+__global__ void convert_kernel(const IN* X, int64_t N, int d, int xs, const double* center, OUT* Y) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = N * xs;
+    if (q >= total) return;
+    const int64_t i = q / xs;
+    const int j = (int)(q % xs);
+    double v = 0.0;
+    if (j < d) v = to_d(X[i * d + j]) - center[j];
+    Y[q] = from_d<OUT>(v);
+}
+
+template <typename IN>
+static cudaError_t convert_any(dpmm_ctx* c, const IN* src, bool compute_center) {
+    const int d = c->d;
+    if (compute_center) {
+        const int G = 256;
+        int64_t R = (c->N + G - 1) / G;
+        double* part = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&part, sizeof(double) * G * d, c->stream);
+        if (e != cudaSuccess) return e;
+        colsum_kernel<IN><<<G, 256, 0, c->stream>>>(src, c->N, d, R, part);
+        colmean_kernel<<<1, 256, 0, c->stream>>>(part, G, d, c->N, c->center);
+        cudaFreeAsync(part, c->stream);
+    }
+    int64_t total = c->N * c->xs;
+    unsigned grid = (unsigned)((total + 255) / 256);
+    if (c->xdt == 0) convert_kernel<IN, double><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, (double*)c->X);
+    else if (c->xdt == 1) convert_kernel<IN, float><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, (float*)c->X);
+    else convert_kernel<IN, __nv_bfloat16><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, (__nv_bfloat16*)c->X);
+    return cudaGetLastError();
+}
+
+static size_t dt_size(dpmm_dtype t) { return t == DPMM_F64 ? 8 : (t == DPMM_BF16 ? 2 : 4); }
+
+// upload (host or device) input of type dt and convert it into the storage buffer
+static dpmm_status upload(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_device, bool compute_center) {
+    const size_t bytes = (size_t)c->N * c->d * dt_size(dt);
+    const void* src = X;
+    void* tmp = nullptr;
+    if (!on_device) {
+        CK(c, cudaMallocAsync(&tmp, bytes, c->stream));
+        CK(c, cudaMemcpyAsync(tmp, X, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = tmp;
+    }
+    cudaError_t e;
+    switch (dt) {
+        case DPMM_F64: e = convert_any(c, (const double*)src, compute_center); break;
+        case DPMM_F32: e = convert_any(c, (const float*)src, compute_center); break;
+        case DPMM_BF16: e = convert_any(c, (const __nv_bfloat16*)src, compute_center); break;
+        default: e = convert_any(c, (const int32_t*)src, compute_center); break;
+    }
+    if (tmp) cudaFreeAsync(tmp, c->stream);
+    CK(c, e);
+    return DPMM_OK;
+}
+
+static dpmm_status check_derr(dpmm_ctx* c) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (h != 0) {
+        int z = 0;
+        cudaMemcpy(c->derr, &z, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(c, (dpmm_status)h, h == DPMM_ENUMERIC ? "non-positive-definite scale matrix or NaN seen on the device"
+                                                         : "device error");
+    }
+    return DPMM_OK;
+}
+
+static void free_data(dpmm_ctx* c) {
+    dfree(c->X); dfree(c->z); dfree(c->zbar); dfree(c->idx); dfree(c->hist);
+    c->X = nullptr; c->z = nullptr; c->zbar = nullptr; c->idx = nullptr; c->hist = nullptr;
+}
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* dpmm_last_error(const dpmm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max, dpmm_ctx** out) {
+    if (!out) return DPMM_EINVAL;
+    *out = nullptr;
+    if (!prior || d < 1 || K_max < 1 || K_max > 1000 || !(alpha > 0.0)) return DPMM_EINVAL;
+    double ld0 = 0.0;
+    if (prior->kind == DPMM_PRIOR_NIW) {
+        if (!prior->m0 || !prior->psi0 || !(prior->kappa0 > 0.0) || !(prior->nu0 > d - 1.0) || d > 256)
+            return DPMM_EINVAL;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j)
+                if (prior->psi0[i * d + j] != prior->psi0[j * d + i]) return DPMM_EINVAL;
+        if (!host_logdet_spd(prior->psi0, d, &ld0)) return DPMM_EINVAL;
+    } else if (prior->kind == DPMM_PRIOR_DIRICHLET) {
+        if (!prior->beta) return DPMM_EINVAL;
+        for (int j = 0; j < d; ++j)
+            if (!(prior->beta[j] > 0.0)) return DPMM_EINVAL;
+    } else {
+        return DPMM_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return DPMM_ECUDA;
+    dpmm_ctx* c = new dpmm_ctx();
+    cudaGetDevice(&c->device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
+        delete c;
+        return DPMM_ECUDA;  // built for sm_103a only
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->kind = prior->kind;
+    c->d = d;
+    c->K_max = K_max;
+    c->alpha = alpha;
+    c->logdet_psi0 = ld0;
+    if (c->kind == DPMM_PRIOR_NIW) {
+        c->kappa0 = prior->kappa0;
+        c->nu0 = prior->nu0;
+        c->m0.assign(prior->m0, prior->m0 + d);
+        c->psi0.assign(prior->psi0, prior->psi0 + (size_t)d * d);
+    } else {
+        c->beta.assign(prior->beta, prior->beta + d);
+    }
+    c->st.init(d, c->kind == DPMM_PRIOR_NIW ? STAT_FULL : STAT_FIRST);
+    if (c->st.nblk > 1024) {
+        delete c;
+        return DPMM_EINVAL;
+    }
+    c->G2 = 2 * c->num_sms;
+    const size_t S = 3 * (size_t)K_max;
+    bool ok = true;
+    auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
+    A(&c->dK, sizeof(int));
+    A(&c->diter, sizeof(uint32_t));
+    A(&c->age, sizeof(int) * K_max);
+    A(&c->counters, sizeof(int) * 8);
+    A(&c->derr, sizeof(int));
+    A(&c->stats, sizeof(double) * 2 * K_max * c->st.E);
+    A(&c->shift_new, sizeof(double) * K_max * d);
+    A(&c->shift_stats, sizeof(double) * K_max * d);
+    A(&c->shift32, sizeof(float) * K_max * d);
+    A(&c->p_logw, sizeof(double) * S);
+    A(&c->p_mu, sizeof(double) * S * d);
+    A(&c->p_W, sizeof(double) * S * d * d);
+    A(&c->p_logdetW, sizeof(double) * S);
+    A(&c->p_c, sizeof(double) * S);
+    A(&c->p_logtheta, sizeof(double) * S * d);
+    A(&c->q_mu, sizeof(float) * S * d);
+    A(&c->q_W, sizeof(float) * S * d * d);
+    A(&c->q_c, sizeof(float) * S);
+    A(&c->q_b, sizeof(float) * S * d);
+    A(&c->q_logtheta, sizeof(float) * S * d);
+    A(&c->cweights, sizeof(double) * K_max);
+    A(&c->tot, sizeof(int) * (K_max + 1));
+    c->records_bytes = sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
+    A(&c->records, c->records_bytes);
+    A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
+    A(&c->relabel, sizeof(int) * 4 * K_max);
+    A(&c->center, sizeof(double) * (2 * (size_t)d + (size_t)d * d));
+    if (!ok) {
+        dpmm_destroy(c);
+        return DPMM_ENOMEM;
+    }
+    cudaMemset(c->derr, 0, sizeof(int));
+    cudaMemset(c->counters, 0, sizeof(int) * 8);
+    cudaMemset(c->p_logw, 0, sizeof(double) * S);
+    cudaMemset(c->center, 0, sizeof(double) * (2 * (size_t)d + (size_t)d * d));
+    *out = c;
+    return DPMM_OK;
+}
+
+void dpmm_destroy(dpmm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_data(c);
+    void* ps[] = {c->dK, c->diter, c->age, c->counters, c->derr, c->stats, c->shift_new, c->shift_stats,
+                  c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
+                  c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
+                  c->relabel, c->center, c->tc_img};
+    for (void* p : ps) dfree(p);
+    for (auto& p : c->prof)
+        for (auto e : p.ev) cudaEventDestroy(e);
+    delete c;
+}
+
+dpmm_status dpmm_set_options(dpmm_ctx* c, dpmm_prec prec, int init_K, int burn_out, void* stream) {
+    if (!c) return DPMM_EINVAL;
+    if (prec < DPMM_PREC_FP64_PLAIN || prec > DPMM_PREC_FP32) return fail(c, DPMM_EINVAL, "unknown precision");
+    if (init_K < 1 || init_K > c->K_max) return fail(c, DPMM_EINVAL, "init_K must be in [1, K_max]");
+    if (burn_out < 0) return fail(c, DPMM_EINVAL, "burn_out must be >= 0");
+    if (c->X && prec != c->prec) return fail(c, DPMM_ESTATE, "set the precision before dpmm_set_data");
+    int old = c->prec;
+    c->prec = prec;
+    if ((prec == DPMM_PREC_TF32 || prec == DPMM_PREC_BF16) && !tc_supported(c)) {
+        c->prec = old;
+        return fail(c, DPMM_EINVAL, "tensor-core precision not available for this prior/dimension");
+    }
+    c->init_K = init_K;
+    c->burn_out = burn_out;
+    c->stream = (cudaStream_t)stream;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, int on_device) {
+    if (!c) return DPMM_EINVAL;
+    if (!X || N < 1 || N > 0x7FFFFFFFLL) return fail(c, DPMM_EINVAL, "need 1 <= N < 2^31 and a non-NULL X");
+    if (dt < DPMM_F64 || dt > DPMM_I32) return fail(c, DPMM_EINVAL, "unknown dtype");
+    if (c->kind == DPMM_PRIOR_NIW && dt == DPMM_I32) return fail(c, DPMM_EINVAL, "Gaussian data must be floating point");
+    CK(c, cudaStreamSynchronize(c->stream));
+    free_data(c);
+    c->N = N;
+    c->in_dt = dt;
+    const int d = c->d;
+    if (c->prec == DPMM_PREC_FP64_PLAIN) {
+        c->xdt = 0;
+        c->xs = d;
+    } else if (c->prec == DPMM_PREC_BF16) {
+        c->xdt = 2;
+        c->xs = (d + 7) / 8 * 8;
+    } else {
+        c->xdt = 1;
+        c->xs = (d + 3) / 4 * 4;
+    }
+    const size_t esz = c->xdt == 0 ? 8 : (c->xdt == 1 ? 4 : 2);
+    c->T_tiles = (int)((N + 255) / 256);
+    bool ok = true;
+    auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
+    A(&c->X, (size_t)N * c->xs * esz);
+    A(&c->z, sizeof(int32_t) * N);
+    A(&c->zbar, N);
+    A(&c->idx, sizeof(int) * N);
+    A(&c->hist, sizeof(int) * (size_t)c->K_max * c->T_tiles);
+    if (!ok) {
+        free_data(c);
+        return fail(c, DPMM_ENOMEM, "device allocation for the data failed");
+    }
+    // centring (Gaussian, reduced precision): computed on the device from the input
+    std::vector<double> cen((size_t)2 * d + (size_t)d * d, 0.0);
+    CK(c, cudaMemcpyAsync(c->center, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice, c->stream));
+    const bool center = c->kind == DPMM_PRIOR_NIW && c->prec != DPMM_PREC_FP64_PLAIN;
+    dpmm_status s = upload(c, X, dt, on_device, center);
+    if (s != DPMM_OK) return s;
+    c->h_center.assign(d, 0.0);
+    CK(c, cudaMemcpyAsync(c->h_center.data(), c->center, sizeof(double) * d, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    // prior in storage coordinates: [center | m0 - center (or beta) | psi0]
+    for (int j = 0; j < d; ++j) cen[j] = c->h_center[j];
+    if (c->kind == DPMM_PRIOR_NIW) {
+        for (int j = 0; j < d; ++j) cen[d + j] = c->m0[j] - c->h_center[j];
+        for (size_t q = 0; q < (size_t)d * d; ++q) cen[2 * d + q] = c->psi0[q];
+    } else {
+        for (int j = 0; j < d; ++j) cen[d + j] = c->beta[j];
+    }
+    CK(c, cudaMemcpyAsync(c->center, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice, c->stream));
+    uint32_t zero = 0;
+    CK(c, cudaMemcpyAsync(c->diter, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->initialized = false;
+    c->h_iter = 0;
+    if (tc_supported(c) && (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16)) CK(c, tc_prepare(c));
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_update_data(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_device) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
+    if (!X || dt != c->in_dt) return fail(c, DPMM_EINVAL, "same dtype as dpmm_set_data required");
+    return upload(c, X, dt, on_device, false);
+}
+
+static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
+    const int K = c->init_K;
+    CK(c, cudaMemcpyAsync(c->dK, &K, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->age, 0, sizeof(int) * c->K_max, c->stream));
+    CK(c, cudaMemsetAsync(c->shift_new, 0, sizeof(double) * c->K_max * c->d, c->stream));
+    CK(c, cudaMemsetAsync(c->shift32, 0, sizeof(float) * c->K_max * c->d, c->stream));
+    CK(c, launch_init_labels(c, seed));
+    CK(c, launch_sort(c));
+    CK(c, launch_substats(c, seed, 0));
+    CK(c, launch_combine(c));
+    // clusters left empty by the initial draw are removed (no ages, no sweep index change)
+    CK(c, launch_splitmerge(c, seed, 2, 0));
+    CK(c, launch_relabel(c, seed));
+    c->initialized = true;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
+    if (iters < 0) return fail(c, DPMM_EINVAL, "iters must be >= 0");
+    if (!c->initialized) {
+        dpmm_status s = init_chain(c, seed);
+        if (s != DPMM_OK) return s;
+    }
+    const bool tc = (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16);
+    for (int it = 0; it < iters; ++it) {
+        if (c->step_mask & 1u) {
+            CK(c, launch_weights(c, seed));
+            CK(c, launch_params(c, seed));
+            CK(c, launch_derive(c));
+        }
+        if (c->step_mask & 2u) {
+            CK(c, tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed));
+            CK(c, launch_sort(c));
+            CK(c, launch_substats(c, seed, 1));
+            CK(c, launch_combine(c));
+        }
+        CK(c, launch_splitmerge(c, seed, (c->step_mask & 2u) ? 1 : 0, (c->step_mask & 4u) ? 1 : 0));
+        CK(c, launch_relabel(c, seed));
+        CK(c, launch_advance(c));
+    }
+    c->seed = seed;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_get_info(dpmm_ctx* c, int* K, uint32_t* iter) {
+    if (!c) return DPMM_EINVAL;
+    int k = 0;
+    uint32_t t = 0;
+    CK(c, cudaMemcpyAsync(&k, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&t, c->diter, sizeof(t), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (K) *K = k;
+    if (iter) *iter = t;
+    return check_derr(c);
+}
+
+dpmm_status dpmm_get_labels(dpmm_ctx* c, int32_t* z, uint8_t* zbar) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "no data");
+    if (z) CK(c, cudaMemcpyAsync(z, c->z, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost, c->stream));
+    if (zbar) CK(c, cudaMemcpyAsync(zbar, c->zbar, c->N, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_derr(c);
+}
+
+dpmm_status dpmm_get_counters(dpmm_ctx* c, int out[4]) {
+    if (!c || !out) return DPMM_EINVAL;
+    CK(c, cudaMemcpyAsync(out, c->counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_derr(c);
+}
+
+dpmm_status dpmm_get_stats(dpmm_ctx* c, int* Kout, int64_t* n, double* sx, double* sxx, double* weights) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "no data");
+    const int d = c->d;
+    const StatLayout& L = c->st;
+    int K = 0;
+    std::vector<double> S((size_t)2 * c->K_max * L.E), sh((size_t)c->K_max * d), w(c->K_max);
+    CK(c, cudaMemcpyAsync(&K, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(S.data(), c->stats, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(sh.data(), c->shift_stats, sizeof(double) * sh.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(w.data(), c->cweights, sizeof(double) * w.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (Kout) *Kout = K;
+    auto M = [&](int k, int h, int j, int l) { return S[(size_t)(2 * k + h) * L.E + L.ent(j, l)]; };
+    std::vector<double> a(d), s1(d), s2((size_t)d * d);
+    for (int k = 0; k < K; ++k) {
+        for (int j = 0; j < d; ++j) a[j] = sh[(size_t)k * d + j] + c->h_center[j];
+        for (int slot = 0; slot < 3; ++slot) {
+            double nn = 0.0;
+            std::fill(s1.begin(), s1.end(), 0.0);
+            std::fill(s2.begin(), s2.end(), 0.0);
+            for (int h = 0; h < 2; ++h) {
+                if (slot != 0 && h != slot - 1) continue;
+                nn += M(k, h, d, d);
+                for (int j = 0; j < d; ++j) s1[j] += M(k, h, j, d);
+                if (c->kind == DPMM_PRIOR_NIW)
+                    for (int j = 0; j < d; ++j)
+                        for (int l = j; l < d; ++l) s2[(size_t)j * d + l] += M(k, h, j, l);
+            }
+            const int s = 3 * k + slot;
+            if (n) n[s] = (int64_t)llround(nn);
+            // shifted sums back to original coordinates: x = y + a
+            if (sx)
+                for (int j = 0; j < d; ++j) sx[(size_t)s * d + j] = s1[j] + nn * a[j];
+            if (sxx && c->kind == DPMM_PRIOR_NIW)
+                for (int j = 0; j < d; ++j)
+                    for (int l = 0; l < d; ++l) {
+                        double y = j <= l ? s2[(size_t)j * d + l] : s2[(size_t)l * d + j];
+                        sxx[((size_t)s * d + j) * d + l] = y + a[j] * s1[l] + s1[j] * a[l] + nn * a[j] * a[l];
+                    }
+        }
+    }
+    if (weights)
+        for (int k = 0; k < K; ++k) weights[k] = w[k];
+    return check_derr(c);
+}
+
+dpmm_status dpmm_set_state(dpmm_ctx* c, int K, const int32_t* z, const uint8_t* zbar) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
+    if (K < 1 || K > c->K_max || !z || !zbar) return fail(c, DPMM_EINVAL, "bad state");
+    for (int64_t i = 0; i < c->N; ++i)
+        if (z[i] < 0 || z[i] >= K || zbar[i] > 1) return fail(c, DPMM_EINVAL, "label out of range");
+    CK(c, cudaMemcpyAsync(c->z, z, sizeof(int32_t) * c->N, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->zbar, zbar, c->N, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->dK, &K, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->age, 0, sizeof(int) * c->K_max, c->stream));
+    CK(c, cudaMemsetAsync(c->shift_new, 0, sizeof(double) * c->K_max * c->d, c->stream));
+    CK(c, cudaMemsetAsync(c->shift32, 0, sizeof(float) * c->K_max * c->d, c->stream));
+    CK(c, launch_sort(c));
+    CK(c, launch_substats(c, 0, 0));
+    CK(c, launch_combine(c));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->initialized = true;
+    return check_derr(c);
+}
+
+dpmm_status dpmm_set_step_mask(dpmm_ctx* c, unsigned mask) {
+    if (!c) return DPMM_EINVAL;
+    if (mask > 7) return fail(c, DPMM_EINVAL, "mask has 3 bits");
+    c->step_mask = mask;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_set_iter(dpmm_ctx* c, uint32_t iter) {
+    if (!c) return DPMM_EINVAL;
+    CK(c, cudaMemcpyAsync(c->diter, &iter, sizeof(iter), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_set_params(dpmm_ctx* c, int K, const double* logw, const double* mu, const double* W,
+                            const double* logdetW, const double* logtheta) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
+    if (K < 1 || K > c->K_max || !logw) return fail(c, DPMM_EINVAL, "bad K or logw");
+    const int d = c->d;
+    const size_t S = 3 * (size_t)K;
+    std::vector<double> cc(S);
+    if (c->kind == DPMM_PRIOR_NIW) {
+        if (!mu || !W || !logdetW) return fail(c, DPMM_EINVAL, "Gaussian parameters need mu, W, logdetW");
+        std::vector<double> ms(S * d);
+        for (size_t s = 0; s < S; ++s) {
+            for (int j = 0; j < d; ++j) ms[s * d + j] = mu[s * d + j] - c->h_center[j];
+            cc[s] = logw[s] + logdetW[s] - 0.5 * d * log(2.0 * M_PI);
+        }
+        CK(c, cudaMemcpyAsync(c->p_mu, ms.data(), sizeof(double) * S * d, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->p_W, W, sizeof(double) * S * d * d, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->p_logdetW, logdetW, sizeof(double) * S, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        if (!logtheta) return fail(c, DPMM_EINVAL, "multinomial parameters need logtheta");
+        for (size_t s = 0; s < S; ++s) cc[s] = logw[s];
+        CK(c, cudaMemcpyAsync(c->p_logtheta, logtheta, sizeof(double) * S * d, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(c, cudaMemcpyAsync(c->p_logw, logw, sizeof(double) * S, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->p_c, cc.data(), sizeof(double) * S, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->dK, &K, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_derive(c));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_get_params(dpmm_ctx* c, double* logw, double* mu, double* W, double* logdetW, double* logtheta) {
+    if (!c) return DPMM_EINVAL;
+    int K = 0;
+    CK(c, cudaMemcpyAsync(&K, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const int d = c->d;
+    const size_t S = 3 * (size_t)K;
+    if (logw) CK(c, cudaMemcpyAsync(logw, c->p_logw, sizeof(double) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (mu) CK(c, cudaMemcpyAsync(mu, c->p_mu, sizeof(double) * S * d, cudaMemcpyDeviceToHost, c->stream));
+    if (W) CK(c, cudaMemcpyAsync(W, c->p_W, sizeof(double) * S * d * d, cudaMemcpyDeviceToHost, c->stream));
+    if (logdetW) CK(c, cudaMemcpyAsync(logdetW, c->p_logdetW, sizeof(double) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (logtheta) CK(c, cudaMemcpyAsync(logtheta, c->p_logtheta, sizeof(double) * S * d, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (mu && !c->h_center.empty())
+        for (size_t s = 0; s < S; ++s)
+            for (int j = 0; j < d; ++j) mu[s * d + j] += c->h_center[j];
+    return check_derr(c);
+}
+
+dpmm_status dpmm_profile(dpmm_ctx* c, int enable) {
+    if (!c) return DPMM_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->prof)
+        for (auto e : p.ev) cudaEventDestroy(e);
+    c->prof.clear();
+    c->profiling = enable != 0;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_get_profile(dpmm_ctx* c, int cap, const char** names, int* launches, double* ms, int* count) {
+    if (!c) return DPMM_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    int i = 0;
+    for (auto& p : c->prof) {
+        for (size_t q = 0; q + 1 < p.ev.size(); q += 2) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, p.ev[q], p.ev[q + 1]);
+            p.ms += t;
+            cudaEventDestroy(p.ev[q]);
+            cudaEventDestroy(p.ev[q + 1]);
+        }
+        p.ev.clear();
+        if (i < cap) {
+            if (names) names[i] = p.name.c_str();
+            if (launches) launches[i] = p.launches;
+            if (ms) ms[i] = p.ms;
+        }
+        ++i;
+    }
+    if (count) *count = i;
+    return DPMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+// k_params.cu -- steps (a)-(d) of the sweep (Sec. 4.1, Eqs. sample_weights,
+// sample_sub_weights, sample_params, sample_sub_params) on the GPU in FP64:
+// one CTA draws the weights; one CTA per (sub-)cluster slot draws its parameters
+// from the conjugate posterior of its sufficient statistics.
+#include <math.h>
+
+#include "dpmm_internal.cuh"
+
+namespace dpmm {
+
+struct StatView {
+    const double* S;  // stats table
+    StatLayout L;
+    // M[j][l] of slot (k, h); h = -1 sums both sub-clusters (the cluster)
+    __device__ double m(int k, int h, int j, int l) const {
+        int e = L.ent(j, l);
+        if (h >= 0) return S[(size_t)(2 * k + h) * L.E + e];
+        return S[(size_t)(2 * k) * L.E + e] + S[(size_t)(2 * k + 1) * L.E + e];
+    }
+    __device__ double count(int k, int h) const { return m(k, h, L.d, L.d); }
+};
+
+__device__ inline double block_reduce_max(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    v = -INFINITY;
+    for (int i = 0; i < nw; ++i) v = fmax(v, sh[i]);
+    __syncthreads();
+    return v;
+}
+
+__device__ inline double block_reduce_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    for (int i = 0; i < nw; ++i) v += sh[i];  // fixed order: deterministic
+    __syncthreads();
+    return v;
+}
+
+// (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2).
+__global__ void weights_kernel(StatView sv, const int* dK, const uint32_t* diter, uint64_t seed, double alpha,
+                               double* logw, double* cweights) {
+    __shared__ double sh[32];
+    const int K = *dK;
+    Key key{seed, *diter, 0};
+    double lmax = -INFINITY;
+    // each thread keeps at most a few draws; K + 1 <= 4 * blockDim
+    double lg[4];
+    int cnt = 0;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) {
+        double v = (k < K) ? d_log_gamma(key, (uint32_t)k, TAG_WEIGHT, 0, sv.count(k, -1))
+                           : d_log_gamma(key, 0xFFFFFFFFu, TAG_WEIGHT, 0, alpha);
+        lg[cnt] = v;
+        lmax = fmax(lmax, v);
+    }
+    lmax = block_reduce_max(lmax, sh);
+    double s = 0.0;
+    cnt = 0;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) s += exp(lg[cnt] - lmax);
+    double lse = lmax + log(block_reduce_sum(s, sh));
+    cnt = 0;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) {
+        if (k < K) {
+            logw[3 * k] = lg[cnt] - lse;
+            cweights[k] = exp(lg[cnt] - lse);
+        }
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double gl = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 0, sv.count(k, 0) + 0.5 * alpha);
+        double gr = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 64, sv.count(k, 1) + 0.5 * alpha);
+        double m = fmax(gl, gr);
+        double l2 = m + log(exp(gl - m) + exp(gr - m));
+        logw[3 * k + 1] = gl - l2;
+        logw[3 * k + 2] = gr - l2;
+    }
+}
+
+struct NiwPrior {
+    double kappa0, nu0;
+    const double* m0s;   // prior mean in storage coordinates (m0 - center), device
+    const double* psi0;  // device, d x d
+};
+
+// (c), (d): (mu, Lambda) ~ NIW posterior of one slot.  Lambda = W W^T with
+// W = U^-T B (Psi_n = U U^T, B upper-triangular Bartlett factor of Wishart(nu_n, I):
+// B_jj^2 ~ chi^2(nu_n - d + j), j = 1..d, N(0,1) above the diagonal);
+// mu = m_n + W^-T eps / sqrt(kappa_n).  Dynamic shared memory: d*d + 4*d doubles.
+__global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPrior pr, const int* dK,
+                                  const uint32_t* diter, uint64_t seed, const double* logw, double* p_mu,
+                                  double* p_W, double* p_logdetW, double* p_c, int* derr) {
+    extern __shared__ double smem[];
+    const int d = sv.L.d;
+    const int K = *dK;
+    const int s = blockIdx.x;
+    if (s >= 3 * K) return;
+    const int k = s / 3, h = s % 3 - 1;  // h = -1: the cluster
+    double* A = smem;             // d x d: Psi_n, then its Cholesky factor U (lower)
+    double* mn = A + d * d;       // d
+    double* xb = mn + d;          // d
+    double* Bd = xb + d;          // d: Bartlett diagonal
+    double* acc = Bd + d;         // d
+    __shared__ double sh[32];
+    __shared__ double s_n, s_kn, s_nun;
+    Key key{seed, *diter, 0};
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    if (tid == 0) {
+        double n = sv.count(k, h);
+        s_n = n;
+        s_kn = pr.kappa0 + n;
+        s_nun = pr.nu0 + n;
+    }
+    __syncthreads();
+    const double n = s_n, kn = s_kn, nun = s_nun;
+    const double* sh_k = shift_stats + (size_t)k * d;
+    for (int j = tid; j < d; j += nt) {
+        double xbar = n > 0 ? sh_k[j] + sv.m(k, h, j, d) / n : 0.0;
+        xb[j] = xbar;
+        mn[j] = (pr.kappa0 * pr.m0s[j] + n * xbar) / kn;
+    }
+    __syncthreads();
+    // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n
+    const double f = n > 0 ? pr.kappa0 * n / kn : 0.0;
+    for (int e = tid; e < d * d; e += nt) {
+        int j = e / d, l = e % d;
+        int a = min(j, l), b = max(j, l);
+        double C = 0.0;
+        if (n > 0) {
+            double s1a = sv.m(k, h, a, d), s1b = sv.m(k, h, b, d);
+            C = sv.m(k, h, a, b) - s1a * s1b / n;
+        }
+        A[e] = pr.psi0[e] + C + f * (xb[j] - pr.m0s[j]) * (xb[l] - pr.m0s[l]);
+    }
+    __syncthreads();
+    // right-looking Cholesky, A = U U^T (lower)
+    for (int j = 0; j < d; ++j) {
+        if (tid == 0) {
+            double v = A[j * d + j];
+            if (!(v > 0.0)) {
+                atomicExch(derr, (int)DPMM_ENUMERIC);
+                v = 1e-300;
+            }
+            A[j * d + j] = sqrt(v);
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] /= A[j * d + j];
+        __syncthreads();
+        int m = d - j - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            int i = j + 1 + e / m, l = j + 1 + e % m;
+            if (l <= i) A[i * d + l] -= A[i * d + j] * A[l * d + j];
+        }
+        __syncthreads();
+    }
+    // Bartlett diagonal (chi^2 via Gamma)
+    for (int j = tid; j < d; j += nt) {
+        double df = nun - d + (j + 1);
+        double lg = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, 0.5 * df);
+        Bd[j] = sqrt(2.0 * exp(lg));
+        acc[j] = 0.0;
+    }
+    __syncthreads();
+    const uint32_t NB = 64u * d;
+    double* W = p_W + (size_t)s * d * d;
+    // W = U^-T B, column c by back substitution (U^T upper-triangular)
+    for (int c = tid; c < d; c += nt) {
+        for (int r = d - 1; r > c; --r) W[r * d + c] = 0.0;
+        for (int r = c; r >= 0; --r) {
+            double b = (r == c) ? Bd[c] : d_normal(key, (uint32_t)s, TAG_PARAM, NB, (uint32_t)(r * d + c));
+            double t = b;
+            for (int m = r + 1; m <= c; ++m) t -= A[m * d + r] * W[m * d + c];
+            W[r * d + c] = t / A[r * d + r];
+        }
+    }
+    __syncthreads();
+    // W^T v = eps (forward substitution), mu = m_n + v / sqrt(kappa_n)
+    double* mu = p_mu + (size_t)s * d;
+    for (int j = 0; j < d; ++j) {
+        if (tid == 0) {
+            double e = d_normal(key, (uint32_t)s, TAG_PARAM, NB, (uint32_t)(d * d + j));
+            double v = (e - acc[j]) / W[j * d + j];
+            Bd[j] = v;  // reuse as v
+        }
+        __syncthreads();
+        double v = Bd[j];
+        for (int m = j + 1 + tid; m < d; m += nt) acc[m] += W[j * d + m] * v;
+        __syncthreads();
+    }
+    for (int j = tid; j < d; j += nt) mu[j] = mn[j] + Bd[j] / sqrt(kn);
+    double ld = 0.0;
+    for (int j = tid; j < d; j += nt) ld += log(W[j * d + j]);
+    ld = block_reduce_sum(ld, sh);
+    if (tid == 0) {
+        p_logdetW[s] = ld;
+        p_c[s] = logw[s] + ld - 0.5 * d * log(2.0 * M_PI);
+    }
+}
+
+// theta ~ Dir(beta + counts), as log theta (log-space Gamma draws).
+__global__ void dirichlet_params_kernel(StatView sv, const double* beta, const int* dK, const uint32_t* diter,
+                                        uint64_t seed, const double* logw, double* p_logtheta, double* p_c) {
+    __shared__ double sh[32];
+    const int d = sv.L.d;
+    const int K = *dK;
+    const int s = blockIdx.x;
+    if (s >= 3 * K) return;
+    const int k = s / 3, h = s % 3 - 1;
+    Key key{seed, *diter, 0};
+    double* lt = p_logtheta + (size_t)s * d;
+    double mx = -INFINITY;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double v = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, beta[j] + sv.m(k, h, j, d));
+        lt[j] = v;
+        mx = fmax(mx, v);
+    }
+    mx = block_reduce_max(mx, sh);
+    double sum = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sum += exp(lt[j] - mx);
+    double lse = mx + log(block_reduce_sum(sum, sh));
+    for (int j = threadIdx.x; j < d; j += blockDim.x) lt[j] -= lse;
+    if (threadIdx.x == 0) p_c[s] = logw[s];
+}
+
+// FP32 mirrors of the drawn parameters for the reduced-precision paths, and the
+// shift the next statistics are accumulated with (the cluster's drawn mean).
+__global__ void derive_kernel(int kind, int d, const int* dK, const double* p_logw, const double* p_mu,
+                              const double* p_W, const double* p_c, const double* p_logtheta, float* q_mu,
+                              float* q_W, float* q_c, float* q_b, float* q_logtheta, double* shift_new,
+                              float* shift32) {
+    const int K = *dK;
+    const int s = blockIdx.x;
+    if (s >= 3 * K) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (kind == DPMM_PRIOR_NIW) {
+        const double* W = p_W + (size_t)s * d * d;
+        const double* mu = p_mu + (size_t)s * d;
+        for (int e = tid; e < d * d; e += nt) q_W[(size_t)s * d * d + e] = (float)W[e];
+        for (int j = tid; j < d; j += nt) {
+            q_mu[(size_t)s * d + j] = (float)mu[j];
+            double b = 0.0;  // b_j = sum_l mu_l W_lj
+            for (int l = 0; l <= j; ++l) b += mu[l] * W[l * d + j];
+            q_b[(size_t)s * d + j] = (float)b;
+            if (s % 3 == 0) {
+                shift_new[(size_t)(s / 3) * d + j] = (double)(float)mu[j];
+                shift32[(size_t)(s / 3) * d + j] = (float)mu[j];
+            }
+        }
+    } else {
+        for (int j = tid; j < d; j += nt) q_logtheta[(size_t)s * d + j] = (float)p_logtheta[(size_t)s * d + j];
+    }
+    if (tid == 0) q_c[s] = (float)p_c[s];
+}
+
+static StatView make_sv(dpmm_ctx* c) { return StatView{c->stats, c->st}; }
+
+cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
+    prof_begin(c, "weights");
+    weights_kernel<<<1, 1024, 0, c->stream>>>(make_sv(c), c->dK, c->diter, seed, c->alpha, c->p_logw, c->cweights);
+    prof_end(c, "weights");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
+    if (c->kind == DPMM_PRIOR_NIW) {
+        size_t sm = sizeof(double) * ((size_t)c->d * c->d + 4 * c->d);
+        static int attr_set = 0;
+        if (sm > 48 * 1024 && !attr_set) {
+            cudaFuncSetAttribute(niw_params_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            attr_set = 1;
+        }
+        NiwPrior pr{c->kappa0, c->nu0, c->center + c->d, c->center + 2 * c->d};
+        prof_begin(c, "niw_params");
+        niw_params_kernel<<<3 * c->K_max, 128, sm, c->stream>>>(make_sv(c), c->shift_stats, pr, c->dK, c->diter, seed,
+                                                               c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c,
+                                                               c->derr);
+        prof_end(c, "niw_params");
+    } else {
+        prof_begin(c, "dirichlet_params");
+        dirichlet_params_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(make_sv(c), c->center + c->d, c->dK, c->diter,
+                                                                     seed, c->p_logw, c->p_logtheta, c->p_c);
+        prof_end(c, "dirichlet_params");
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_derive(dpmm_ctx* c) {
+    prof_begin(c, "derive");
+    derive_kernel<<<3 * c->K_max, 128, 0, c->stream>>>(c->kind, c->d, c->dK, c->p_logw, c->p_mu, c->p_W, c->p_c,
+                                                       c->p_logtheta, c->q_mu, c->q_W, c->q_c, c->q_b,
+                                                       c->q_logtheta, c->shift_new, c->shift32);
+    prof_end(c, "derive");
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && tc_supported(c)) e = tc_prepare(c);
+    return e;
+}
+
+}  // namespace dpmm

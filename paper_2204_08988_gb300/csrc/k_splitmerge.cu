@@ -1,0 +1,393 @@
+// k_splitmerge.cu -- splits and merges (Sec. 4.1, Eqs. sample_splits and
+// sample_merges; Sec. 4.3 "a cluster takes part in at most one merge").
+//
+//   marginal : log f_x(C; lambda) for every cluster, sub-cluster and cluster pair,
+//              FP64, one CTA per item (NIW: Cholesky log-determinant of Psi_n;
+//              Dirichlet-multinomial: lgamma sums).
+//   decision : one thread walks the proposals in the fixed order (splits by
+//              increasing k, then merge pairs in lexicographic order) with the
+//              Philox uniforms (tag SPLIT, c0 = k; tag MERGE, c0 = k1, block k2,
+//              indices after removing emptied clusters), and writes the relabel map.
+//   relabel  : applies it to z, z-bar (sub-labels of split clusters re-drawn, tag
+//              RESUB); gated: it returns at once when nothing changed.
+#include <math.h>
+
+#include "dpmm_internal.cuh"
+
+namespace dpmm {
+
+struct SMArgs {
+    const double* stats;
+    StatLayout L;
+    const double* shift_stats;  // K_max x d
+    const double* m0s;          // d (storage coordinates)
+    const double* psi0;         // d x d
+    const double* beta;         // d
+    double kappa0, nu0, logdet_psi0, alpha;
+    int kind, K_max;
+    const int* dK;
+};
+
+__device__ inline double smv(const SMArgs& a, int k, int h, int j, int l) {
+    int e = a.L.ent(j, l);
+    if (h >= 0) return a.stats[(size_t)(2 * k + h) * a.L.E + e];
+    return a.stats[(size_t)(2 * k) * a.L.E + e] + a.stats[(size_t)(2 * k + 1) * a.L.E + e];
+}
+
+__device__ inline double lmvgamma(double x, int d) {
+    double s = 0.25 * d * (d - 1) * log(M_PI);
+    for (int j = 1; j <= d; ++j) s += lgamma(x + 0.5 * (1 - j));
+    return s;
+}
+
+__device__ inline void pair_of(int p, int K, int& k1, int& k2) {
+    int r = 0, off = 0;
+    while (off + (K - r - 1) <= p) {
+        off += K - r - 1;
+        ++r;
+    }
+    k1 = r;
+    k2 = r + 1 + (p - off);
+}
+
+// Dynamic shared memory: d*d + 4*d doubles.
+__global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
+    extern __shared__ double smem[];
+    __shared__ double sh[32];
+    __shared__ double s_n, s_n1, s_n2;
+    const int K = *a.dK;
+    const int e = blockIdx.x;
+    const int npairs = K * (K - 1) / 2;
+    if (e >= 3 * K + npairs) return;
+    const int d = a.L.d, tid = threadIdx.x, nt = blockDim.x;
+    int k1, k2, h;
+    if (e < 3 * K) {
+        k1 = e / 3;
+        k2 = -1;
+        h = e % 3 - 1;
+    } else {
+        pair_of(e - 3 * K, K, k1, k2);
+        h = -1;
+    }
+    double* out = Ltab + (e < 3 * K ? e : 3 * a.K_max + (e - 3 * K));
+    if (a.kind == DPMM_PRIOR_DIRICHLET) {
+        double sb = 0.0, sc = 0.0, acc = 0.0;
+        for (int j = tid; j < d; j += nt) {
+            double c = smv(a, k1, h, j, d) + (k2 >= 0 ? smv(a, k2, -1, j, d) : 0.0);
+            sb += a.beta[j];
+            sc += c;
+            acc += lgamma(a.beta[j] + c) - lgamma(a.beta[j]);
+        }
+        sb = 0.0;
+        for (int j = 0; j < d; ++j) sb += a.beta[j];
+        double tot = 0.0;
+        // sum counts and lgamma terms over the block (fixed order)
+        for (int o = 16; o > 0; o >>= 1) {
+            sc += __shfl_xor_sync(0xffffffffu, sc, o);
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        }
+        __shared__ double shc[32], sha[32];
+        if ((tid & 31) == 0) {
+            shc[tid >> 5] = sc;
+            sha[tid >> 5] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double c = 0.0, l = 0.0;
+            for (int w = 0; w < (nt + 31) / 32; ++w) {
+                c += shc[w];
+                l += sha[w];
+            }
+            tot = l + lgamma(sb) - lgamma(sb + c);
+            *out = tot;
+        }
+        return;
+    }
+    double* A = smem;          // d x d
+    double* xb = A + d * d;    // merged mean
+    double* x1 = xb + d;
+    double* x2 = x1 + d;
+    if (tid == 0) {
+        s_n1 = smv(a, k1, h, d, d);
+        s_n2 = k2 >= 0 ? smv(a, k2, -1, d, d) : 0.0;
+        s_n = s_n1 + s_n2;
+    }
+    __syncthreads();
+    const double n1 = s_n1, n2 = s_n2, n = s_n;
+    for (int j = tid; j < d; j += nt) {
+        double m1 = n1 > 0 ? a.shift_stats[(size_t)k1 * d + j] + smv(a, k1, h, j, d) / n1 : 0.0;
+        double m2 = (k2 >= 0 && n2 > 0) ? a.shift_stats[(size_t)k2 * d + j] + smv(a, k2, -1, j, d) / n2 : 0.0;
+        x1[j] = m1;
+        x2[j] = m2;
+        xb[j] = n > 0 ? (n1 * m1 + n2 * m2) / n : 0.0;
+    }
+    __syncthreads();
+    const double kn = a.kappa0 + n, nun = a.nu0 + n;
+    const double f = n > 0 ? a.kappa0 * n / kn : 0.0;
+    for (int q = tid; q < d * d; q += nt) {
+        int j = q / d, l = q % d, lo = min(j, l), hi = max(j, l);
+        double C = 0.0;
+        if (n1 > 0) C += smv(a, k1, h, lo, hi) - smv(a, k1, h, lo, d) * smv(a, k1, h, hi, d) / n1;
+        if (k2 >= 0 && n2 > 0) {
+            C += smv(a, k2, -1, lo, hi) - smv(a, k2, -1, lo, d) * smv(a, k2, -1, hi, d) / n2;
+            if (n1 > 0) C += (n1 * n2 / n) * (x1[j] - x2[j]) * (x1[l] - x2[l]);
+        }
+        A[q] = a.psi0[q] + C + f * (xb[j] - a.m0s[j]) * (xb[l] - a.m0s[l]);
+    }
+    __syncthreads();
+    for (int j = 0; j < d; ++j) {
+        if (tid == 0) {
+            double v = A[j * d + j];
+            if (!(v > 0.0)) {
+                atomicExch(derr, (int)DPMM_ENUMERIC);
+                v = 1e-300;
+            }
+            A[j * d + j] = sqrt(v);
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] /= A[j * d + j];
+        __syncthreads();
+        int m = d - j - 1;
+        for (int q = tid; q < m * m; q += nt) {
+            int i = j + 1 + q / m, l = j + 1 + q % m;
+            if (l <= i) A[i * d + l] -= A[i * d + j] * A[l * d + j];
+        }
+        __syncthreads();
+    }
+    double ld = 0.0;
+    for (int j = tid; j < d; j += nt) ld += log(A[j * d + j]);
+    for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
+    if ((tid & 31) == 0) sh[tid >> 5] = ld;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (nt + 31) / 32; ++w) s += sh[w];
+        double ldn = 2.0 * s;
+        *out = -0.5 * n * d * log(M_PI) + lmvgamma(0.5 * nun, d) - lmvgamma(0.5 * a.nu0, d) +
+               0.5 * a.nu0 * a.logdet_psi0 - 0.5 * nun * ldn + 0.5 * d * (log(a.kappa0) - log(kn));
+    }
+}
+
+struct DecArgs {
+    SMArgs s;
+    const double* Ltab;
+    const uint32_t* diter;
+    uint64_t seed;
+    int burn_out, labels_ran, sm_enabled, init_mode;
+    int* age;          // K_max
+    int* dK;
+    int* relabel;      // 3 K_max: map_l, map_r, zmode
+    int* counters;     // [0] splits [1] merges [2] rejected (K_max) [3] removed [4] changed
+    double* shift_new; // K_max x d
+    float* shift32;
+};
+
+#define DEC_KMAX 1024
+
+__global__ void decision_kernel(DecArgs a) {
+    __shared__ int live[DEC_KMAX], cid[DEC_KMAX], split_to[DEC_KMAX], merged_into[DEC_KMAX], head[DEC_KMAX];
+    __shared__ int newid[DEC_KMAX], newid_split[DEC_KMAX], src[DEC_KMAX], nage[DEC_KMAX];
+    __shared__ int s_K, s_Knew;
+    const int tid = threadIdx.x;
+    const int K = *a.s.dK;
+    const int d = a.s.L.d;
+    if (tid == 0) {
+        Key key{a.seed, *a.diter, 0};
+        const double la = log(a.s.alpha), al = a.s.alpha;
+        int Kc = 0;
+        for (int k = 0; k < K; ++k) {
+            double nk = smv(a.s, k, -1, d, d);
+            live[k] = a.labels_ran ? (nk > 0) : 1;
+            cid[k] = live[k] ? Kc++ : -1;
+            split_to[k] = -1;
+            merged_into[k] = -1;
+            head[k] = 0;
+        }
+        int nsplit = 0, nmerge = 0, nrej = 0;
+        if (a.sm_enabled) {
+            int S = Kc;
+            for (int k = 0; k < K; ++k) {
+                if (!live[k]) continue;
+                double nl = smv(a.s, k, 0, d, d), nr = smv(a.s, k, 1, d, d), nk = nl + nr;
+                if (a.age[k] < a.burn_out || nl < 1 || nr < 1) continue;
+                double lH = la + lgamma(nl) + a.Ltab[3 * k + 1] + lgamma(nr) + a.Ltab[3 * k + 2] - lgamma(nk) -
+                            a.Ltab[3 * k];
+                double u = d_uniform(key, (uint32_t)cid[k], TAG_SPLIT, 0);
+                if (log(u) < lH) {
+                    if (S >= a.s.K_max) {
+                        ++nrej;
+                        continue;
+                    }
+                    split_to[k] = S++;
+                    ++nsplit;
+                }
+            }
+            for (int k1 = 0; k1 < K; ++k1) {
+                if (!live[k1] || split_to[k1] >= 0 || merged_into[k1] >= 0 || head[k1]) continue;
+                for (int k2 = k1 + 1; k2 < K; ++k2) {
+                    if (!live[k2] || split_to[k2] >= 0 || merged_into[k2] >= 0 || head[k2]) continue;
+                    double n1 = smv(a.s, k1, -1, d, d), n2 = smv(a.s, k2, -1, d, d), nm = n1 + n2;
+                    int p = k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1);
+                    double lH = lgamma(nm) - la - lgamma(n1) - lgamma(n2) + a.Ltab[3 * a.s.K_max + p] -
+                                a.Ltab[3 * k1] - a.Ltab[3 * k2] + lgamma(al) - lgamma(al + nm) + lgamma(0.5 * al + n1) +
+                                lgamma(0.5 * al + n2) - 2.0 * lgamma(0.5 * al);
+                    double u = d_uniform(key, (uint32_t)cid[k1], TAG_MERGE, (uint32_t)cid[k2]);
+                    if (log(u) < lH) {
+                        merged_into[k2] = k1;
+                        head[k1] = 1;
+                        ++nmerge;
+                        break;
+                    }
+                }
+            }
+        }
+        int nid = 0;
+        for (int k = 0; k < K; ++k)
+            if (live[k] && merged_into[k] < 0) {
+                newid[k] = nid;
+                src[nid] = k;
+                nage[nid] = (split_to[k] >= 0 || head[k]) ? 0 : a.age[k] + (a.init_mode ? 0 : 1);
+                ++nid;
+            } else {
+                newid[k] = -1;
+            }
+        for (int k = 0; k < K; ++k)
+            if (split_to[k] >= 0) {
+                newid_split[k] = nid;
+                src[nid] = k;
+                nage[nid] = 0;
+                ++nid;
+            }
+        int* map_l = a.relabel;
+        int* map_r = a.relabel + a.s.K_max;
+        int* zmode = a.relabel + 2 * a.s.K_max;
+        for (int k = 0; k < K; ++k) {
+            if (!live[k]) {
+                map_l[k] = map_r[k] = -1;
+                zmode[k] = 0;
+            } else if (split_to[k] >= 0) {
+                map_l[k] = newid[k];
+                map_r[k] = newid_split[k];
+                zmode[k] = 3;
+            } else if (merged_into[k] >= 0) {
+                map_l[k] = map_r[k] = newid[merged_into[k]];
+                zmode[k] = 2;
+            } else if (head[k]) {
+                map_l[k] = map_r[k] = newid[k];
+                zmode[k] = 1;
+            } else {
+                map_l[k] = map_r[k] = newid[k];
+                zmode[k] = 0;
+            }
+        }
+        a.counters[0] = nsplit;
+        a.counters[1] = nmerge;
+        a.counters[2] = nrej;
+        a.counters[3] = K - Kc;
+        a.counters[4] = (nid != K || nsplit || nmerge) ? 1 : 0;
+        s_K = K;
+        s_Knew = nid;
+    }
+    __syncthreads();
+    const int Kn = s_Knew;
+    for (int q = tid; q < Kn * d; q += blockDim.x) {
+        int k = q / d, j = q % d;
+        double v = a.s.shift_stats[(size_t)src[k] * d + j];
+        a.shift_new[(size_t)k * d + j] = v;
+        a.shift32[(size_t)k * d + j] = (float)v;
+    }
+    for (int k = tid; k < Kn; k += blockDim.x) a.age[k] = nage[k];
+    __syncthreads();
+    if (tid == 0) *a.dK = Kn;
+}
+
+__global__ void relabel_kernel(int64_t N, const int* relabel, int Kmax, const int* gate, const uint32_t* diter,
+                               uint64_t seed, int32_t* z, uint8_t* zbar) {
+    if (*gate == 0) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int k = z[i], h = zbar[i];
+    const int mode = relabel[2 * Kmax + k];
+    z[i] = h ? relabel[Kmax + k] : relabel[k];
+    if (mode == 1) zbar[i] = 0;
+    else if (mode == 2) zbar[i] = 1;
+    else if (mode == 3) {
+        Key key{seed, *diter, 0};
+        zbar[i] = d_uniform(key, (uint32_t)i, TAG_RESUB, 0) < 0.5 ? 0 : 1;
+    }
+}
+
+__global__ void advance_kernel(uint32_t* diter) { *diter += 1; }
+
+static SMArgs sm_args(dpmm_ctx* c) {
+    SMArgs a;
+    a.stats = c->stats;
+    a.L = c->st;
+    a.shift_stats = c->shift_stats;
+    a.m0s = c->center + c->d;
+    a.psi0 = c->center + 2 * c->d;
+    a.beta = c->center + c->d;
+    a.kappa0 = c->kappa0;
+    a.nu0 = c->nu0;
+    a.logdet_psi0 = c->logdet_psi0;
+    a.alpha = c->alpha;
+    a.kind = c->kind;
+    a.K_max = c->K_max;
+    a.dK = c->dK;
+    return a;
+}
+
+cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate);
+
+cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm_enabled) {
+    SMArgs s = sm_args(c);
+    if (sm_enabled) {
+        int items = 3 * c->K_max + c->K_max * (c->K_max - 1) / 2;
+        size_t sm = sizeof(double) * ((size_t)c->d * c->d + 4 * c->d);
+        static int attr = 0;
+        if (!attr) {
+            cudaFuncSetAttribute(marginal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            attr = 1;
+        }
+        prof_begin(c, "marginal");
+        marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);
+        prof_end(c, "marginal");
+    }
+    DecArgs a;
+    a.s = s;
+    a.Ltab = c->Ltab;
+    a.diter = c->diter;
+    a.seed = seed;
+    a.burn_out = c->burn_out;
+    a.labels_ran = labels_ran;
+    a.sm_enabled = sm_enabled;
+    a.init_mode = (labels_ran == 2);
+    a.labels_ran = labels_ran ? 1 : 0;
+    a.age = c->age;
+    a.dK = c->dK;
+    a.relabel = c->relabel;
+    a.counters = c->counters;
+    a.shift_new = c->shift_new;
+    a.shift32 = c->shift32;
+    prof_begin(c, "decision");
+    decision_kernel<<<1, 256, 0, c->stream>>>(a);
+    prof_end(c, "decision");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed) {
+    prof_begin(c, "relabel");
+    relabel_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->relabel, c->K_max, c->counters + 4,
+                                                                         c->diter, seed, c->z, c->zbar);
+    prof_end(c, "relabel");
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_restats_gated(c, c->counters + 4);
+    return e;
+}
+
+cudaError_t launch_advance(dpmm_ctx* c) {
+    advance_kernel<<<1, 1, 0, c->stream>>>(c->diter);
+    return cudaGetLastError();
+}
+
+}  // namespace dpmm

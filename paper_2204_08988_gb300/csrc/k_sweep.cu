@@ -1,0 +1,574 @@
+// k_sweep.cu -- the label step and the sufficient statistics (Sec. 4.1 steps (e),
+// (f); Sec. 4.4 "updating the sufficient statistics" in three steps).
+//
+//   labels_simt  : z_i = argmax_k [log pi_k + log f(x_i; theta_k) + G_ik] on CUDA
+//                  cores (FP64 parity path, FP32 for small d), one thread per point,
+//                  cluster parameters staged in shared memory and read by broadcast.
+//   hist/scan/scatter : stable counting sort of the points by cluster (tiles of 256
+//                  points), so that the next kernel sees each cluster as one run.
+//   substats     : per sorted run, z-bar_i from the two sub-clusters of z_i, then the
+//                  per-sub-cluster sums of xt xt^T (xt = [x - shift_k, 1]) as 4x4
+//                  register blocks, one partial record per (CTA, cluster) run.
+//   combine      : sums each cluster's records in CTA order (deterministic).
+#include <math.h>
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "dpmm_internal.cuh"
+
+namespace dpmm {
+
+template <typename T, typename XT>
+__device__ inline T ldx(const XT* p) { return (T)(*p); }
+template <>
+__device__ inline float ldx<float, __nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <typename T>
+struct ParamView {
+    const T* W;      // slots x d x d
+    const T* mu;     // slots x d
+    const T* c;      // slots
+    const T* lt;     // slots x d (multinomial)
+};
+
+template <typename T>
+__device__ inline T gumbel_of(uint32_t w0, uint32_t w1);
+template <>
+__device__ inline double gumbel_of<double>(uint32_t a, uint32_t b) {
+    return -log(-log(u01_f64(a, b)));
+}
+template <>
+__device__ inline float gumbel_of<float>(uint32_t a, uint32_t) {
+    // the inner log must be accurate near u = 1 (-log u is as small as 6e-8 there)
+    return -__logf(-logf(u01_f32(a)));
+}
+template <typename T>
+__device__ inline T gmax();
+template <>
+__device__ inline double gmax<double>() { return GUMBEL_MAX_F64; }
+template <>
+__device__ inline float gmax<float>() { return GUMBEL_MAX_F32; }
+
+// ------------------------------------------------------------------ labels (simt)
+// Dynamic shared memory: CB clusters x (d*d + d + 1) T, then 256 x (d + 1) T rows.
+template <typename T, typename XT>
+__global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int xs, int64_t N, const XT* __restrict__ X,
+                                                          ParamView<T> pv, const int* dK, const uint32_t* diter,
+                                                          uint64_t seed, int CB, int32_t* z) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sW = (T*)smraw;
+    const int per = kind == DPMM_PRIOR_NIW ? d * d + d + 1 : d + 1;
+    T* sx = sW + (size_t)CB * per;
+    const int K = *dK;
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    const bool live = i < N;
+    T* xr = sx + (size_t)tid * (d + 1);
+    if (live)
+        for (int j = 0; j < d; ++j) xr[j] = ldx<T, XT>(X + i * xs + j);
+    Key key{seed, *diter, 0};
+    T best = -INFINITY;
+    int zb = 0;
+    uint32_t w[4];
+    int wblk = -1;
+    for (int k0 = 0; k0 < K; k0 += CB) {
+        const int nc = min(CB, K - k0);
+        __syncthreads();
+        for (int e = tid; e < nc * per; e += 256) {
+            int cc = e / per, r = e % per;
+            int s = 3 * (k0 + cc);
+            T v;
+            if (kind == DPMM_PRIOR_NIW) {
+                if (r < d * d) v = pv.W[(size_t)s * d * d + r];
+                else if (r < d * d + d) v = pv.mu[(size_t)s * d + (r - d * d)];
+                else v = pv.c[s];
+            } else {
+                v = (r < d) ? pv.lt[(size_t)s * d + r] : pv.c[s];
+            }
+            sW[e] = v;
+        }
+        __syncthreads();
+        if (!live) continue;
+        for (int cc = 0; cc < nc; ++cc) {
+            const T* Wk = sW + (size_t)cc * per;
+            T sc;
+            if (kind == DPMM_PRIOR_NIW) {
+                const T* mk = Wk + d * d;
+                T q = 0;
+                for (int j = 0; j < d; ++j) {
+                    T y = 0;
+                    for (int l = 0; l <= j; ++l) y += Wk[l * d + j] * (xr[l] - mk[l]);
+                    q += y * y;
+                }
+                sc = Wk[d * d + d] - (T)0.5 * q;
+            } else {
+                T a = 0;
+                for (int j = 0; j < d; ++j) a += xr[j] * Wk[j];
+                sc = Wk[d] + a;
+            }
+            const int k = k0 + cc;
+            if (sc + gmax<T>() > best) {  // otherwise k cannot win the argmax
+                if ((k >> 1) != wblk) {
+                    key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
+                    wblk = k >> 1;
+                }
+                T g = (k & 1) ? gumbel_of<T>(w[2], w[3]) : gumbel_of<T>(w[0], w[1]);
+                T v = sc + g;
+                if (v > best) {
+                    best = v;
+                    zb = k;
+                }
+            }
+        }
+    }
+    if (live) z[i] = zb;
+}
+
+// ------------------------------------------------------------------ counting sort
+__global__ void hist_kernel(const int32_t* z, int64_t N, int T_tiles, int Kmax, const int* gate, int* hist) {
+    if (gate && *gate == 0) return;
+    extern __shared__ int cnt[];
+    const int t = blockIdx.x;
+    for (int k = threadIdx.x; k < Kmax; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)t * 256 + threadIdx.x;
+    if (i < N) atomicAdd(&cnt[z[i]], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < Kmax; k += blockDim.x) hist[(size_t)k * T_tiles + t] = cnt[k];
+}
+
+// exclusive scan of each cluster's row of tile counts; row total into tot[k]
+__global__ void scan_kernel(int* hist, int T_tiles, const int* dK, const int* gate, int* tot) {
+    if (gate && *gate == 0) return;
+    const int k = blockIdx.x;
+    if (k >= *dK) {
+        if (threadIdx.x == 0) tot[k] = 0;
+        return;
+    }
+    __shared__ int wsum[32];
+    int* row = hist + (size_t)k * T_tiles;
+    const int per = (T_tiles + blockDim.x - 1) / blockDim.x;
+    const int a = threadIdx.x * per, b = min(T_tiles, a + per);
+    int s = 0;
+    for (int t = a; t < b; ++t) s += row[t];
+    // block exclusive scan of s
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int v = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < nw) wsum[lane] = v;
+    }
+    __syncthreads();
+    int excl = x - s + (w > 0 ? wsum[w - 1] : 0);
+    for (int t = a; t < b; ++t) {
+        int v = row[t];
+        row[t] = excl;
+        excl += v;
+    }
+    if (threadIdx.x == blockDim.x - 1) tot[k] = excl;
+}
+
+// totals -> starts (exclusive prefix), starts[K] = N
+__global__ void starts_kernel(const int* dK, const int* gate, int* tot) {
+    if (gate && *gate == 0) return;
+    if (threadIdx.x != 0) return;
+    int K = *dK, acc = 0;
+    for (int k = 0; k < K; ++k) {
+        int v = tot[k];
+        tot[k] = acc;
+        acc += v;
+    }
+    tot[K] = acc;
+}
+
+__global__ void scatter_kernel(const int32_t* z, int64_t N, int T_tiles, const int* hist, const int* starts,
+                               const int* gate, int Kmax, int* idx) {
+    if (gate && *gate == 0) return;
+    extern __shared__ int wc[];  // 8 warps x Kmax
+    const int t = blockIdx.x;
+    for (int e = threadIdx.x; e < 8 * Kmax; e += blockDim.x) wc[e] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)t * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool live = i < N;
+    const int k = live ? z[i] : -1 - lane;  // dead lanes never match live ones
+    unsigned m = __match_any_sync(0xffffffffu, k);
+    int r = __popc(m & ((1u << lane) - 1u));
+    if (live && r == 0) wc[w * Kmax + k] = __popc(m);
+    __syncthreads();
+    if (live) {
+        int before = 0;
+        for (int v = 0; v < w; ++v) before += wc[v * Kmax + k];
+        int pos = starts[k] + hist[(size_t)k * T_tiles + t] + before + r;
+        idx[pos] = (int)i;
+    }
+}
+
+// ------------------------------------------------------------------ sub-labels + stats
+template <typename T>
+struct SubArgs {
+    int kind, d, xs;
+    int64_t N;
+    const void* X;
+    ParamView<T> pv;
+    const T* shift;  // K_max x d, storage coordinates
+    const int32_t* z;
+    uint8_t* zbar;
+    const int* idx;
+    const int* dK;
+    const uint32_t* diter;
+    const int* gate;
+    uint64_t seed;
+    int draw;        // 1: draw z-bar; 0: keep
+    int P;           // points per tile
+    int G;           // point groups per block
+    int64_t R;       // points per CTA
+    StatLayout L;
+    double* rec;     // (G2 + K_max) x 2 x E
+};
+
+template <typename T, typename XT>
+__device__ inline T sub_score(const SubArgs<T>& a, int s, const T* xr) {
+    const int d = a.d;
+    if (a.kind == DPMM_PRIOR_NIW) {
+        const T* W = a.pv.W + (size_t)s * d * d;
+        const T* mu = a.pv.mu + (size_t)s * d;
+        T q = 0;
+        for (int j = 0; j < d; ++j) {
+            T y = 0;
+            for (int l = 0; l <= j; ++l) y += __ldg(W + l * d + j) * (xr[l] - __ldg(mu + l));
+            q += y * y;
+        }
+        return __ldg(a.pv.c + s) - (T)0.5 * q;
+    }
+    const T* lt = a.pv.lt + (size_t)s * d;
+    T acc = 0;
+    for (int j = 0; j < d; ++j) acc += xr[j] * __ldg(lt + j);
+    return __ldg(a.pv.c + s) + acc;
+}
+
+// Dynamic shared memory: P x dp T (point rows), P ints (k), P bytes (h), then the
+// flush buffer G x nblk x 32 T.
+template <typename T, typename XT, int MAXT>
+__global__ void __launch_bounds__(MAXT) substats_kernel(SubArgs<T> a) {
+    if (a.gate && *a.gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int d = a.d, dp = a.L.dp, P = a.P, G = a.G, nblk = a.L.nblk;
+    T* xs = (T*)smraw;
+    int* kq = (int*)(xs + (size_t)P * dp);
+    int* runs = kq + P;          // run starts, P + 1
+    int* nruns = runs + P + 1;
+    unsigned char* hq = (unsigned char*)(nruns + 1);
+    T* red = (T*)(smraw + (((size_t)P * dp * sizeof(T) + (2 * P + 2) * sizeof(int) + P + 15) / 16) * 16);
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int g = blockIdx.x;
+    const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
+    Key key{a.seed, *a.diter, 0};
+    const XT* X = (const XT*)a.X;
+
+    // register block of this thread
+    const bool worker = tid < nblk * G;
+    const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
+    int jb = 0, lb = 0;
+    a.L.blk_coords(myblk, jb, lb);
+    T acc[16], accr[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = accr[e] = 0;
+    int cur = -1;
+
+    auto flush = [&](int k) {
+        __syncthreads();
+        if (worker) {
+            T* r = red + ((size_t)grp * nblk + myblk) * 32;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                r[e] = acc[e];
+                r[16 + e] = accr[e];
+            }
+        }
+        __syncthreads();
+        double* out = a.rec + (size_t)(g + k) * 2 * a.L.E;
+        for (int e = tid; e < nblk * 16; e += nt) {
+            int b = e >> 4, q = e & 15;
+            double all = 0.0, rr = 0.0;
+            for (int gg = 0; gg < G; ++gg) {
+                all += (double)red[((size_t)gg * nblk + b) * 32 + q];
+                rr += (double)red[((size_t)gg * nblk + b) * 32 + 16 + q];
+            }
+            out[b * 16 + q] = all - rr;       // sub-cluster l
+            out[a.L.E + b * 16 + q] = rr;     // sub-cluster r
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = accr[e] = 0;
+    };
+
+    for (int64_t base = p0; base < p1; base += P) {
+        const int np = (int)min((int64_t)P, p1 - base);
+        __syncthreads();
+        if (tid < np) {
+            const int i = a.idx[base + tid];
+            const int k = a.z[i];
+            T* xr = xs + (size_t)tid * dp;
+            for (int j = 0; j < d; ++j) xr[j] = ldx<T, XT>(X + (int64_t)i * a.xs + j);
+            int h;
+            if (a.draw) {
+                uint32_t w[4];
+                key.block((uint32_t)i, TAG_ZBAR, 0, w);
+                T vl = sub_score<T, XT>(a, 3 * k + 1, xr) + gumbel_of<T>(w[0], w[1]);
+                T vr = sub_score<T, XT>(a, 3 * k + 2, xr) + gumbel_of<T>(w[2], w[3]);
+                h = vr > vl ? 1 : 0;
+                a.zbar[i] = (uint8_t)h;
+            } else {
+                h = a.zbar[i];
+            }
+            const T* sh = a.shift + (size_t)k * d;
+            for (int j = 0; j < d; ++j) xr[j] -= sh[j];
+            xr[d] = 1;
+            for (int j = d + 1; j < dp; ++j) xr[j] = 0;
+            kq[tid] = k;
+            hq[tid] = (unsigned char)h;
+        }
+        __syncthreads();
+        if (tid == 0) {  // run starts of equal clusters in this tile
+            int n = 0;
+            for (int q = 0; q < np; ++q)
+                if (q == 0 || kq[q] != kq[q - 1]) runs[n++] = q;
+            runs[n] = np;
+            *nruns = n;
+        }
+        __syncthreads();
+        const int nr = *nruns;
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (k != cur) {
+                if (cur >= 0) flush(cur);
+                cur = k;
+            }
+            if (worker) {
+                for (int q = qs + grp; q < qe; q += G) {
+                    const T* xr = xs + (size_t)q * dp;
+                    T xj[4], xl[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        xj[u] = xr[jb * 4 + u];
+                        xl[u] = xr[lb * 4 + u];
+                    }
+                    const T hm = hq[q] ? (T)1 : (T)0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            T pr = xj[u] * xl[v];
+                            acc[u * 4 + v] += pr;
+                            accr[u * 4 + v] += hm * pr;
+                        }
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush(cur);
+}
+
+// stats[(2k + h) E + e] = sum over the CTAs g covering cluster k's run of rec[g + k]
+__global__ void combine_kernel(const double* rec, const int* starts, const int* dK, int64_t R, int E,
+                               const double* shift_new, double* shift_stats, int d, const int* gate,
+                               double* stats) {
+    if (gate && *gate == 0) return;
+    const int K = *dK;
+    const int kh = blockIdx.y, k = kh >> 1, h = kh & 1;
+    if (k >= K) return;
+    const int64_t st = starts[k], cnt = (int64_t)starts[k + 1] - st;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && h == 0)
+        for (int j = threadIdx.x; j < d; j += blockDim.x) shift_stats[(size_t)k * d + j] = shift_new[(size_t)k * d + j];
+    if (e >= E) return;
+    double v = 0.0;
+    if (cnt > 0) {
+        const int64_t g0 = st / R, g1 = (st + cnt - 1) / R;
+        for (int64_t g = g0; g <= g1; ++g) v += rec[((size_t)(g + k) * 2 + h) * E + e];
+    }
+    stats[(size_t)kh * E + e] = v;
+}
+
+// initial labels: K = init_K, z uniform over K, z-bar a fair coin (tag INIT, c1 = 0)
+__global__ void init_labels_kernel(int64_t N, int initK, uint64_t seed, int32_t* z, uint8_t* zbar) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    Key key{seed, 0, 0};
+    uint32_t w[4];
+    key.block((uint32_t)i, TAG_INIT, 0, w);
+    int k = (int)(u01_f64(w[0], w[1]) * initK);
+    if (k >= initK) k = initK - 1;
+    z[i] = k;
+    zbar[i] = u01_f64(w[2], w[3]) < 0.5 ? 0 : 1;
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+static ParamView<T> pview(dpmm_ctx* c);
+template <>
+ParamView<double> pview<double>(dpmm_ctx* c) { return {c->p_W, c->p_mu, c->p_c, c->p_logtheta}; }
+template <>
+ParamView<float> pview<float>(dpmm_ctx* c) { return {c->q_W, c->q_mu, c->q_c, c->q_logtheta}; }
+
+template <typename T, typename XT>
+static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed) {
+    const int d = c->d;
+    const size_t per = c->kind == DPMM_PRIOR_NIW ? (size_t)d * d + d + 1 : (size_t)d + 1;
+    const size_t rows = (size_t)256 * (d + 1) * sizeof(T);
+    size_t budget = 200 * 1024;
+    if (rows + per * sizeof(T) > budget) return cudaErrorInvalidValue;  // d too large for this kernel
+    int CB = (int)std::max<size_t>(1, std::min<size_t>(32, (budget - rows) / (per * sizeof(T))));
+    size_t sm = CB * per * sizeof(T) + rows;
+    cudaFuncSetAttribute(labels_simt_kernel<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int grid = (int)((c->N + 255) / 256);
+    labels_simt_kernel<T, XT><<<grid, 256, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c),
+                                                            c->dK, c->diter, seed, CB, c->z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_simt(dpmm_ctx* c, uint64_t seed) {
+    prof_begin(c, "labels_simt");
+    cudaError_t e;
+    if (c->prec == DPMM_PREC_FP64_PLAIN) e = labels_simt_t<double, double>(c, seed);
+    else e = labels_simt_t<float, float>(c, seed);
+    prof_end(c, "labels_simt");
+    return e;
+}
+
+static cudaError_t sort_impl(dpmm_ctx* c, const int* gate) {
+    prof_begin(c, "sort");
+    hist_kernel<<<c->T_tiles, 256, sizeof(int) * c->K_max, c->stream>>>(c->z, c->N, c->T_tiles, c->K_max, gate,
+                                                                         c->hist);
+    scan_kernel<<<c->K_max, 1024, 0, c->stream>>>(c->hist, c->T_tiles, c->dK, gate, c->tot);
+    starts_kernel<<<1, 32, 0, c->stream>>>(c->dK, gate, c->tot);
+    scatter_kernel<<<c->T_tiles, 256, sizeof(int) * 8 * c->K_max, c->stream>>>(c->z, c->N, c->T_tiles, c->hist, c->tot,
+                                                                               gate, c->K_max, c->idx);
+    prof_end(c, "sort");
+    return cudaGetLastError();
+}
+
+struct SubCfg {
+    int P, BT, G;
+    size_t smem;
+};
+
+template <typename T>
+static SubCfg sub_cfg(const dpmm_ctx* c) {
+    SubCfg q;
+    const StatLayout& L = c->st;
+    int P = (int)((64 * 1024) / ((size_t)L.dp * sizeof(T)));
+    P = std::max(32, std::min(256, P / 32 * 32));
+    int BT = std::max(P, L.nblk);
+    BT = std::min(1024, std::max(256, (BT + 31) / 32 * 32));
+    q.P = P;
+    q.BT = BT;
+    q.G = std::max(1, BT / L.nblk);
+    size_t head = (size_t)P * L.dp * sizeof(T) + (2 * (size_t)P + 2) * sizeof(int) + P;
+    head = (head + 15) / 16 * 16;
+    q.smem = head + (size_t)q.G * L.nblk * 32 * sizeof(T);
+    return q;
+}
+
+size_t substats_smem(const dpmm_ctx* c) {
+    return c->prec == DPMM_PREC_FP64_PLAIN ? sub_cfg<double>(c).smem : sub_cfg<float>(c).smem;
+}
+
+template <typename T, typename XT>
+static cudaError_t substats_t(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
+    SubCfg q = sub_cfg<T>(c);
+    SubArgs<T> a;
+    a.kind = c->kind;
+    a.d = c->d;
+    a.xs = c->xs;
+    a.N = c->N;
+    a.X = c->X;
+    a.pv = pview<T>(c);
+    a.shift = (const T*)(sizeof(T) == 8 ? (const void*)c->shift_new : (const void*)c->shift32);
+    a.z = c->z;
+    a.zbar = c->zbar;
+    a.idx = c->idx;
+    a.dK = c->dK;
+    a.diter = c->diter;
+    a.gate = gate;
+    a.seed = seed;
+    a.draw = draw;
+    a.P = q.P;
+    a.G = q.G;
+    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.L = c->st;
+    a.rec = c->records;
+    if (q.BT <= 256) {
+        cudaFuncSetAttribute(substats_kernel<T, XT, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+        substats_kernel<T, XT, 256><<<c->G2, q.BT, q.smem, c->stream>>>(a);
+    } else {
+        cudaFuncSetAttribute(substats_kernel<T, XT, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+        substats_kernel<T, XT, 1024><<<c->G2, q.BT, q.smem, c->stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t combine_impl(dpmm_ctx* c, const int* gate) {
+    dim3 grid((c->st.E + 255) / 256, 2 * c->K_max);
+    int64_t R = (c->N + c->G2 - 1) / c->G2;
+    combine_kernel<<<grid, 256, 0, c->stream>>>(c->records, c->tot, c->dK, R, c->st.E, c->shift_new, c->shift_stats,
+                                                c->d, gate, c->stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(dpmm_ctx* c) { return sort_impl(c, nullptr); }
+
+static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
+    prof_begin(c, draw ? "substats" : "restats");
+    cudaError_t e;
+    if (c->prec == DPMM_PREC_FP64_PLAIN) e = substats_t<double, double>(c, seed, draw, gate);
+    else if (c->xdt == 2) e = substats_t<float, __nv_bfloat16>(c, seed, draw, gate);
+    else e = substats_t<float, float>(c, seed, draw, gate);
+    prof_end(c, draw ? "substats" : "restats");
+    return e;
+}
+
+cudaError_t launch_substats(dpmm_ctx* c, uint64_t seed, int draw_zbar) {
+    return substats_dispatch(c, seed, draw_zbar, nullptr);
+}
+
+cudaError_t launch_combine(dpmm_ctx* c) {
+    prof_begin(c, "combine");
+    cudaError_t e = combine_impl(c, nullptr);
+    prof_end(c, "combine");
+    return e;
+}
+
+// statistics recomputed from the labels, only when the split/merge step changed them
+cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate) {
+    cudaError_t e = sort_impl(c, gate);
+    if (e == cudaSuccess) e = substats_dispatch(c, 0, 0, gate);
+    if (e == cudaSuccess) {
+        prof_begin(c, "combine");
+        e = combine_impl(c, gate);
+        prof_end(c, "combine");
+    }
+    return e;
+}
+
+cudaError_t launch_init_labels(dpmm_ctx* c, uint64_t seed) {
+    init_labels_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->init_K, seed, c->z, c->zbar);
+    return cudaGetLastError();
+}
+
+}  // namespace dpmm
