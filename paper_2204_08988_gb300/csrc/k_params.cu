@@ -45,13 +45,13 @@ __device__ inline double block_reduce_sum(double v, double* sh) {
 }
 
 // (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2).
-__global__ void weights_kernel(StatView sv, const int* dK, const uint32_t* diter, uint64_t seed, double alpha,
+__global__ void __launch_bounds__(256) weights_kernel(StatView sv, const int* dK, const uint32_t* diter, uint64_t seed, double alpha,
                                double* logw, double* cweights) {
     __shared__ double sh[32];
     const int K = *dK;
     Key key{seed, *diter, 0};
     double lmax = -INFINITY;
-    // each thread keeps at most a few draws; K + 1 <= 4 * blockDim
+    // each thread keeps at most 4 draws: K + 1 <= 1001 <= 4 * 256
     double lg[4];
     int cnt = 0;
     for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) {
@@ -262,7 +262,7 @@ static StatView make_sv(dpmm_ctx* c) { return StatView{c->stats, c->st}; }
 
 cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
     prof_begin(c, "weights");
-    weights_kernel<<<1, 1024, 0, c->stream>>>(make_sv(c), c->dK, c->diter, seed, c->alpha, c->p_logw, c->cweights);
+    weights_kernel<<<1, 256, 0, c->stream>>>(make_sv(c), c->dK, c->diter, seed, c->alpha, c->p_logw, c->cweights);
     prof_end(c, "weights");
     return cudaGetLastError();
 }
@@ -270,10 +270,9 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
 cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
     if (c->kind == DPMM_PRIOR_NIW) {
         size_t sm = sizeof(double) * ((size_t)c->d * c->d + 4 * c->d);
-        static int attr_set = 0;
-        if (sm > 48 * 1024 && !attr_set) {
-            cudaFuncSetAttribute(niw_params_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr_set = 1;
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(niw_params_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
         }
         NiwPrior pr{c->kappa0, c->nu0, c->center + c->d, c->center + 2 * c->d};
         prof_begin(c, "niw_params");

@@ -344,10 +344,9 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     if (sm_enabled) {
         int items = 3 * c->K_max + c->K_max * (c->K_max - 1) / 2;
         size_t sm = sizeof(double) * ((size_t)c->d * c->d + 4 * c->d);
-        static int attr = 0;
-        if (!attr) {
-            cudaFuncSetAttribute(marginal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr = 1;
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(marginal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
         }
         prof_begin(c, "marginal");
         marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);

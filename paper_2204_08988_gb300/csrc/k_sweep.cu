@@ -435,7 +435,8 @@ static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed) {
     if (rows + per * sizeof(T) > budget) return cudaErrorInvalidValue;  // d too large for this kernel
     int CB = (int)std::max<size_t>(1, std::min<size_t>(32, (budget - rows) / (per * sizeof(T))));
     size_t sm = CB * per * sizeof(T) + rows;
-    cudaFuncSetAttribute(labels_simt_kernel<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t ea = cudaFuncSetAttribute(labels_simt_kernel<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ea != cudaSuccess) return ea;
     int grid = (int)((c->N + 255) / 256);
     labels_simt_kernel<T, XT><<<grid, 256, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c),
                                                             c->dK, c->diter, seed, CB, c->z);
@@ -514,10 +515,12 @@ static cudaError_t substats_t(dpmm_ctx* c, uint64_t seed, int draw, const int* g
     a.L = c->st;
     a.rec = c->records;
     if (q.BT <= 256) {
-        cudaFuncSetAttribute(substats_kernel<T, XT, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+        cudaError_t ea = cudaFuncSetAttribute(substats_kernel<T, XT, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+        if (ea != cudaSuccess) return ea;
         substats_kernel<T, XT, 256><<<c->G2, q.BT, q.smem, c->stream>>>(a);
     } else {
-        cudaFuncSetAttribute(substats_kernel<T, XT, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+        cudaError_t ea = cudaFuncSetAttribute(substats_kernel<T, XT, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
+        if (ea != cudaSuccess) return ea;
         substats_kernel<T, XT, 1024><<<c->G2, q.BT, q.smem, c->stream>>>(a);
     }
     return cudaGetLastError();
