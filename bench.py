@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Throughput of the DPMM sweep (point-sweeps/s = N * sweeps / second) on GB300.
+
+One step is one sweep of Sec. 4.1 -- parameter draws, label step, sufficient
+statistics, splits and merges -- over all N points, with the data resident in HBM.
+The default workload is the d=32, N=1e6 Gaussian mixture (20 clusters, Dirichlet(1)
+weights, means N(0, 25 I), Wishart(I, d+2) covariances, FP32 data, NIW prior with
+kappa0=1, m0=0, nu0=d+3, Psi0=I, alpha=10), synthetic and seeded.  The chain is
+burned in (untimed) from K=1 until its cluster count has settled, then W warm-up
+and K timed sweeps follow.  L2 is flushed (256 MiB write) between timed steps,
+outside the timed events.
+
+--impl reference times the FP64 CPU oracle (the paper's method written as plain
+loops) on a bounded sample of the same workload, on this host's cores.
+Multi-GPU (torchrun): independent replicas, one chain per GPU (weak scaling).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
+DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32"}
+METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
+WORKLOADS = {
+    "gauss_d32": dict(K_max=64),
+    "gauss_d2": dict(K_max=64),
+    "multinomial": dict(K_max=128),
+    "gauss_d128": dict(K_max=128),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gauss_d32", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="tf32", choices=sorted(PREC))
+    ap.add_argument("--burnin", type=int, default=150)
+    ap.add_argument("--n", type=int, default=None, help="override N (smaller cases for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.3)
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if len(r) > 5 + j and r[5 + j].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_workload(name, n, seed_offset):
+    from paper_2204_08988_gb300 import synth
+
+    base = {"gauss_d2": 1001, "gauss_d32": 1002, "multinomial": 1003, "gauss_d128": 1004}[name]
+    X, y, prior, opt = synth.workload(name, N=n, seed=base + seed_offset)
+    return X, y, prior, opt
+
+
+def oracle_rate(name, X, y, prior, opt, budget_s=12.0, max_sweeps=4):
+    """The FP64 oracle on a bounded sample: its own chain from the generating labels."""
+    import oracle as O
+
+    kind = O.NIW if prior["kind"] == 0 else O.DIRICHLET
+    kw = {k: v for k, v in prior.items() if k != "kind"}
+    K = int(y.max()) + 1
+    o = O.Oracle(kind, X.shape[1], max(64, K), opt["alpha"], burn_out=15, **kw)
+    # size the sample from a probe so the whole measurement stays ~budget_s
+    n0 = min(len(X), 2000)
+    o.set_data(X[:n0].astype(np.float64))
+    o.set_state(K, y[:n0] % K, (np.arange(n0) % 2).astype(np.uint8))
+    t0 = time.perf_counter()
+    o.sweep(1, 1)
+    per_pt = (time.perf_counter() - t0) / n0
+    n = int(min(len(X), max(n0, budget_s / max_sweeps / max(per_pt, 1e-9))))
+    o.set_data(X[:n].astype(np.float64))
+    o.set_state(K, y[:n] % K, (np.arange(n) % 2).astype(np.uint8))
+    sweeps = 0
+    t0 = time.perf_counter()
+    while sweeps < max_sweeps and (time.perf_counter() - t0) < budget_s:
+        o.sweep(1, 1)
+        sweeps += 1
+    el = time.perf_counter() - t0
+    return n * sweeps / el, dict(n=n, sweeps=sweeps, K=K, seconds=el)
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    X, y, prior, opt = load_workload(a.workload, a.n, 0)
+    N = X.shape[0]
+    vals = []
+    info = None
+    steps = max(1, min(a.steps, 3))
+    for _ in range(steps):
+        v, info = oracle_rate(a.workload, X, y, prior, opt, budget_s=8.0, max_sweeps=2)
+        vals.append(v)
+    v = float(np.median(vals))
+    sample = "first %d of the N=%d points, %d sweeps per step from the generating labels (K=%d)" % (
+        info["n"], N, info["sweeps"], info["K"])
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-sweeps/s", "n_gpus": a.gpus,
+           "steps": steps, "warmup": 0, "ms_per_step": 1e3 * N / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": a.workload, "N": N, "d": int(X.shape[1]), "sample": sample},
+           "cpu_baseline": {"value": v, "unit": "point-sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "point-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    import paper_2204_08988_gb300 as P
+    from paper_2204_08988_gb300 import _build
+
+    _build.build()
+
+    X, y, prior, opt = load_workload(a.workload, a.n, rank)
+    N, d = X.shape
+    kind = prior["kind"]
+    kw = {k: v for k, v in prior.items() if k != "kind"}
+    K_max = WORKLOADS[a.workload]["K_max"]
+    stream = torch.cuda.Stream()
+    g = P.DPMM(kind, d, K_max, opt["alpha"], prec=PREC[a.prec], init_K=1, burn_out=15,
+               stream=stream.cuda_stream, **kw)
+    Xd = torch.from_numpy(X).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        g.set_data(Xd)
+    seed = 0
+    g.sweep(a.burnin, seed)
+    K0 = g.K
+    g.sweep(a.warmup, seed)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P.dpmm_profile(g.h, 2)  # events around the label kernel only
+    Ks = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    barrier()
+    with Clocks(local) as clk:
+        for s in range(a.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush, outside the timed events
+                ev[s][0].record(stream)
+            g.sweep(1, seed)
+            with torch.cuda.stream(stream):
+                ev[s][1].record(stream)
+            Ks.append(g.K)  # synchronises, outside the events
+        barrier()
+    step_ms = [b.elapsed_time(e) for b, e in ev]
+    total_ms = float(sum(step_ms))
+    prof = P.dpmm_get_profile(g.h)
+    P.dpmm_profile(g.h, 0)
+    if dist:
+        t = torch.tensor([total_ms])
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * N * a.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel: the label step
+    lk = [k for k in prof if k.startswith("labels")]
+    roof = None
+    if lk:
+        launches, ms = prof[lk[0]]
+        avg_s = ms / max(launches, 1) / 1e3
+        Kavg = float(np.mean(Ks))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        if kind == 0:
+            flops = 2.0 * N * d * d * Kavg  # X (N x d) times the K stacked d x d factors
+            if a.prec in ("tf32", "bf16"):
+                bf16 = peaks.get("bf16_tflops", 1900.0)
+                peak = bf16 * (1.1 / 2.25) if a.prec == "tf32" else bf16
+                roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "peak_source": ("measured bf16 x nominal tf32/bf16 ratio 1.1/2.25" if a.prec == "tf32"
+                                        else "measured bf16 burst")}
+            else:
+                # CUDA-core paths: FMA pipe peak from 152 SMs x 128 FP32 lanes x 2 flop at the max SM clock
+                peak = 152 * 128 * 2 * 2.07e9 / 1e12 if a.prec == "fp32" else 1.25
+                roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "peak_source": "fp32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz" if a.prec == "fp32"
+                        else "fp64: nominal 1.25 TFLOP/s"}
+        else:
+            bytes_ = N * d * (2 if a.prec == "bf16" else 4) + 4 * N
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "peak_source": "measured copy bandwidth"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        roof["kernel"] = lk[0]
+        roof["kernel_ms_avg"] = ms / max(launches, 1)
+    gpu_launches = prof.get("all_kernels", (0, 0))[0]
+
+    # end to end through the C ABI: pinned host X in, labels out, every step
+    e2e = None
+    if not a.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        zh = torch.empty(N, dtype=torch.int32).pin_memory()
+        zbh = torch.empty(N, dtype=torch.uint8).pin_memory()
+        h2d = Xh.numel() * Xh.element_size()
+        d2h = N * 5
+        g.update_data(Xh)
+        P.dpmm_get_labels(g.h, N, zh, zbh)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(a.steps):
+            g.update_data(Xh)
+            g.sweep(1, seed)
+            P.dpmm_get_labels(g.h, N, zh, zbh)
+        barrier()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el])
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * N * a.steps / el, "unit": "point-sweeps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        v, info = oracle_rate(a.workload, X, y, prior, opt)
+        cpu = {"value": v, "unit": "point-sweeps/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d of the N=%d points, %d sweep(s) from the generating labels (K=%d), "
+                         "single-threaded FP64 oracle" % (info["n"], N, info["sweeps"], info["K"])}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "point-sweeps/s", "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": DTYPE[a.prec], "data": "synthetic",
+               "config": {"workload": a.workload, "N": N, "d": d, "K_start": K0, "K_timed": Ks, "K_max": K_max,
+                          "prec": a.prec, "burnin_sweeps": a.burnin, "parallelism": "replicas" if world > 1 else "1gpu",
+                          "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+               "gpu_launches": gpu_launches, "step_ms": step_ms}
+        print(json.dumps(out))
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

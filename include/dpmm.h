@@ -155,10 +155,12 @@ dpmm_status dpmm_get_params(dpmm_ctx* ctx, double* logw, double* mu, double* W, 
 /* Overwrite the sweep counter (so that a test can replay one sweep index). */
 dpmm_status dpmm_set_iter(dpmm_ctx* ctx, uint32_t iter);
 
-/* Kernel timing: when enabled, every kernel launch of the sweep is bracketed by
- * CUDA events on the context's stream.  dpmm_get_profile returns, for up to `cap`
- * kernels, the name, the number of launches and the summed device time (ms)
- * since the last reset, and the number of kernels known.  Synchronises. */
+/* Kernel timing.  enable = 1 brackets every kernel launch of the sweep with CUDA
+ * events on the context's stream; enable = 2 only the label-step kernel; 0 turns
+ * it off.  Each call resets the records.  dpmm_get_profile returns, for up to
+ * `cap` entries, the kernel name, its launches and summed device time (ms) since
+ * the reset, then one entry "all_kernels" whose launch count is every kernel the
+ * library launched since the reset; *count is the number of entries.  Synchronises. */
 dpmm_status dpmm_profile(dpmm_ctx* ctx, int enable);
 dpmm_status dpmm_get_profile(dpmm_ctx* ctx, int cap, const char** names, int* launches, double* ms, int* count);
 

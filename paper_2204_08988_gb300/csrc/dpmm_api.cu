@@ -15,8 +15,12 @@ using namespace dpmm;
 namespace dpmm {
 cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate);
 
+static bool prof_on(const dpmm_ctx* c, const char* name) {
+    return c->profiling == 1 || (c->profiling == 2 && strncmp(name, "labels", 6) == 0);
+}
+
 void prof_begin(dpmm_ctx* c, const char* name) {
-    if (!c->profiling) return;
+    if (!prof_on(c, name)) return;
     Profile* p = nullptr;
     for (auto& q : c->prof)
         if (q.name == name) p = &q;
@@ -32,7 +36,7 @@ void prof_begin(dpmm_ctx* c, const char* name) {
 }
 
 void prof_end(dpmm_ctx* c, const char* name) {
-    if (!c->profiling) return;
+    if (!prof_on(c, name)) return;
     for (auto& q : c->prof)
         if (q.name == name) {
             cudaEvent_t e;
@@ -598,7 +602,8 @@ dpmm_status dpmm_profile(dpmm_ctx* c, int enable) {
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
     c->prof.clear();
-    c->profiling = enable != 0;
+    c->profiling = enable;
+    c->nlaunch = 0;
     return DPMM_OK;
 }
 
@@ -622,6 +627,13 @@ dpmm_status dpmm_get_profile(dpmm_ctx* c, int cap, const char** names, int* laun
         }
         ++i;
     }
+    static const char* total = "all_kernels";
+    if (i < cap) {
+        if (names) names[i] = total;
+        if (launches) launches[i] = (int)c->nlaunch;
+        if (ms) ms[i] = 0.0;
+    }
+    ++i;
     if (count) *count = i;
     return DPMM_OK;
 }

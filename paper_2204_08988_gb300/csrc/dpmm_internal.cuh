@@ -208,8 +208,9 @@ struct dpmm_ctx {
     // tensor-core path
     void* tmap_x = nullptr;  // host copy of the CUtensorMap for X (128 bytes)
 
-    // profiling
-    bool profiling = false;
+    // profiling: 0 off, 1 every kernel, 2 only the label kernel
+    int profiling = 0;
+    int64_t nlaunch = 0;  // kernels launched since the last dpmm_profile call
     std::vector<dpmm::Profile> prof;
 };
 

@@ -264,6 +264,7 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
     prof_begin(c, "weights");
     weights_kernel<<<1, 256, 0, c->stream>>>(make_sv(c), c->dK, c->diter, seed, c->alpha, c->p_logw, c->cweights);
     prof_end(c, "weights");
+    c->nlaunch += 1;
     return cudaGetLastError();
 }
 
@@ -280,11 +281,13 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
                                                                c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c,
                                                                c->derr);
         prof_end(c, "niw_params");
+        c->nlaunch += 1;
     } else {
         prof_begin(c, "dirichlet_params");
         dirichlet_params_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(make_sv(c), c->center + c->d, c->dK, c->diter,
                                                                      seed, c->p_logw, c->p_logtheta, c->p_c);
         prof_end(c, "dirichlet_params");
+        c->nlaunch += 1;
     }
     return cudaGetLastError();
 }
@@ -295,6 +298,7 @@ cudaError_t launch_derive(dpmm_ctx* c) {
                                                        c->p_logtheta, c->q_mu, c->q_W, c->q_c, c->q_b,
                                                        c->q_logtheta, c->shift_new, c->shift32);
     prof_end(c, "derive");
+    c->nlaunch += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && tc_supported(c)) e = tc_prepare(c);
     return e;

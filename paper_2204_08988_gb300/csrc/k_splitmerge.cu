@@ -351,6 +351,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
         prof_begin(c, "marginal");
         marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);
         prof_end(c, "marginal");
+        c->nlaunch += 1;
     }
     DecArgs a;
     a.s = s;
@@ -371,6 +372,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     prof_begin(c, "decision");
     decision_kernel<<<1, 256, 0, c->stream>>>(a);
     prof_end(c, "decision");
+    c->nlaunch += 1;
     return cudaGetLastError();
 }
 
@@ -379,6 +381,7 @@ cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed) {
     relabel_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->relabel, c->K_max, c->counters + 4,
                                                                          c->diter, seed, c->z, c->zbar);
     prof_end(c, "relabel");
+    c->nlaunch += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_restats_gated(c, c->counters + 4);
     return e;
@@ -386,6 +389,7 @@ cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed) {
 
 cudaError_t launch_advance(dpmm_ctx* c) {
     advance_kernel<<<1, 1, 0, c->stream>>>(c->diter);
+    c->nlaunch += 1;
     return cudaGetLastError();
 }
 

@@ -449,6 +449,7 @@ cudaError_t launch_labels_simt(dpmm_ctx* c, uint64_t seed) {
     if (c->prec == DPMM_PREC_FP64_PLAIN) e = labels_simt_t<double, double>(c, seed);
     else e = labels_simt_t<float, float>(c, seed);
     prof_end(c, "labels_simt");
+    c->nlaunch += 1;
     return e;
 }
 
@@ -461,6 +462,7 @@ static cudaError_t sort_impl(dpmm_ctx* c, const int* gate) {
     scatter_kernel<<<c->T_tiles, 256, sizeof(int) * 8 * c->K_max, c->stream>>>(c->z, c->N, c->T_tiles, c->hist, c->tot,
                                                                                gate, c->K_max, c->idx);
     prof_end(c, "sort");
+    c->nlaunch += 4;
     return cudaGetLastError();
 }
 
@@ -543,6 +545,7 @@ static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const
     else if (c->xdt == 2) e = substats_t<float, __nv_bfloat16>(c, seed, draw, gate);
     else e = substats_t<float, float>(c, seed, draw, gate);
     prof_end(c, draw ? "substats" : "restats");
+    c->nlaunch += 1;
     return e;
 }
 
@@ -554,6 +557,7 @@ cudaError_t launch_combine(dpmm_ctx* c) {
     prof_begin(c, "combine");
     cudaError_t e = combine_impl(c, nullptr);
     prof_end(c, "combine");
+    c->nlaunch += 1;
     return e;
 }
 
@@ -565,11 +569,13 @@ cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate) {
         prof_begin(c, "combine");
         e = combine_impl(c, gate);
         prof_end(c, "combine");
+        c->nlaunch += 1;
     }
     return e;
 }
 
 cudaError_t launch_init_labels(dpmm_ctx* c, uint64_t seed) {
+    c->nlaunch += 1;
     init_labels_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->init_K, seed, c->z, c->zbar);
     return cudaGetLastError();
 }
