@@ -164,6 +164,30 @@ dpmm_status dpmm_set_iter(dpmm_ctx* ctx, uint32_t iter);
 dpmm_status dpmm_profile(dpmm_ctx* ctx, int enable);
 dpmm_status dpmm_get_profile(dpmm_ctx* ctx, int cap, const char** names, int* launches, double* ms, int* count);
 
+/* ---- allocation-free statistics (no counterpart in the paper) ---- */
+
+/* Sufficient statistics of given labels without allocating any memory: for callers
+ * that cannot call cudaMalloc where they need this (code running inside a stream
+ * capture for a CUDA graph, or an application that partitions device memory up
+ * front with its own allocator and forbids allocation afterwards).
+ *
+ * Inputs, all device memory of the current device: X (N x d row-major FP32), z[N]
+ * in [0, K) and zbar[N] in {0, 1}.  Outputs, device memory of length 2K, 2K x d and
+ * 2K x d x d: for sub-cluster slot 2k + h, n_out = count, sx_out = sum of x,
+ * sxx_out = sum of x x^T over the points with (z, zbar) = (k, h), in FP64 (per-tile
+ * FP32 sums added in FP64).  Points whose label is outside that range are ignored.
+ * The call is asynchronous on `stream` (a cudaStream_t or NULL).
+ *
+ * Limits: 1 <= d <= 32, 1 <= K <= 16, N >= 1; anything else returns DPMM_EINVAL
+ * before any work.  Scratch is a fixed 5.6 MiB array inside the library's device
+ * image (held by every GPU that loads the library until the process exits); the
+ * first call on each device looks up its address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls on a device share the
+ * array: calls whose kernels overlap on the GPU (other streams, other threads) race
+ * and give wrong results; serialise them.  Returns DPMM_ECUDA on a CUDA error. */
+dpmm_status dpmm_suffstats_noalloc(const float* X, int64_t N, int d, const int32_t* z, const uint8_t* zbar,
+                                   int K, double* n_out, double* sx_out, double* sxx_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

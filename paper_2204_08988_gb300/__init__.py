@@ -31,7 +31,7 @@ EXPORTS = [
     "dpmm_create", "dpmm_set_options", "dpmm_set_data", "dpmm_update_data", "dpmm_sweep", "dpmm_get_labels",
     "dpmm_get_stats", "dpmm_get_info", "dpmm_get_counters", "dpmm_last_error", "dpmm_destroy",
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
-    "dpmm_profile", "dpmm_get_profile",
+    "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc",
 ]
 
 
@@ -79,6 +79,7 @@ def load():
             "dpmm_set_iter": ([vp, u32], i32),
             "dpmm_profile": ([vp, i32], i32),
             "dpmm_get_profile": ([vp, i32, vp, vp, vp, C.POINTER(i32)], i32),
+            "dpmm_suffstats_noalloc": ([vp, i64, i32, vp, vp, i32, vp, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -217,6 +218,15 @@ def dpmm_get_profile(h):
     cnt = C.c_int()
     _check(h, load().dpmm_get_profile(h, cap, C.cast(names, C.c_void_p), _p(launches), _p(ms), C.byref(cnt)))
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(cnt.value, cap))}
+
+
+def dpmm_suffstats_noalloc(X, z, zbar, K, n_out, sx_out, sxx_out, stream=None):
+    """Statistics of given labels with no allocation (CUDA tensors in and out)."""
+    N, d = X.shape
+    st = load().dpmm_suffstats_noalloc(C.c_void_p(X.data_ptr()), int(N), int(d), C.c_void_p(z.data_ptr()),
+                                       C.c_void_p(zbar.data_ptr()), int(K), C.c_void_p(n_out.data_ptr()),
+                                       C.c_void_p(sx_out.data_ptr()), C.c_void_p(sxx_out.data_ptr()), stream)
+    _check(None, st)
 
 
 def dpmm_last_error(h):
