@@ -152,6 +152,12 @@ dpmm_status dpmm_set_params(dpmm_ctx* ctx, int K, const double* logw, const doub
 dpmm_status dpmm_get_params(dpmm_ctx* ctx, double* logw, double* mu, double* W, double* logdetW,
                             double* logtheta);
 
+/* The label step's cluster scores log pi_k + log f(x_i; theta_k) (before the Gumbel
+ * perturbation) for the current parameters, computed by this precision's label
+ * kernel, into a host array scores[N x K] (K from dpmm_get_info).  The chain's
+ * labels are left as they were.  Synchronises. */
+dpmm_status dpmm_label_scores(dpmm_ctx* ctx, double* scores);
+
 /* Overwrite the sweep counter (so that a test can replay one sweep index). */
 dpmm_status dpmm_set_iter(dpmm_ctx* ctx, uint32_t iter);
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "dpmm_create", "dpmm_set_options", "dpmm_set_data", "dpmm_update_data", "dpmm_sweep", "dpmm_get_labels",
     "dpmm_get_stats", "dpmm_get_info", "dpmm_get_counters", "dpmm_last_error", "dpmm_destroy",
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
-    "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc",
+    "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores",
 ]
 
 
@@ -80,6 +80,7 @@ def load():
             "dpmm_profile": ([vp, i32], i32),
             "dpmm_get_profile": ([vp, i32, vp, vp, vp, C.POINTER(i32)], i32),
             "dpmm_suffstats_noalloc": ([vp, i64, i32, vp, vp, i32, vp, vp, vp, vp], i32),
+            "dpmm_label_scores": ([vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -206,6 +207,12 @@ def dpmm_get_params(h, d, gaussian=True):
     return dict(logw=logw, logtheta=lt)
 
 
+def dpmm_label_scores(h, N, K):
+    out = np.empty((N, K))
+    _check(h, load().dpmm_label_scores(h, _p(out)))
+    return out
+
+
 def dpmm_profile(h, enable):
     _check(h, load().dpmm_profile(h, int(enable)))
 
@@ -301,3 +308,6 @@ class DPMM:
 
     def params(self):
         return dpmm_get_params(self.h, self.d, self.kind == PRIOR_NIW)
+
+    def label_scores(self):
+        return dpmm_label_scores(self.h, self.N, self.K)

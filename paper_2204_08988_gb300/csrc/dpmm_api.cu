@@ -123,7 +123,7 @@ template <>
 __device__ inline __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
 template <typename IN, typename OUT>
-__global__ void convert_kernel(const IN* X, int64_t N, int d, int xs, const double* center, OUT* Y) {
+__global__ void convert_kernel(const IN* X, int64_t N, int d, int xs, const double* center, int tf32, OUT* Y) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = N * xs;
     if (q >= total) return;
@@ -132,6 +132,9 @@ __global__ void convert_kernel(const IN* X, int64_t N, int d, int xs, const doub
     double v = 0.0;
     if (j < d) v = to_d(X[i * d + j]) - center[j];
     Y[q] = from_d<OUT>(v);
+    if constexpr (sizeof(OUT) == 4) {
+        if (tf32) Y[q] = round_tf32((float)Y[q]);  // the tensor-core operand, stored exactly
+    }
 }
 
 template <typename IN>
@@ -149,9 +152,10 @@ static cudaError_t convert_any(dpmm_ctx* c, const IN* src, bool compute_center) 
     }
     int64_t total = c->N * c->xs;
     unsigned grid = (unsigned)((total + 255) / 256);
-    if (c->xdt == 0) convert_kernel<IN, double><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, (double*)c->X);
-    else if (c->xdt == 1) convert_kernel<IN, float><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, (float*)c->X);
-    else convert_kernel<IN, __nv_bfloat16><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, (__nv_bfloat16*)c->X);
+    const int tf32 = c->prec == DPMM_PREC_TF32;
+    if (c->xdt == 0) convert_kernel<IN, double><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, 0, (double*)c->X);
+    else if (c->xdt == 1) convert_kernel<IN, float><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, tf32, (float*)c->X);
+    else convert_kernel<IN, __nv_bfloat16><<<grid, 256, 0, c->stream>>>(src, c->N, d, c->xs, c->center, 0, (__nv_bfloat16*)c->X);
     return cudaGetLastError();
 }
 
@@ -287,6 +291,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     cudaMemset(c->derr, 0, sizeof(int));
     cudaMemset(c->counters, 0, sizeof(int) * 8);
     cudaMemset(c->p_logw, 0, sizeof(double) * S);
+    cudaMemset(c->dK, 0, sizeof(int));
     cudaMemset(c->center, 0, sizeof(double) * (2 * (size_t)d + (size_t)d * d));
     *out = c;
     return DPMM_OK;
@@ -299,7 +304,7 @@ void dpmm_destroy(dpmm_ctx* c) {
     void* ps[] = {c->dK, c->diter, c->age, c->counters, c->derr, c->stats, c->shift_new, c->shift_stats,
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
-                  c->relabel, c->center, c->tc_img};
+                  c->relabel, c->center, c->tc_img, c->tc_flag, c->dbg_scores};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
@@ -343,6 +348,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     } else {
         c->xdt = 1;
         c->xs = (d + 3) / 4 * 4;
+        if (c->prec == DPMM_PREC_TF32 && c->xs < 32) c->xs = 32;  // one 128-byte TMA box per row
     }
     const size_t esz = c->xdt == 0 ? 8 : (c->xdt == 1 ? 4 : 2);
     c->T_tiles = (int)((N + 255) / 256);
@@ -380,7 +386,6 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     CK(c, cudaStreamSynchronize(c->stream));
     c->initialized = false;
     c->h_iter = 0;
-    if (tc_supported(c) && (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16)) CK(c, tc_prepare(c));
     return DPMM_OK;
 }
 
@@ -593,6 +598,31 @@ dpmm_status dpmm_get_params(dpmm_ctx* c, double* logw, double* mu, double* W, do
     if (mu && !c->h_center.empty())
         for (size_t s = 0; s < S; ++s)
             for (int j = 0; j < d; ++j) mu[s * d + j] += c->h_center[j];
+    return check_derr(c);
+}
+
+dpmm_status dpmm_label_scores(dpmm_ctx* c, double* scores) {
+    if (!c || !scores) return DPMM_EINVAL;
+    if (!c->X || !c->initialized) return fail(c, DPMM_ESTATE, "no chain");
+    int K = 0;
+    CK(c, cudaMemcpyAsync(&K, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const size_t bytes = sizeof(double) * (size_t)c->N * K;
+    CK(c, cudaMalloc(&c->dbg_scores, bytes));
+    // the label kernel of this precision with the current parameters; the labels it
+    // draws are put back afterwards
+    int32_t* zkeep = nullptr;
+    CK(c, cudaMalloc(&zkeep, sizeof(int32_t) * c->N));
+    CK(c, cudaMemcpyAsync(zkeep, c->z, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    const bool tc = c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16;
+    cudaError_t e = tc ? launch_labels_tc(c, c->seed) : launch_labels_simt(c, c->seed);
+    CK(c, e);
+    CK(c, cudaMemcpyAsync(scores, c->dbg_scores, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(c->z, zkeep, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    cudaFree(zkeep);
+    cudaFree(c->dbg_scores);
+    c->dbg_scores = nullptr;
     return check_derr(c);
 }
 

@@ -13,6 +13,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 #include <vector>
@@ -100,6 +101,26 @@ __device__ inline double d_log_gamma(const Key& k, uint32_t c0, uint32_t tag, ui
         if (log(u) < 0.5 * x * x + dd - dd * v + dd * log(v)) return log(dd) + log(v) + boost;
     }
     return log(dd) + boost;
+}
+
+// Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits, ties away
+// from zero).  The tensor cores would otherwise truncate FP32 operands, which scales
+// every product by up to 1 - 2^-10 in the same direction.
+__host__ __device__ inline float round_tf32(float x) {
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(x);
+#else
+    uint32_t u;
+    memcpy(&u, &x, 4);
+#endif
+    if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x1000u) & 0xFFFFE000u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+#endif
 }
 
 // ---------------------------------------------------------------- statistics
@@ -206,7 +227,8 @@ struct dpmm_ctx {
     double* canon = nullptr; // canonical (n, xbar, C) per cluster and sub-cluster: 3 K_max x (1 + d + d d)
 
     // tensor-core path
-    void* tmap_x = nullptr;  // host copy of the CUtensorMap for X (128 bytes)
+    int* tc_flag = nullptr;        // device: 1 when K did not fit the tensor-core kernel
+    double* dbg_scores = nullptr;  // device N x K scores when the score hook is active
 
     // profiling: 0 off, 1 every kernel, 2 only the label kernel
     int profiling = 0;

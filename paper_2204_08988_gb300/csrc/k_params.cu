@@ -230,7 +230,7 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
 
 // FP32 mirrors of the drawn parameters for the reduced-precision paths, and the
 // shift the next statistics are accumulated with (the cluster's drawn mean).
-__global__ void derive_kernel(int kind, int d, const int* dK, const double* p_logw, const double* p_mu,
+__global__ void derive_kernel(int kind, int d, int tf32, const int* dK, const double* p_logw, const double* p_mu,
                               const double* p_W, const double* p_c, const double* p_logtheta, float* q_mu,
                               float* q_W, float* q_c, float* q_b, float* q_logtheta, double* shift_new,
                               float* shift32) {
@@ -244,8 +244,8 @@ __global__ void derive_kernel(int kind, int d, const int* dK, const double* p_lo
         for (int e = tid; e < d * d; e += nt) q_W[(size_t)s * d * d + e] = (float)W[e];
         for (int j = tid; j < d; j += nt) {
             q_mu[(size_t)s * d + j] = (float)mu[j];
-            double b = 0.0;  // b_j = sum_l mu_l W_lj
-            for (int l = 0; l <= j; ++l) b += mu[l] * W[l * d + j];
+            double b = 0.0;  // b_j = sum_l mu_l W_lj, with W as the tensor cores see it
+            for (int l = 0; l <= j; ++l) b += mu[l] * (tf32 ? (double)round_tf32((float)W[l * d + j]) : W[l * d + j]);
             q_b[(size_t)s * d + j] = (float)b;
             if (s % 3 == 0) {
                 shift_new[(size_t)(s / 3) * d + j] = (double)(float)mu[j];
@@ -294,7 +294,7 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
 
 cudaError_t launch_derive(dpmm_ctx* c) {
     prof_begin(c, "derive");
-    derive_kernel<<<3 * c->K_max, 128, 0, c->stream>>>(c->kind, c->d, c->dK, c->p_logw, c->p_mu, c->p_W, c->p_c,
+    derive_kernel<<<3 * c->K_max, 128, 0, c->stream>>>(c->kind, c->d, c->prec == DPMM_PREC_TF32, c->dK, c->p_logw, c->p_mu, c->p_W, c->p_c,
                                                        c->p_logtheta, c->q_mu, c->q_W, c->q_c, c->q_b,
                                                        c->q_logtheta, c->shift_new, c->shift32);
     prof_end(c, "derive");

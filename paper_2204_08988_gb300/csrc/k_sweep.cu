@@ -56,7 +56,9 @@ __device__ inline float gmax<float>() { return GUMBEL_MAX_F32; }
 template <typename T, typename XT>
 __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int xs, int64_t N, const XT* __restrict__ X,
                                                           ParamView<T> pv, const int* dK, const uint32_t* diter,
-                                                          uint64_t seed, int CB, int32_t* z) {
+                                                          uint64_t seed, int CB, const int* gate,
+                                                          double* scores, int32_t* z) {
+    if (gate && *gate == 0) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sW = (T*)smraw;
     const int per = kind == DPMM_PRIOR_NIW ? d * d + d + 1 : d + 1;
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
                 sc = Wk[d] + a;
             }
             const int k = k0 + cc;
+            if (scores) scores[i * K + k] = (double)sc;
             if (sc + gmax<T>() > best) {  // otherwise k cannot win the argmax
                 if ((k >> 1) != wblk) {
                     key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
@@ -427,7 +430,7 @@ template <>
 ParamView<float> pview<float>(dpmm_ctx* c) { return {c->q_W, c->q_mu, c->q_c, c->q_logtheta}; }
 
 template <typename T, typename XT>
-static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed) {
+static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed, const int* gate) {
     const int d = c->d;
     const size_t per = c->kind == DPMM_PRIOR_NIW ? (size_t)d * d + d + 1 : (size_t)d + 1;
     const size_t rows = (size_t)256 * (d + 1) * sizeof(T);
@@ -439,19 +442,23 @@ static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed) {
     if (ea != cudaSuccess) return ea;
     int grid = (int)((c->N + 255) / 256);
     labels_simt_kernel<T, XT><<<grid, 256, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c),
-                                                            c->dK, c->diter, seed, CB, c->z);
+                                                            c->dK, c->diter, seed, CB, gate, c->dbg_scores, c->z);
     return cudaGetLastError();
 }
 
-cudaError_t launch_labels_simt(dpmm_ctx* c, uint64_t seed) {
-    prof_begin(c, "labels_simt");
+cudaError_t launch_labels_simt_gated(dpmm_ctx* c, uint64_t seed, const int* gate) {
+    const char* name = gate ? "labels_simt_overflow" : "labels_simt";
+    prof_begin(c, name);
     cudaError_t e;
-    if (c->prec == DPMM_PREC_FP64_PLAIN) e = labels_simt_t<double, double>(c, seed);
-    else e = labels_simt_t<float, float>(c, seed);
-    prof_end(c, "labels_simt");
+    if (c->prec == DPMM_PREC_FP64_PLAIN) e = labels_simt_t<double, double>(c, seed, gate);
+    else if (c->xdt == 2) e = labels_simt_t<float, __nv_bfloat16>(c, seed, gate);
+    else e = labels_simt_t<float, float>(c, seed, gate);
+    prof_end(c, name);
     c->nlaunch += 1;
     return e;
 }
+
+cudaError_t launch_labels_simt(dpmm_ctx* c, uint64_t seed) { return launch_labels_simt_gated(c, seed, nullptr); }
 
 static cudaError_t sort_impl(dpmm_ctx* c, const int* gate) {
     prof_begin(c, "sort");

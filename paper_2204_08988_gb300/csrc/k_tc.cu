@@ -1,10 +1,517 @@
-// k_tc.cu -- tensor-core (tcgen05) label step for the reduced-precision paths.
+// k_tc.cu -- the cluster label step (Sec. 4.1 step (e), Eq. sample_labels) on the
+// 5th-generation tensor cores.
+//
+// The Gaussian log-likelihood of every point under every cluster is one stacked
+// contraction: with Lambda_k = W_k W_k^T (W_k upper-triangular), y_k = x W_k and
+// b_k = mu_k^T W_k, log N(x; mu_k, Lambda_k^-1) = c'_k - 1/2 ||y_k - b_k||^2.  So
+// Y = X [W_1 ... W_K] (N x d times d x Kd) runs as tcgen05.mma (TF32 operands,
+// FP32 accumulation in tensor memory), and the epilogue adds log pi_k and the
+// log-determinant (c_k), takes the squared norm of each d-wide block, and draws
+// z_i = argmax_k (s_ik + G_ik) by Gumbel-max with Philox (tag Z, block k/2, word
+// 0 or 2).  Gumbels are drawn only for clusters that can still win: a cluster whose
+// score plus the largest possible FP32 Gumbel is below the best perturbed score seen
+// so far is skipped, which leaves the argmax unchanged.
+//
+// CTA roles (320 threads, one CTA per SM, persistent over 128-point tiles):
+//   warp 0    : TMA producer (X tiles, 128 rows x 128 B, SWIZZLE_128B, 3 stages)
+//   warp 1    : TMEM allocation (512 columns) and the single-thread MMA issue
+//   warps 2-9 : epilogue, two warps per TMEM lane quarter, each taking every other
+//               cluster of a chunk; the two halves merge their argmax per point.
+// The factor image of all clusters is copied once into shared memory (pre-swizzled
+// by tc_prepare).  Accumulators are double-buffered in TMEM (2 x 256 columns).
+// Every mbarrier wait is bounded; on timeout the kernel records DPMM_ETIMEOUT,
+// drains its own copies and MMAs (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "dpmm_internal.cuh"
 
 namespace dpmm {
 
-bool tc_supported(const dpmm_ctx*) { return false; }
-cudaError_t tc_prepare(dpmm_ctx*) { return cudaSuccess; }
-cudaError_t launch_labels_tc(dpmm_ctx*, uint64_t) { return cudaErrorNotSupported; }
+namespace tc {
+
+constexpr int BM = 128;          // points per tile (MMA M)
+constexpr int XST = 3;           // X stages
+constexpr int XBYTES = BM * 128; // one X tile: 128 rows x 128 B
+constexpr int NTHREADS = 320;
+constexpr int EPI0 = 2;          // first epilogue warp
+constexpr int NEPI = 8;          // epilogue warps
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t SPIN = 1u << 22;  // bounded waits (a few seconds at most)
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+    for (uint32_t it = 0; it < SPIN; ++it) {
+        if (mbar_try(b, parity)) return true;
+        if ((it & 1023u) == 1023u && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            saddr(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     saddr(dst)),
+                 "l"((uint64_t)src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle layout:
+// 8-row groups of 128-byte rows, 1024 bytes apart (SBO); LBO unused (1); version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor: D FP32, A and B TF32 (kind::tf32, format 2) or BF16
+// (kind::f16, format 1), both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc(int n, int fmt) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (FMT == 2) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(id), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                tmem),
+            "l"(a), "l"(b), "r"(id), "r"(acc)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+struct Args {
+    int64_t N;
+    int d, dn;        // dimension and per-cluster column block (round_up(d, 8))
+    int NC;           // clusters per MMA chunk (NC * dn <= 256, multiple of 16)
+    int cap_rows;     // factor rows that fit in shared memory
+    int Kmax;
+    const int* dK;
+    const uint32_t* diter;
+    uint64_t seed;
+    const void* img;  // factor image: rows (k * dn + j) x 128 B, swizzled
+    const float* qb;  // b_k[j] = (mu_k^T W_k)_j, slot 3k
+    const float* qc;  // c_k, slot 3k
+    int32_t* z;
+    int* overflow;    // set to 1 when K does not fit (the CUDA-core kernel then runs)
+    int* derr;
+    double* scores;   // optional N x K scores (test hook), else null
+};
+
+// shared memory: [X stages | factor image | b table | c table | barriers]
+template <int FMT>
+__global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_constant__ CUtensorMap xmap, Args a) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char* xs = base;                                   // XST x XBYTES
+    unsigned char* bs = xs + XST * XBYTES;                      // cap_rows x 128
+    float* bt = (float*)(bs + (size_t)a.cap_rows * 128);        // Kmax x dn
+    float* ct = bt + (size_t)a.Kmax * a.dn;                     // Kmax
+    uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + a.Kmax) + 7) & ~(uintptr_t)7);
+    uint64_t* full = bars;            // XST
+    uint64_t* empty = full + XST;     // XST
+    uint64_t* tfull = empty + XST;    // 2
+    uint64_t* tempty = tfull + 2;     // 2
+    uint64_t* bload = tempty + 2;     // 1
+    uint64_t* mfull = bload + 1;      // 2: half 1 published its argmax
+    uint64_t* mempty = mfull + 2;     // 2: half 0 consumed it
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ float mbest[2][BM];
+    __shared__ int mz[2][BM];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = *a.dK;
+    const int rows = K * a.dn;
+    const int rows_pad = (rows + 15) / 16 * 16;
+    if (rows_pad > a.cap_rows) {  // does not fit: leave the step to the CUDA-core kernel
+        if (blockIdx.x == 0 && threadIdx.x == 0) *a.overflow = 1;
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.overflow = 0;
+    const int nch = (K + a.NC - 1) / a.NC;
+    const int64_t ntiles = (a.N + BM - 1) / BM;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < XST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], NEPI * 32);
+        }
+        mbar_init(bload, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&mfull[b], 4 * 32);
+            mbar_init(&mempty[b], 4 * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // b and c tables (zero beyond d)
+    for (int e = threadIdx.x; e < K * a.dn; e += blockDim.x) {
+        int k = e / a.dn, j = e % a.dn;
+        bt[e] = j < a.d ? a.qb[(size_t)3 * k * a.d + j] : 0.f;
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) ct[k] = a.qc[3 * k];
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int* abort = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // factor image, once
+            const uint32_t bbytes = (uint32_t)rows_pad * 128u;
+            mbar_expect_tx(bload, bbytes);
+            for (uint32_t off = 0; off < bbytes; off += 32768u) {
+                uint32_t n = min(32768u, bbytes - off);
+                bulk_load(bs + off, (const unsigned char*)a.img + off, n, bload);
+            }
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+                const int s = (int)(it % XST);
+                const uint32_t ph = (uint32_t)((it / XST) & 1);
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort)) { ok = false; break; }
+                mbar_expect_tx(&full[s], XBYTES);
+                tma_load_2d(xs + (size_t)s * XBYTES, &xmap, 0, (int)(t * BM), &full[s]);
+            }
+            if (!ok) {
+                atomicExch(a.derr, (int)DPMM_ETIMEOUT);
+                *abort = 1;
+            }
+            // own copies must land before the CTA may exit
+            mbar_wait(bload, 0, abort);
+            for (int64_t j = (it > XST ? it - XST : 0); j < it; ++j)
+                mbar_wait(&full[(int)(j % XST)], (uint32_t)((j / XST) & 1), abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(bload, 0, abort);
+            int64_t it = 0, ch = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+                const int s = (int)(it % XST);
+                if (!mbar_wait(&full[s], (uint32_t)((it / XST) & 1), abort)) { ok = false; break; }
+                fence_after();
+                const uint32_t xa = saddr(xs + (size_t)s * XBYTES);
+                for (int c = 0; c < nch; ++c, ++ch) {
+                    const int b = (int)(ch & 1);
+                    if (!mbar_wait(&tempty[b], (uint32_t)(((ch >> 1) & 1) ^ 1), abort)) { ok = false; break; }
+                    fence_after();
+                    const int nclus = min(a.NC, K - c * a.NC);
+                    const int n = (nclus * a.dn + 15) / 16 * 16;
+                    const uint32_t ba = saddr(bs + (size_t)c * a.NC * a.dn * 128);
+                    const uint32_t id = idesc(n, FMT);
+                    const int ksteps = 4;  // 128-byte rows in 32-byte MMA steps
+#pragma unroll
+                    for (int kk = 0; kk < ksteps; ++kk)
+                        mma<FMT>(tmem + (uint32_t)(b * 256), sdesc(xa + kk * 32), sdesc(ba + kk * 32), id, kk > 0);
+                    mma_commit(&tfull[b]);
+                }
+                if (!ok) break;
+                mma_commit(&empty[s]);
+            }
+            if (!ok) {
+                atomicExch(a.derr, (int)DPMM_ETIMEOUT);
+                *abort = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue: thread <-> TMEM lane (point row); two warps per lane quarter
+        const int ew = warp - EPI0;
+        const int quarter = warp & 3, half = ew >> 2;
+        const int r = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const uint32_t iter = *a.diter;
+        Key key{a.seed, iter, 0};
+        int64_t ch = 0, it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+            const int64_t i = t * BM + r;
+            float best = -INFINITY;
+            int zb = 0;
+            uint32_t w[4];
+            int wblk = -1;
+            for (int c = 0; c < nch; ++c, ++ch) {
+                const int b = (int)(ch & 1);
+                if (!mbar_wait(&tfull[b], (uint32_t)((ch >> 1) & 1), abort)) { ok = false; break; }
+                fence_after();
+                const int nclus = min(a.NC, K - c * a.NC);
+                for (int cc = half; cc < nclus; cc += 2) {
+                    const int k = c * a.NC + cc;
+                    const float* bk = bt + (size_t)k * a.dn;
+                    float q = 0.f;
+                    const uint32_t col = tmem + lane_off + (uint32_t)(b * 256 + cc * a.dn);
+                    if (a.dn == 32) {  // the loads never pass the block's own columns
+                        float y[32];
+                        tmem_ld32(col, y);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float tdiff = y[j] - bk[j];
+                            q = fmaf(tdiff, tdiff, q);
+                        }
+                    } else {
+                        for (int j0 = 0; j0 < a.dn; j0 += 8) {
+                            float y[8];
+                            tmem_ld8(col + (uint32_t)j0, y);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float tdiff = y[j] - bk[j0 + j];
+                                q = fmaf(tdiff, tdiff, q);
+                            }
+                        }
+                    }
+                    const float sc = ct[k] - 0.5f * q;
+                    if (a.scores && i < a.N) a.scores[i * K + k] = (double)sc;
+                    if (sc + GUMBEL_MAX_F32 > best) {
+                        if ((k >> 1) != wblk) {
+                            key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
+                            wblk = k >> 1;
+                        }
+                        const float u = u01_f32((k & 1) ? w[2] : w[0]);
+                        const float v = sc - __logf(-logf(u));
+                        if (v > best) {
+                            best = v;
+                            zb = k;
+                        }
+                    }
+                }
+                fence_before();
+                mbar_arrive(&tempty[b]);
+            }
+            if (!ok) break;
+            // merge the two halves: the larger perturbed score wins, the lower k on a tie
+            const int sl = (int)(it & 1);
+            const uint32_t use = (uint32_t)((it >> 1) & 1);
+            if (half == 1) {
+                if (!mbar_wait(&mempty[sl], use ^ 1u, abort)) { ok = false; break; }
+                mbest[sl][r] = best;
+                mz[sl][r] = zb;
+                mbar_arrive(&mfull[sl]);
+            } else {
+                if (!mbar_wait(&mfull[sl], use, abort)) { ok = false; break; }
+                const float ob = mbest[sl][r];
+                const int oz = mz[sl][r];
+                mbar_arrive(&mempty[sl]);
+                if (ob > best || (ob == best && oz < zb)) zb = oz;
+                if (i < a.N) a.z[i] = zb;
+            }
+        }
+        if (!ok) {
+            atomicExch(a.derr, (int)DPMM_ETIMEOUT);
+            *abort = 1;
+        }
+    }
+    // teardown: MMAs must be complete before TMEM is released.  On the normal path the
+    // epilogue has consumed every commit; after an abort, give in-flight MMAs time.
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (*abort && warp == 1) __nanosleep(1000000);
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                                 : "memory");
+}
+
+// factor image: row n = k * dn + j holds W_k[l][j], l = 0..31 (zero beyond d), in the
+// 128-byte swizzle pattern: 16-byte chunk c of row n sits at chunk c ^ (n & 7).
+__global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const float* qW, int rows_cap, float* img) {
+    const int K = *dK;
+    const int rows = (K * dn + 15) / 16 * 16;
+    const int64_t total = (int64_t)min(rows, rows_cap) * 32;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(e / 32), l = (int)(e % 32);
+        const int k = n / dn, j = n % dn;
+        float v = 0.f;
+        if (k < K && k < Kmax && j < d && l < d) v = round_tf32(qW[((size_t)3 * k * d + l) * d + j]);
+        const int chunk = (l >> 2) ^ (n & 7);
+        img[(size_t)n * 32 + chunk * 4 + (l & 3)] = v;
+    }
+}
+
+}  // namespace tc
+
+// -------------------------------------------------------------------------- host
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+struct TcCfg {
+    int dn, NC, cap_rows;
+    size_t smem;
+};
+
+static TcCfg tc_cfg(const dpmm_ctx* c) {
+    TcCfg q;
+    q.dn = (c->d + 7) / 8 * 8;
+    q.NC = 256 / q.dn;
+    while ((q.NC * q.dn) % 16) --q.NC;
+    const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)c->K_max * (q.dn + 1) * 4 + 32 * 8 + 64;
+    const size_t limit = 227 * 1024 - 2048;  // leave room for static shared memory
+    size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * 128;
+    size_t cap = std::min(want, limit - fixed);
+    q.cap_rows = (int)(cap / 128 / 16 * 16);
+    q.smem = fixed + (size_t)q.cap_rows * 128;
+    if (q.smem < 120 * 1024) q.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
+    return q;
+}
+
+bool tc_supported(const dpmm_ctx* c) {
+    // Gaussian, TF32 or BF16 storage, one 128-byte swizzle atom in the contraction dimension
+    return c->kind == DPMM_PRIOR_NIW && c->prec == DPMM_PREC_TF32 && c->d >= 1 && c->d <= 32 &&
+           get_encode() != nullptr;
+}
+
+cudaError_t tc_prepare(dpmm_ctx* c) {
+    if (c->prec != DPMM_PREC_TF32) return cudaSuccess;
+    TcCfg q = tc_cfg(c);
+    const size_t bytes = (size_t)q.cap_rows * 128;
+    if (!c->tc_img || c->tc_img_bytes < bytes) {
+        if (c->tc_img) cudaFree(c->tc_img);
+        c->tc_img = nullptr;
+        cudaError_t e = cudaMalloc(&c->tc_img, bytes);
+        if (e != cudaSuccess) return e;
+        c->tc_img_bytes = bytes;
+        cudaMemset(c->tc_img, 0, bytes);
+    }
+    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->q_W, q.cap_rows,
+                                                    (float*)c->tc_img);
+    c->nlaunch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_simt_gated(dpmm_ctx* c, uint64_t seed, const int* gate);
+
+cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
+    TcCfg q = tc_cfg(c);
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc || !c->tc_img) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t gdim[2] = {(cuuint64_t)c->xs, (cuuint64_t)c->N};
+    const cuuint64_t gstride[1] = {(cuuint64_t)c->xs * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)tc::BM};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->X, gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (!c->tc_flag) {
+        cudaError_t e = cudaMalloc(&c->tc_flag, sizeof(int));
+        if (e != cudaSuccess) return e;
+    }
+    tc::Args a;
+    a.N = c->N;
+    a.d = c->d;
+    a.dn = q.dn;
+    a.NC = q.NC;
+    a.cap_rows = q.cap_rows;
+    a.Kmax = c->K_max;
+    a.dK = c->dK;
+    a.diter = c->diter;
+    a.seed = seed;
+    a.img = c->tc_img;
+    a.qb = c->q_b;
+    a.qc = c->q_c;
+    a.z = c->z;
+    a.overflow = c->tc_flag;
+    a.derr = c->derr;
+    a.scores = c->dbg_scores;
+    cudaError_t e = cudaFuncSetAttribute(tc::labels_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)q.smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (c->N + tc::BM - 1) / tc::BM;
+    const int grid = (int)std::min<int64_t>(c->num_sms, ntiles);
+    prof_begin(c, "labels_tc");
+    tc::labels_tc_kernel<2><<<grid, tc::NTHREADS, q.smem, c->stream>>>(map, a);
+    prof_end(c, "labels_tc");
+    c->nlaunch += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // K beyond the shared-memory capacity: the CUDA-core kernel does the step
+    return launch_labels_simt_gated(c, seed, c->tc_flag);
+}
 
 }  // namespace dpmm
