@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override N (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="add a per-kernel time table from a separate profiled pass")
+    ap.add_argument("--init-truth", action="store_true",
+                    help="start the chain from the generating labels instead of a burn-in from K=1 (profiling runs)")
     return ap.parse_args()
 
 
@@ -187,6 +190,10 @@ def main():
     with torch.cuda.stream(stream):
         g.set_data(Xd)
     seed = 0
+    if a.init_truth:
+        K_true = int(y.max()) + 1
+        g.set_state(K_true, y, (np.arange(N) % 2).astype(np.uint8))
+        a.burnin = 0
     g.sweep(a.burnin, seed)
     K0 = g.K
     g.sweep(a.warmup, seed)
@@ -255,6 +262,15 @@ def main():
         roof["kernel_ms_avg"] = ms / max(launches, 1)
     gpu_launches = prof.get("all_kernels", (0, 0))[0]
 
+    breakdown = None
+    if a.breakdown:  # separate pass, events around every kernel (not the timed steps)
+        P.dpmm_profile(g.h, 1)
+        for s in range(a.steps):
+            g.sweep(1, seed)
+        bd = P.dpmm_get_profile(g.h)
+        P.dpmm_profile(g.h, 0)
+        breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in bd.items() if k != "all_kernels"}
+
     # end to end through the C ABI: pinned host X in, labels out, every step
     e2e = None
     if not a.no_e2e:
@@ -292,10 +308,12 @@ def main():
                "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": DTYPE[a.prec], "data": "synthetic",
                "config": {"workload": a.workload, "N": N, "d": d, "K_start": K0, "K_timed": Ks, "K_max": K_max,
-                          "prec": a.prec, "burnin_sweeps": a.burnin, "parallelism": "replicas" if world > 1 else "1gpu",
+                          "prec": a.prec, "burnin_sweeps": a.burnin, "init": "generating labels" if a.init_truth else "K=1", "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                "gpu_launches": gpu_launches, "step_ms": step_ms}
+        if breakdown is not None:
+            out["breakdown"] = breakdown
         print(json.dumps(out))
     g.close()
     if dist:

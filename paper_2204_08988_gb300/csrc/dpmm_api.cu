@@ -283,6 +283,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     A(&c->records, c->records_bytes);
     A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
     A(&c->relabel, sizeof(int) * 4 * K_max);
+    A(&c->acc, sizeof(int) * ((size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
     A(&c->center, sizeof(double) * (2 * (size_t)d + (size_t)d * d));
     if (!ok) {
         dpmm_destroy(c);
@@ -304,7 +305,7 @@ void dpmm_destroy(dpmm_ctx* c) {
     void* ps[] = {c->dK, c->diter, c->age, c->counters, c->derr, c->stats, c->shift_new, c->shift_stats,
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
-                  c->relabel, c->center, c->tc_img, c->tc_flag, c->dbg_scores};
+                  c->relabel, c->acc, c->center, c->tc_img, c->tc_flag, c->dbg_scores};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);

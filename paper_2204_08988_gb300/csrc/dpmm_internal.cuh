@@ -224,6 +224,7 @@ struct dpmm_ctx {
     // split/merge scratch
     double* Ltab = nullptr;  // 3 K_max + K_max (K_max - 1)/2 log marginals
     int* relabel = nullptr;  // 4 K_max
+    int* acc = nullptr;      // K_max + K_max (K_max - 1)/2 accept flags of the split/merge proposals
     double* canon = nullptr; // canonical (n, xbar, C) per cluster and sub-cluster: 3 K_max x (1 + d + d d)
 
     // tensor-core path

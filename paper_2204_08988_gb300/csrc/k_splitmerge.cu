@@ -168,12 +168,57 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     }
 }
 
+// Every split and merge ratio with its Philox uniform, in parallel: acc[k] for the
+// split of cluster k, acc[K_max + p] for merge pair p; 1 = accepted if proposed.
+// Indices in the Philox counters are those after removing emptied clusters.
+__global__ void hastings_kernel(SMArgs a, const double* Ltab, const uint32_t* diter, uint64_t seed, int labels_ran,
+                                int* acc) {
+    const int K = *a.dK;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npairs = K * (K - 1) / 2;
+    if (e >= K + npairs) return;
+    const int d = a.L.d;
+    Key key{seed, *diter, 0};
+    auto live = [&](int k) { return labels_ran ? smv(a, k, -1, d, d) > 0 : true; };
+    auto cid = [&](int k) {
+        int c = 0;
+        for (int q = 0; q < k; ++q) c += live(q);
+        return c;
+    };
+    const double la = log(a.alpha), al = a.alpha;
+    if (e < K) {
+        const int k = e;
+        const double nl = smv(a, k, 0, d, d), nr = smv(a, k, 1, d, d), nk = nl + nr;
+        int ok = 0;
+        if (live(k) && nl >= 1 && nr >= 1) {
+            const double lH = la + lgamma(nl) + Ltab[3 * k + 1] + lgamma(nr) + Ltab[3 * k + 2] - lgamma(nk) -
+                              Ltab[3 * k];
+            ok = log(d_uniform(key, (uint32_t)cid(k), TAG_SPLIT, 0)) < lH;
+        }
+        acc[k] = ok;
+    } else {
+        const int p = e - K;
+        int k1, k2;
+        pair_of(p, K, k1, k2);
+        int ok = 0;
+        if (live(k1) && live(k2)) {
+            const double n1 = smv(a, k1, -1, d, d), n2 = smv(a, k2, -1, d, d), nm = n1 + n2;
+            const double lH = lgamma(nm) - la - lgamma(n1) - lgamma(n2) + Ltab[3 * a.K_max + p] - Ltab[3 * k1] -
+                              Ltab[3 * k2] + lgamma(al) - lgamma(al + nm) + lgamma(0.5 * al + n1) +
+                              lgamma(0.5 * al + n2) - 2.0 * lgamma(0.5 * al);
+            ok = log(d_uniform(key, (uint32_t)cid(k1), TAG_MERGE, (uint32_t)cid(k2))) < lH;
+        }
+        acc[a.K_max + p] = ok;
+    }
+}
+
 struct DecArgs {
     SMArgs s;
     const double* Ltab;
     const uint32_t* diter;
     uint64_t seed;
     int burn_out, labels_ran, sm_enabled, init_mode;
+    const int* acc;    // hastings_kernel's accept flags
     int* age;          // K_max
     int* dK;
     int* relabel;      // 3 K_max: map_l, map_r, zmode
@@ -192,8 +237,6 @@ __global__ void decision_kernel(DecArgs a) {
     const int K = *a.s.dK;
     const int d = a.s.L.d;
     if (tid == 0) {
-        Key key{a.seed, *a.diter, 0};
-        const double la = log(a.s.alpha), al = a.s.alpha;
         int Kc = 0;
         for (int k = 0; k < K; ++k) {
             double nk = smv(a.s, k, -1, d, d);
@@ -208,12 +251,8 @@ __global__ void decision_kernel(DecArgs a) {
             int S = Kc;
             for (int k = 0; k < K; ++k) {
                 if (!live[k]) continue;
-                double nl = smv(a.s, k, 0, d, d), nr = smv(a.s, k, 1, d, d), nk = nl + nr;
-                if (a.age[k] < a.burn_out || nl < 1 || nr < 1) continue;
-                double lH = la + lgamma(nl) + a.Ltab[3 * k + 1] + lgamma(nr) + a.Ltab[3 * k + 2] - lgamma(nk) -
-                            a.Ltab[3 * k];
-                double u = d_uniform(key, (uint32_t)cid[k], TAG_SPLIT, 0);
-                if (log(u) < lH) {
+                if (a.age[k] < a.burn_out) continue;
+                if (a.acc[k]) {
                     if (S >= a.s.K_max) {
                         ++nrej;
                         continue;
@@ -226,13 +265,8 @@ __global__ void decision_kernel(DecArgs a) {
                 if (!live[k1] || split_to[k1] >= 0 || merged_into[k1] >= 0 || head[k1]) continue;
                 for (int k2 = k1 + 1; k2 < K; ++k2) {
                     if (!live[k2] || split_to[k2] >= 0 || merged_into[k2] >= 0 || head[k2]) continue;
-                    double n1 = smv(a.s, k1, -1, d, d), n2 = smv(a.s, k2, -1, d, d), nm = n1 + n2;
-                    int p = k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1);
-                    double lH = lgamma(nm) - la - lgamma(n1) - lgamma(n2) + a.Ltab[3 * a.s.K_max + p] -
-                                a.Ltab[3 * k1] - a.Ltab[3 * k2] + lgamma(al) - lgamma(al + nm) + lgamma(0.5 * al + n1) +
-                                lgamma(0.5 * al + n2) - 2.0 * lgamma(0.5 * al);
-                    double u = d_uniform(key, (uint32_t)cid[k1], TAG_MERGE, (uint32_t)cid[k2]);
-                    if (log(u) < lH) {
+                    const int p = k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1);
+                    if (a.acc[a.s.K_max + p]) {
                         merged_into[k2] = k1;
                         head[k1] = 1;
                         ++nmerge;
@@ -353,8 +387,17 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
         prof_end(c, "marginal");
         c->nlaunch += 1;
     }
+    if (sm_enabled) {
+        const int items = c->K_max + c->K_max * (c->K_max - 1) / 2;
+        prof_begin(c, "hastings");
+        hastings_kernel<<<(items + 127) / 128, 128, 0, c->stream>>>(s, c->Ltab, c->diter, seed, labels_ran ? 1 : 0,
+                                                                   c->acc);
+        prof_end(c, "hastings");
+        c->nlaunch += 1;
+    }
     DecArgs a;
     a.s = s;
+    a.acc = c->acc;
     a.Ltab = c->Ltab;
     a.diter = c->diter;
     a.seed = seed;

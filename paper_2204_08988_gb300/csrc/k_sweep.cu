@@ -387,6 +387,195 @@ __global__ void __launch_bounds__(MAXT) substats_kernel(SubArgs<T> a) {
     if (cur >= 0) flush(cur);
 }
 
+// FP32 variant for d <= DV (DV = 32 or 64): the sub-cluster parameters of the current
+// cluster run are staged in shared memory (factor transposed and zero-padded to
+// DV x DV, so row j holds W[l][j] for l <= j), the point's x - mu sits in registers,
+// and each sub-cluster score costs d(d+1)/2 FMAs fed by float4 broadcast loads.
+// Statistics: one 4x4 register block per worker thread and one accumulator set per
+// sub-cluster (the branch on h is uniform within a warp: a warp's lanes share the
+// point).  Dynamic shared memory: P x dp point rows, P ints (k), P + 2 ints (runs),
+// P bytes (h), then 2 DV x DV + 2 DV + 2 + d floats (staged parameters), then the
+// flush buffer G x nblk x 32 floats.
+template <int DV, typename XT>
+__global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
+    if (a.gate && *a.gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int d = a.d, dp = a.L.dp, P = a.P, G = a.G, nblk = a.L.nblk;
+    float* xs = (float*)smraw;
+    int* kq = (int*)(xs + (size_t)P * dp);
+    int* runs = kq + P;
+    int* nruns = runs + P + 1;
+    unsigned char* hq = (unsigned char*)(nruns + 1);
+    float* stg = (float*)(smraw + (((size_t)P * dp * 4 + (2 * P + 2) * sizeof(int) + P + 15) / 16) * 16);
+    float* WT0 = stg;                 // DV x DV
+    float* WT1 = WT0 + DV * DV;       // DV x DV
+    float* mu0 = WT1 + DV * DV;       // DV
+    float* mu1 = mu0 + DV;            // DV
+    float* cc = mu1 + DV;             // 2
+    float* shf = cc + 2;              // d (cluster shift)
+    float* red = (float*)(((uintptr_t)(shf + DV) + 15) & ~(uintptr_t)15);
+    __shared__ int staged;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int g = blockIdx.x;
+    const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
+    Key key{a.seed, *a.diter, 0};
+    const XT* X = (const XT*)a.X;
+    const bool worker = tid < nblk * G;
+    const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
+    int jb = 0, lb = 0;
+    a.L.blk_coords(myblk, jb, lb);
+    float acc0[16], acc1[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc0[e] = acc1[e] = 0.f;
+    int cur = -1;
+    if (tid == 0) staged = -1;
+
+    auto flush = [&](int k) {
+        __syncthreads();
+        if (worker) {
+            float* r = red + ((size_t)grp * nblk + myblk) * 32;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                r[e] = acc0[e];
+                r[16 + e] = acc1[e];
+            }
+        }
+        __syncthreads();
+        double* out = a.rec + (size_t)(g + k) * 2 * a.L.E;
+        for (int e = tid; e < nblk * 16; e += nt) {
+            int b = e >> 4, q = e & 15;
+            double s0 = 0.0, s1 = 0.0;
+            for (int gg = 0; gg < G; ++gg) {
+                s0 += (double)red[((size_t)gg * nblk + b) * 32 + q];
+                s1 += (double)red[((size_t)gg * nblk + b) * 32 + 16 + q];
+            }
+            out[b * 16 + q] = s0;
+            out[a.L.E + b * 16 + q] = s1;
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc0[e] = acc1[e] = 0.f;
+    };
+
+    for (int64_t base = p0; base < p1; base += P) {
+        const int np = (int)min((int64_t)P, p1 - base);
+        __syncthreads();
+        int i = 0;
+        float v[DV];
+        if (tid < np) {
+            i = a.idx[base + tid];
+            kq[tid] = a.z[i];
+#pragma unroll
+            for (int j = 0; j < DV; ++j) v[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : 0.f;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int n = 0;
+            for (int q = 0; q < np; ++q)
+                if (q == 0 || kq[q] != kq[q - 1]) runs[n++] = q;
+            runs[n] = np;
+            *nruns = n;
+        }
+        __syncthreads();
+        const int nr = *nruns;
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (k != staged) {  // uniform: stage this cluster's two sub-clusters
+                __syncthreads();
+                for (int e = tid; e < 2 * DV * DV; e += nt) {
+                    const int h = e / (DV * DV), jj = (e / DV) % DV, l = e % DV;
+                    const int s = 3 * k + 1 + h;
+                    stg[e] = (jj < d && l <= jj) ? a.pv.W[((size_t)s * d + l) * d + jj] : 0.f;
+                }
+                for (int e = tid; e < 2 * DV; e += nt) {
+                    const int h = e / DV, j = e % DV;
+                    mu0[e] = j < d ? a.pv.mu[(size_t)(3 * k + 1 + h) * d + j] : 0.f;
+                }
+                if (tid < 2) cc[tid] = a.pv.c[3 * k + 1 + tid];
+                for (int j = tid; j < d; j += nt) shf[j] = a.shift[(size_t)k * d + j];
+                __syncthreads();
+                if (tid == 0) staged = k;
+            }
+            if (tid >= qs && tid < qe) {
+                int h;
+                if (a.draw) {
+                    float sc[2];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const float* WT = hh ? WT1 : WT0;
+                        const float* mu = hh ? mu1 : mu0;
+                        float t[DV];
+#pragma unroll
+                        for (int l = 0; l < DV; ++l) t[l] = v[l] - mu[l];
+                        float q = 0.f;
+#pragma unroll
+                        for (int j = 0; j < DV; ++j) {
+                            if (j < d) {
+                                float y = 0.f;
+#pragma unroll
+                                for (int l4 = 0; l4 <= j / 4; ++l4) {
+                                    const float4 w = *(const float4*)(WT + j * DV + l4 * 4);
+                                    y = fmaf(w.x, t[l4 * 4], y);
+                                    y = fmaf(w.y, t[l4 * 4 + 1], y);
+                                    y = fmaf(w.z, t[l4 * 4 + 2], y);
+                                    y = fmaf(w.w, t[l4 * 4 + 3], y);
+                                }
+                                q = fmaf(y, y, q);
+                            }
+                        }
+                        sc[hh] = cc[hh] - 0.5f * q;
+                    }
+                    uint32_t w[4];
+                    key.block((uint32_t)i, TAG_ZBAR, 0, w);
+                    const float vl = sc[0] + gumbel_of<float>(w[0], w[1]);
+                    const float vr = sc[1] + gumbel_of<float>(w[2], w[3]);
+                    h = vr > vl ? 1 : 0;
+                    a.zbar[i] = (uint8_t)h;
+                } else {
+                    h = a.zbar[i];
+                }
+                float* xr = xs + (size_t)tid * dp;
+#pragma unroll
+                for (int j = 0; j < DV; ++j)
+                    if (j < d) xr[j] = v[j] - shf[j];
+                xr[d] = 1.f;
+                for (int j = d + 1; j < dp; ++j) xr[j] = 0.f;
+                hq[tid] = (unsigned char)h;
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (k != cur) {
+                if (cur >= 0) flush(cur);
+                cur = k;
+            }
+            if (worker) {
+                for (int q = qs + grp; q < qe; q += G) {
+                    const float* xr = xs + (size_t)q * dp;
+                    const float4 xj = *(const float4*)(xr + jb * 4);
+                    const float4 xl = *(const float4*)(xr + lb * 4);
+                    const float aj[4] = {xj.x, xj.y, xj.z, xj.w}, al[4] = {xl.x, xl.y, xl.z, xl.w};
+                    if (hq[q]) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int w2 = 0; w2 < 4; ++w2) acc1[u * 4 + w2] = fmaf(aj[u], al[w2], acc1[u * 4 + w2]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int w2 = 0; w2 < 4; ++w2) acc0[u * 4 + w2] = fmaf(aj[u], al[w2], acc0[u * 4 + w2]);
+                    }
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush(cur);
+}
+
 // stats[(2k + h) E + e] = sum over the CTAs g covering cluster k's run of rec[g + k]
 __global__ void combine_kernel(const double* rec, const int* starts, const int* dK, int64_t R, int E,
                                const double* shift_new, double* shift_stats, int d, const int* gate,
@@ -495,6 +684,21 @@ static SubCfg sub_cfg(const dpmm_ctx* c) {
     return q;
 }
 
+static SubCfg sub_cfg_f32(const dpmm_ctx* c, int DV) {
+    SubCfg q;
+    const StatLayout& L = c->st;
+    const size_t stage = ((size_t)2 * DV * DV + 2 * DV + 2 + DV + 4) * 4;
+    int P = (int)((64 * 1024) / ((size_t)L.dp * 4));
+    P = std::max(32, std::min(256, P / 32 * 32));
+    q.P = P;
+    q.BT = 256;
+    q.G = std::max(1, 256 / L.nblk);
+    size_t head = (size_t)P * L.dp * 4 + (2 * (size_t)P + 2) * sizeof(int) + P;
+    head = (head + 15) / 16 * 16;
+    q.smem = head + stage + 16 + (size_t)q.G * L.nblk * 32 * 4;
+    return q;
+}
+
 size_t substats_smem(const dpmm_ctx* c) {
     return c->prec == DPMM_PREC_FP64_PLAIN ? sub_cfg<double>(c).smem : sub_cfg<float>(c).smem;
 }
@@ -545,10 +749,46 @@ static cudaError_t combine_impl(dpmm_ctx* c, const int* gate) {
 
 cudaError_t launch_sort(dpmm_ctx* c) { return sort_impl(c, nullptr); }
 
+template <int DV, typename XT>
+static cudaError_t substats_f32_t(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
+    SubCfg q = sub_cfg_f32(c, DV);
+    SubArgs<float> a;
+    a.kind = c->kind;
+    a.d = c->d;
+    a.xs = c->xs;
+    a.N = c->N;
+    a.X = c->X;
+    a.pv = pview<float>(c);
+    a.shift = c->shift32;
+    a.z = c->z;
+    a.zbar = c->zbar;
+    a.idx = c->idx;
+    a.dK = c->dK;
+    a.diter = c->diter;
+    a.gate = gate;
+    a.seed = seed;
+    a.draw = draw;
+    a.P = q.P;
+    a.G = q.G;
+    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.L = c->st;
+    a.rec = c->records;
+    cudaError_t ea = cudaFuncSetAttribute(substats_f32_kernel<DV, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)q.smem);
+    if (ea != cudaSuccess) return ea;
+    substats_f32_kernel<DV, XT><<<c->G2, q.BT, q.smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
 static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
     prof_begin(c, draw ? "substats" : "restats");
     cudaError_t e;
-    if (c->prec == DPMM_PREC_FP64_PLAIN) e = substats_t<double, double>(c, seed, draw, gate);
+    const bool fast = c->prec != DPMM_PREC_FP64_PLAIN && c->kind == DPMM_PRIOR_NIW && c->d <= 64 && c->st.nblk <= 256;
+    if (fast && c->d <= 32) e = c->xdt == 2 ? substats_f32_t<32, __nv_bfloat16>(c, seed, draw, gate)
+                                             : substats_f32_t<32, float>(c, seed, draw, gate);
+    else if (fast) e = c->xdt == 2 ? substats_f32_t<64, __nv_bfloat16>(c, seed, draw, gate)
+                                   : substats_f32_t<64, float>(c, seed, draw, gate);
+    else if (c->prec == DPMM_PREC_FP64_PLAIN) e = substats_t<double, double>(c, seed, draw, gate);
     else if (c->xdt == 2) e = substats_t<float, __nv_bfloat16>(c, seed, draw, gate);
     else e = substats_t<float, float>(c, seed, draw, gate);
     prof_end(c, draw ? "substats" : "restats");
