@@ -201,6 +201,11 @@ static void free_data(dpmm_ctx* c) {
     c->X = nullptr; c->z = nullptr; c->zbar = nullptr; c->idx = nullptr; c->hist = nullptr;
 }
 
+static void drop_graph(dpmm_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
 // ------------------------------------------------------------------ ABI
 extern "C" {
 
@@ -309,11 +314,13 @@ void dpmm_destroy(dpmm_ctx* c) {
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
+    drop_graph(c);
     delete c;
 }
 
 dpmm_status dpmm_set_options(dpmm_ctx* c, dpmm_prec prec, int init_K, int burn_out, void* stream) {
     if (!c) return DPMM_EINVAL;
+    drop_graph(c);
     if (prec < DPMM_PREC_FP64_PLAIN || prec > DPMM_PREC_FP32) return fail(c, DPMM_EINVAL, "unknown precision");
     if (init_K < 1 || init_K > c->K_max) return fail(c, DPMM_EINVAL, "init_K must be in [1, K_max]");
     if (burn_out < 0) return fail(c, DPMM_EINVAL, "burn_out must be >= 0");
@@ -332,6 +339,7 @@ dpmm_status dpmm_set_options(dpmm_ctx* c, dpmm_prec prec, int init_K, int burn_o
 
 dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, int on_device) {
     if (!c) return DPMM_EINVAL;
+    drop_graph(c);
     if (!X || N < 1 || N > 0x7FFFFFFFLL) return fail(c, DPMM_EINVAL, "need 1 <= N < 2^31 and a non-NULL X");
     if (dt < DPMM_F64 || dt > DPMM_I32) return fail(c, DPMM_EINVAL, "unknown dtype");
     if (c->kind == DPMM_PRIOR_NIW && dt == DPMM_I32) return fail(c, DPMM_EINVAL, "Gaussian data must be floating point");
@@ -414,6 +422,27 @@ static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
     return DPMM_OK;
 }
 
+// the kernels of one sweep, in order, on the context's stream
+static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
+    const bool tc = (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16);
+    cudaError_t e = cudaSuccess;
+    if (c->step_mask & 1u) {
+        if ((e = launch_weights(c, seed)) != cudaSuccess) return e;
+        if ((e = launch_params(c, seed)) != cudaSuccess) return e;
+        if ((e = launch_derive(c)) != cudaSuccess) return e;
+    }
+    if (c->step_mask & 2u) {
+        if ((e = tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed)) != cudaSuccess) return e;
+        if ((e = launch_sort(c)) != cudaSuccess) return e;
+        if ((e = launch_substats(c, seed, 1)) != cudaSuccess) return e;
+        if ((e = launch_combine(c)) != cudaSuccess) return e;
+    }
+    if ((e = launch_splitmerge(c, seed, (c->step_mask & 2u) ? 1 : 0, (c->step_mask & 4u) ? 1 : 0)) != cudaSuccess)
+        return e;
+    if ((e = launch_relabel(c, seed)) != cudaSuccess) return e;
+    return launch_advance(c);
+}
+
 dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
     if (!c) return DPMM_EINVAL;
     if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
@@ -422,22 +451,34 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
         dpmm_status s = init_chain(c, seed);
         if (s != DPMM_OK) return s;
     }
-    const bool tc = (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16);
+    // the first sweep runs eagerly (it allocates what the kernels need); later ones
+    // replay a graph of the same launches, captured once per (seed, mask)
+    const bool graphs = c->use_graph && !c->profiling && c->stream != nullptr;
     for (int it = 0; it < iters; ++it) {
-        if (c->step_mask & 1u) {
-            CK(c, launch_weights(c, seed));
-            CK(c, launch_params(c, seed));
-            CK(c, launch_derive(c));
+        if (graphs && c->graph && c->graph_seed == seed && c->graph_mask == c->step_mask) {
+            CK(c, cudaGraphLaunch(c->graph, c->stream));
+            continue;
         }
-        if (c->step_mask & 2u) {
-            CK(c, tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed));
-            CK(c, launch_sort(c));
-            CK(c, launch_substats(c, seed, 1));
-            CK(c, launch_combine(c));
+        CK(c, enqueue_sweep(c, seed));
+        if (graphs) {  // every buffer exists after the eager sweep: capture allocates nothing
+            drop_graph(c);
+            cudaGraph_t g = nullptr;
+            CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_sweep(c, seed);
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+            if (e == cudaSuccess && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&c->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                c->graph = nullptr;
+                c->use_graph = false;  // run eagerly from now on
+                cudaGetLastError();
+                CK(c, e);
+            } else {
+                c->graph_seed = seed;
+                c->graph_mask = c->step_mask;
+                // the eager sweep above was sweep `it`; the captured one has not run yet
+            }
         }
-        CK(c, launch_splitmerge(c, seed, (c->step_mask & 2u) ? 1 : 0, (c->step_mask & 4u) ? 1 : 0));
-        CK(c, launch_relabel(c, seed));
-        CK(c, launch_advance(c));
     }
     c->seed = seed;
     return DPMM_OK;
@@ -540,6 +581,7 @@ dpmm_status dpmm_set_state(dpmm_ctx* c, int K, const int32_t* z, const uint8_t* 
 
 dpmm_status dpmm_set_step_mask(dpmm_ctx* c, unsigned mask) {
     if (!c) return DPMM_EINVAL;
+    drop_graph(c);
     if (mask > 7) return fail(c, DPMM_EINVAL, "mask has 3 bits");
     c->step_mask = mask;
     return DPMM_OK;
@@ -629,6 +671,7 @@ dpmm_status dpmm_label_scores(dpmm_ctx* c, double* scores) {
 
 dpmm_status dpmm_profile(dpmm_ctx* c, int enable) {
     if (!c) return DPMM_EINVAL;
+    drop_graph(c);
     CK(c, cudaStreamSynchronize(c->stream));
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);

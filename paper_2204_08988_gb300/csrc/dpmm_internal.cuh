@@ -231,6 +231,13 @@ struct dpmm_ctx {
     int* tc_flag = nullptr;        // device: 1 when K did not fit the tensor-core kernel
     double* dbg_scores = nullptr;  // device N x K scores when the score hook is active
 
+    // one sweep captured as a CUDA graph (kernels read K and the sweep index from
+    // device memory, so the graph is reused until the seed, mask or data change)
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_seed = 0;
+    unsigned graph_mask = 0;
+    bool use_graph = true;
+
     // profiling: 0 off, 1 every kernel, 2 only the label kernel
     int profiling = 0;
     int64_t nlaunch = 0;  // kernels launched since the last dpmm_profile call

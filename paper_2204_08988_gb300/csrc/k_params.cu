@@ -45,38 +45,40 @@ __device__ inline double block_reduce_sum(double v, double* sh) {
 }
 
 // (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2).
-__global__ void __launch_bounds__(256) weights_kernel(StatView sv, const int* dK, const uint32_t* diter, uint64_t seed, double alpha,
-                               double* logw, double* cweights) {
+// All 3K + 1 Gamma draws in one parallel phase (draw t: t < K weight k = t, t = K the
+// leftover mass, then sub-weights (k, h) at t = K + 1 + 2k + h), then the two
+// normalisations.  Dynamic shared memory: 3 K_max + 1 doubles.
+__global__ void __launch_bounds__(1024) weights_kernel(StatView sv, const int* dK, const uint32_t* diter,
+                                                       uint64_t seed, double alpha, double* logw,
+                                                       double* cweights) {
+    extern __shared__ double lgs[];
     __shared__ double sh[32];
     const int K = *dK;
     Key key{seed, *diter, 0};
-    double lmax = -INFINITY;
-    // each thread keeps at most 4 draws: K + 1 <= 1001 <= 4 * 256
-    double lg[4];
-    int cnt = 0;
-    for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) {
-        double v = (k < K) ? d_log_gamma(key, (uint32_t)k, TAG_WEIGHT, 0, sv.count(k, -1))
-                           : d_log_gamma(key, 0xFFFFFFFFu, TAG_WEIGHT, 0, alpha);
-        lg[cnt] = v;
-        lmax = fmax(lmax, v);
+    const int T = 3 * K + 1;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        double v;
+        if (t < K) v = d_log_gamma(key, (uint32_t)t, TAG_WEIGHT, 0, sv.count(t, -1));
+        else if (t == K) v = d_log_gamma(key, 0xFFFFFFFFu, TAG_WEIGHT, 0, alpha);
+        else {
+            const int k = (t - K - 1) >> 1, h = (t - K - 1) & 1;
+            v = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 64u * h, sv.count(k, h) + 0.5 * alpha);
+        }
+        lgs[t] = v;
     }
+    __syncthreads();
+    double lmax = -INFINITY;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) lmax = fmax(lmax, lgs[k]);
     lmax = block_reduce_max(lmax, sh);
     double s = 0.0;
-    cnt = 0;
-    for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) s += exp(lg[cnt] - lmax);
-    double lse = lmax + log(block_reduce_sum(s, sh));
-    cnt = 0;
-    for (int k = threadIdx.x; k <= K; k += blockDim.x, ++cnt) {
-        if (k < K) {
-            logw[3 * k] = lg[cnt] - lse;
-            cweights[k] = exp(lg[cnt] - lse);
-        }
-    }
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) s += exp(lgs[k] - lmax);
+    const double lse = lmax + log(block_reduce_sum(s, sh));
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double gl = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 0, sv.count(k, 0) + 0.5 * alpha);
-        double gr = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 64, sv.count(k, 1) + 0.5 * alpha);
-        double m = fmax(gl, gr);
-        double l2 = m + log(exp(gl - m) + exp(gr - m));
+        logw[3 * k] = lgs[k] - lse;
+        cweights[k] = exp(lgs[k] - lse);
+        const double gl = lgs[K + 1 + 2 * k], gr = lgs[K + 2 + 2 * k];
+        const double m = fmax(gl, gr);
+        const double l2 = m + log(exp(gl - m) + exp(gr - m));
         logw[3 * k + 1] = gl - l2;
         logw[3 * k + 2] = gr - l2;
     }
@@ -160,39 +162,70 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         __syncthreads();
     }
     // Bartlett diagonal (chi^2 via Gamma)
+    const uint32_t NB = 64u * d;
+    double* W = p_W + (size_t)s * d * d;
     for (int j = tid; j < d; j += nt) {
         double df = nun - d + (j + 1);
         double lg = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, 0.5 * df);
         Bd[j] = sqrt(2.0 * exp(lg));
-        acc[j] = 0.0;
+    }
+    // every normal of the slot, one Box-Muller per pair: normal q = r*d + c (r < c) goes
+    // to W[r][c], where the back substitution of column c reads it before overwriting
+    // it; normal d*d + j (the mean's eps_j) goes to acc[j]; W below the diagonal is 0
+    const int npair = (d * d + d + 1) / 2;
+    for (int pq = tid; pq < npair; pq += nt) {
+        uint32_t w[4];
+        key.block((uint32_t)s, TAG_PARAM, NB + (uint32_t)pq, w);
+        const double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
+        const double rr = sqrt(-2.0 * log(u1)), ang = 6.283185307179586 * u2;
+        for (int o = 0; o < 2; ++o) {
+            const int q = 2 * pq + o;
+            const double nv = o ? rr * sin(ang) : rr * cos(ang);
+            if (q < d * d) {
+                const int r = q / d, cidx = q % d;
+                W[q] = r < cidx ? nv : 0.0;
+            } else if (q < d * d + d) {
+                acc[q - d * d] = nv;
+            }
+        }
     }
     __syncthreads();
-    const uint32_t NB = 64u * d;
-    double* W = p_W + (size_t)s * d * d;
     // W = U^-T B, column c by back substitution (U^T upper-triangular)
     for (int c = tid; c < d; c += nt) {
-        for (int r = d - 1; r > c; --r) W[r * d + c] = 0.0;
         for (int r = c; r >= 0; --r) {
-            double b = (r == c) ? Bd[c] : d_normal(key, (uint32_t)s, TAG_PARAM, NB, (uint32_t)(r * d + c));
-            double t = b;
+            double t = (r == c) ? Bd[c] : W[r * d + c];
             for (int m = r + 1; m <= c; ++m) t -= A[m * d + r] * W[m * d + c];
             W[r * d + c] = t / A[r * d + r];
         }
     }
     __syncthreads();
-    // W^T v = eps (forward substitution), mu = m_n + v / sqrt(kappa_n)
+    // W^T v = eps (forward substitution) by warp 0, lane m keeps sum_{j<m} W[j][m] v_j;
+    // mu = m_n + v / sqrt(kappa_n)
     double* mu = p_mu + (size_t)s * d;
-    for (int j = 0; j < d; ++j) {
-        if (tid == 0) {
-            double e = d_normal(key, (uint32_t)s, TAG_PARAM, NB, (uint32_t)(d * d + j));
-            double v = (e - acc[j]) / W[j * d + j];
-            Bd[j] = v;  // reuse as v
+    if (tid < 32) {
+        double am[8];  // m = tid + 32 i, d <= 256
+#pragma unroll
+        for (int i = 0; i < 8; ++i) am[i] = 0.0;
+        for (int j = 0; j < d; ++j) {
+            const int own = j & 31, slot = j >> 5;
+            double mine = 0.0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i == slot) mine = am[i];
+            double vj = 0.0;
+            if (tid == own) {
+                vj = (acc[j] - mine) / W[j * d + j];
+                Bd[j] = vj;  // reuse as v
+            }
+            vj = __shfl_sync(0xffffffffu, vj, own);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int m = tid + 32 * i;
+                if (m > j && m < d) am[i] += W[j * d + m] * vj;
+            }
         }
-        __syncthreads();
-        double v = Bd[j];
-        for (int m = j + 1 + tid; m < d; m += nt) acc[m] += W[j * d + m] * v;
-        __syncthreads();
     }
+    __syncthreads();
     for (int j = tid; j < d; j += nt) mu[j] = mn[j] + Bd[j] / sqrt(kn);
     double ld = 0.0;
     for (int j = tid; j < d; j += nt) ld += log(W[j * d + j]);
@@ -262,7 +295,8 @@ static StatView make_sv(dpmm_ctx* c) { return StatView{c->stats, c->st}; }
 
 cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
     prof_begin(c, "weights");
-    weights_kernel<<<1, 256, 0, c->stream>>>(make_sv(c), c->dK, c->diter, seed, c->alpha, c->p_logw, c->cweights);
+    weights_kernel<<<1, 1024, sizeof(double) * (3 * c->K_max + 1), c->stream>>>(make_sv(c), c->dK, c->diter, seed,
+                                                                               c->alpha, c->p_logw, c->cweights);
     prof_end(c, "weights");
     c->nlaunch += 1;
     return cudaGetLastError();

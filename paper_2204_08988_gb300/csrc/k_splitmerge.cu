@@ -154,17 +154,17 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         }
         __syncthreads();
     }
-    double ld = 0.0;
-    for (int j = tid; j < d; j += nt) ld += log(A[j * d + j]);
-    for (int o = 16; o > 0; o >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, o);
-    if ((tid & 31) == 0) sh[tid >> 5] = ld;
+    // -(nun/2) log|Psi_n| and the multivariate-lgamma ratio, summed over j by all threads
+    double part = 0.0;
+    for (int j = tid; j < d; j += nt)
+        part += -nun * log(A[j * d + j]) + lgamma(0.5 * nun - 0.5 * j) - lgamma(0.5 * a.nu0 - 0.5 * j);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) sh[tid >> 5] = part;
     __syncthreads();
     if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < (nt + 31) / 32; ++w) s += sh[w];
-        double ldn = 2.0 * s;
-        *out = -0.5 * n * d * log(M_PI) + lmvgamma(0.5 * nun, d) - lmvgamma(0.5 * a.nu0, d) +
-               0.5 * a.nu0 * a.logdet_psi0 - 0.5 * nun * ldn + 0.5 * d * (log(a.kappa0) - log(kn));
+        *out = -0.5 * n * d * log(M_PI) + s + 0.5 * a.nu0 * a.logdet_psi0 + 0.5 * d * (log(a.kappa0) - log(kn));
     }
 }
 
@@ -229,17 +229,33 @@ struct DecArgs {
 
 #define DEC_KMAX 1024
 
-__global__ void decision_kernel(DecArgs a) {
+// Dynamic shared memory: the accept flags (one byte per proposal) when they fit in
+// dyn_flags bytes, so that the sequential walk reads shared memory only.
+__global__ void decision_kernel(DecArgs a, int dyn_flags) {
     __shared__ int live[DEC_KMAX], cid[DEC_KMAX], split_to[DEC_KMAX], merged_into[DEC_KMAX], head[DEC_KMAX];
     __shared__ int newid[DEC_KMAX], newid_split[DEC_KMAX], src[DEC_KMAX], nage[DEC_KMAX];
     __shared__ int s_K, s_Knew;
+    __shared__ double cnt[DEC_KMAX];
+    extern __shared__ unsigned char flg[];
     const int tid = threadIdx.x;
     const int K = *a.s.dK;
     const int d = a.s.L.d;
+    const int nflags = K + K * (K - 1) / 2;
+    const bool staged = a.sm_enabled && nflags <= dyn_flags;
+    for (int k = tid; k < K; k += blockDim.x) {
+        cnt[k] = smv(a.s, k, -1, d, d);
+        nage[k] = a.age[k];
+    }
+    if (staged) {
+        for (int q = tid; q < nflags; q += blockDim.x) flg[q] = (unsigned char)(q < K ? a.acc[q] : a.acc[a.s.K_max + q - K]);
+    }
+    __syncthreads();
+    auto acc_split = [&](int k) { return staged ? (int)flg[k] : a.acc[k]; };
+    auto acc_merge = [&](int p) { return staged ? (int)flg[K + p] : a.acc[a.s.K_max + p]; };
     if (tid == 0) {
         int Kc = 0;
         for (int k = 0; k < K; ++k) {
-            double nk = smv(a.s, k, -1, d, d);
+            double nk = cnt[k];
             live[k] = a.labels_ran ? (nk > 0) : 1;
             cid[k] = live[k] ? Kc++ : -1;
             split_to[k] = -1;
@@ -251,8 +267,8 @@ __global__ void decision_kernel(DecArgs a) {
             int S = Kc;
             for (int k = 0; k < K; ++k) {
                 if (!live[k]) continue;
-                if (a.age[k] < a.burn_out) continue;
-                if (a.acc[k]) {
+                if (nage[k] < a.burn_out) continue;
+                if (acc_split(k)) {
                     if (S >= a.s.K_max) {
                         ++nrej;
                         continue;
@@ -266,7 +282,7 @@ __global__ void decision_kernel(DecArgs a) {
                 for (int k2 = k1 + 1; k2 < K; ++k2) {
                     if (!live[k2] || split_to[k2] >= 0 || merged_into[k2] >= 0 || head[k2]) continue;
                     const int p = k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1);
-                    if (a.acc[a.s.K_max + p]) {
+                    if (acc_merge(p)) {
                         merged_into[k2] = k1;
                         head[k1] = 1;
                         ++nmerge;
@@ -275,12 +291,12 @@ __global__ void decision_kernel(DecArgs a) {
                 }
             }
         }
+        // nage holds the old ages; the new ones go to cid (free after the proposals)
         int nid = 0;
         for (int k = 0; k < K; ++k)
             if (live[k] && merged_into[k] < 0) {
                 newid[k] = nid;
                 src[nid] = k;
-                nage[nid] = (split_to[k] >= 0 || head[k]) ? 0 : a.age[k] + (a.init_mode ? 0 : 1);
                 ++nid;
             } else {
                 newid[k] = -1;
@@ -289,9 +305,14 @@ __global__ void decision_kernel(DecArgs a) {
             if (split_to[k] >= 0) {
                 newid_split[k] = nid;
                 src[nid] = k;
-                nage[nid] = 0;
                 ++nid;
             }
+        // ages: survivors one sweep older, clusters created by a split or merge start at 0
+        for (int q = 0; q < nid; ++q) {
+            const int k = src[q];
+            const bool fresh = split_to[k] >= 0 || head[k];  // both halves of a split, and a merge
+            cid[q] = fresh ? 0 : nage[k] + (a.init_mode ? 0 : 1);
+        }
         int* map_l = a.relabel;
         int* map_r = a.relabel + a.s.K_max;
         int* zmode = a.relabel + 2 * a.s.K_max;
@@ -330,7 +351,7 @@ __global__ void decision_kernel(DecArgs a) {
         a.shift_new[(size_t)k * d + j] = v;
         a.shift32[(size_t)k * d + j] = (float)v;
     }
-    for (int k = tid; k < Kn; k += blockDim.x) a.age[k] = nage[k];
+    for (int k = tid; k < Kn; k += blockDim.x) a.age[k] = cid[k];
     __syncthreads();
     if (tid == 0) *a.dK = Kn;
 }
@@ -413,7 +434,10 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     a.shift_new = c->shift_new;
     a.shift32 = c->shift32;
     prof_begin(c, "decision");
-    decision_kernel<<<1, 256, 0, c->stream>>>(a);
+    const int dyn = 32 * 1024;
+    cudaError_t ea = cudaFuncSetAttribute(decision_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (ea != cudaSuccess) return ea;
+    decision_kernel<<<1, 256, dyn, c->stream>>>(a, dyn);
     prof_end(c, "decision");
     c->nlaunch += 1;
     return cudaGetLastError();

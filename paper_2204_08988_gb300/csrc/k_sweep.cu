@@ -53,7 +53,7 @@ __device__ inline float gmax<float>() { return GUMBEL_MAX_F32; }
 
 // ------------------------------------------------------------------ labels (simt)
 // Dynamic shared memory: CB clusters x (d*d + d + 1) T, then 256 x (d + 1) T rows.
-template <typename T, typename XT>
+template <typename T, typename XT, bool SCORES>
 __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int xs, int64_t N, const XT* __restrict__ X,
                                                           ParamView<T> pv, const int* dK, const uint32_t* diter,
                                                           uint64_t seed, int CB, const int* gate,
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
                 sc = Wk[d] + a;
             }
             const int k = k0 + cc;
-            if (scores) scores[i * K + k] = (double)sc;
+            if constexpr (SCORES) scores[i * K + k] = (double)sc;
             if (sc + gmax<T>() > best) {  // otherwise k cannot win the argmax
                 if ((k >> 1) != wblk) {
                     key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
@@ -221,6 +221,28 @@ __global__ void scatter_kernel(const int32_t* z, int64_t N, int T_tiles, const i
 }
 
 // ------------------------------------------------------------------ sub-labels + stats
+// Starts of the runs of equal labels among kq[0..np) (np <= blockDim), by warp ballots:
+// runs[0..n) are the starts, runs[n] = np, *nruns = n.  All threads must call it.
+__device__ inline void find_runs(const int* kq, int np, int* runs, int* nruns, int* wcnt) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = (blockDim.x + 31) >> 5;
+    const bool f = tid < np && (tid == 0 || kq[tid] != kq[tid - 1]);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcnt[w] = __popc(m);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int v = 0; v < nw; ++v) {
+        if (v < w) before += wcnt[v];
+        total += wcnt[v];
+    }
+    if (f) runs[before + __popc(m & ((1u << lane) - 1u))] = tid;
+    if (tid == 0) {
+        runs[total] = np;
+        *nruns = total;
+    }
+    __syncthreads();
+}
+
+
 template <typename T>
 struct SubArgs {
     int kind, d, xs;
@@ -346,14 +368,10 @@ __global__ void __launch_bounds__(MAXT) substats_kernel(SubArgs<T> a) {
             hq[tid] = (unsigned char)h;
         }
         __syncthreads();
-        if (tid == 0) {  // run starts of equal clusters in this tile
-            int n = 0;
-            for (int q = 0; q < np; ++q)
-                if (q == 0 || kq[q] != kq[q - 1]) runs[n++] = q;
-            runs[n] = np;
-            *nruns = n;
+        {
+            __shared__ int wcnt[32];
+            find_runs(kq, np, runs, nruns, wcnt);
         }
-        __syncthreads();
         const int nr = *nruns;
         for (int r = 0; r < nr; ++r) {
             const int qs = runs[r], qe = runs[r + 1];
@@ -465,18 +483,29 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
         if (tid < np) {
             i = a.idx[base + tid];
             kq[tid] = a.z[i];
+            if constexpr (sizeof(XT) == 4) {  // rows are 16-byte aligned (stride a multiple of 4 floats)
+                const float4* xr4 = (const float4*)(X + (int64_t)i * a.xs);
 #pragma unroll
-            for (int j = 0; j < DV; ++j) v[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : 0.f;
+                for (int j4 = 0; j4 < DV / 4; ++j4) {
+                    const float4 q = j4 * 4 < d ? xr4[j4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[4 * j4] = q.x;
+                    v[4 * j4 + 1] = q.y;
+                    v[4 * j4 + 2] = q.z;
+                    v[4 * j4 + 3] = q.w;
+                }
+#pragma unroll
+                for (int j = 0; j < DV; ++j)
+                    if (j >= d) v[j] = 0.f;
+            } else {
+#pragma unroll
+                for (int j = 0; j < DV; ++j) v[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : 0.f;
+            }
         }
         __syncthreads();
-        if (tid == 0) {
-            int n = 0;
-            for (int q = 0; q < np; ++q)
-                if (q == 0 || kq[q] != kq[q - 1]) runs[n++] = q;
-            runs[n] = np;
-            *nruns = n;
+        {
+            __shared__ int wcnt2[32];
+            find_runs(kq, np, runs, nruns, wcnt2);
         }
-        __syncthreads();
         const int nr = *nruns;
         for (int r = 0; r < nr; ++r) {
             const int qs = runs[r], qe = runs[r + 1];
@@ -535,12 +564,21 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
                 } else {
                     h = a.zbar[i];
                 }
-                float* xr = xs + (size_t)tid * dp;
+                // the centred row, then 1, then zeros, as float4 stores (conflict-free at any
+                // row stride that is a multiple of 4 floats)
+                float4* xr4 = (float4*)(xs + (size_t)tid * dp);
 #pragma unroll
-                for (int j = 0; j < DV; ++j)
-                    if (j < d) xr[j] = v[j] - shf[j];
-                xr[d] = 1.f;
-                for (int j = d + 1; j < dp; ++j) xr[j] = 0.f;
+                for (int j4 = 0; j4 < (DV + 4) / 4; ++j4) {
+                    if (j4 * 4 < dp) {
+                        float e[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = 4 * j4 + u;
+                            e[u] = j < d ? v[j < DV ? j : 0] - shf[j < DV ? j : 0] : (j == d ? 1.f : 0.f);
+                        }
+                        xr4[j4] = make_float4(e[0], e[1], e[2], e[3]);
+                    }
+                }
                 hq[tid] = (unsigned char)h;
             }
         }
@@ -627,11 +665,12 @@ static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed, const int* gate) {
     if (rows + per * sizeof(T) > budget) return cudaErrorInvalidValue;  // d too large for this kernel
     int CB = (int)std::max<size_t>(1, std::min<size_t>(32, (budget - rows) / (per * sizeof(T))));
     size_t sm = CB * per * sizeof(T) + rows;
-    cudaError_t ea = cudaFuncSetAttribute(labels_simt_kernel<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = c->dbg_scores ? labels_simt_kernel<T, XT, true> : labels_simt_kernel<T, XT, false>;
+    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (ea != cudaSuccess) return ea;
     int grid = (int)((c->N + 255) / 256);
-    labels_simt_kernel<T, XT><<<grid, 256, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c),
-                                                            c->dK, c->diter, seed, CB, gate, c->dbg_scores, c->z);
+    kern<<<grid, 256, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c), c->dK, c->diter, seed,
+                                       CB, gate, c->dbg_scores, c->z);
     return cudaGetLastError();
 }
 

@@ -35,9 +35,13 @@ namespace tc {
 constexpr int BM = 128;          // points per tile (MMA M)
 constexpr int XST = 3;           // X stages
 constexpr int XBYTES = BM * 128; // one X tile: 128 rows x 128 B
-constexpr int NTHREADS = 320;
+constexpr int NPART = 4;         // epilogue warps per TMEM lane quarter
 constexpr int EPI0 = 2;          // first epilogue warp
-constexpr int NEPI = 8;          // epilogue warps
+constexpr int NEPI = 4 * NPART;  // epilogue warps
+constexpr int NTHREADS = 32 * (EPI0 + NEPI);
+// A cluster can win the Gumbel-max only if its score is within G_MAX - G_MIN of the
+// best score (FP32 uniforms: 16.64 + 2.82), plus one nat for rounding.
+constexpr float WINDOW = 20.5f;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t SPIN = 1u << 22;  // bounded waits (a few seconds at most)
 
@@ -135,6 +139,50 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// two 32-column loads, one wait
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+    uint32_t r[32], u[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+          "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+          "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        va[q] = __uint_as_float(r[q]);
+        vb[q] = __uint_as_float(u[q]);
+    }
+}
+
+// squared distance of a 32-wide block to b (four independent chains)
+__device__ __forceinline__ float sqdist32(const float* y, const float* b) {
+    const float4* b4 = (const float4*)b;
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 bb = b4[j4];
+        const float t0 = y[4 * j4] - bb.x, t1 = y[4 * j4 + 1] - bb.y, t2 = y[4 * j4 + 2] - bb.z,
+                    t3 = y[4 * j4 + 3] - bb.w;
+        q0 = fmaf(t0, t0, q0);
+        q1 = fmaf(t1, t1, q1);
+        q2 = fmaf(t2, t2, q2);
+        q3 = fmaf(t3, t3, q3);
+    }
+    return (q0 + q1) + (q2 + q3);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -164,7 +212,7 @@ struct Args {
 };
 
 // shared memory: [X stages | factor image | b table | c table | barriers]
-template <int FMT>
+template <int FMT, bool SCORES>
 __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_constant__ CUtensorMap xmap, Args a) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -178,12 +226,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     uint64_t* tfull = empty + XST;    // 2
     uint64_t* tempty = tfull + 2;     // 2
     uint64_t* bload = tempty + 2;     // 1
-    uint64_t* mfull = bload + 1;      // 2: half 1 published its argmax
-    uint64_t* mempty = mfull + 2;     // 2: half 0 consumed it
+    uint64_t* mfull = bload + 1;      // 2: parts 1.. published their argmax
+    uint64_t* mempty = mfull + 2;     // 2: part 0 consumed them
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ float mbest[2][BM];
-    __shared__ int mz[2][BM];
+    __shared__ float mbest[2][NPART - 1][BM];
+    __shared__ int mz[2][NPART - 1][BM];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = *a.dK;
@@ -209,7 +257,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         }
         mbar_init(bload, 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&mfull[b], 4 * 32);
+            mbar_init(&mfull[b], (NPART - 1) * 4 * 32);
             mbar_init(&mempty[b], 4 * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -293,9 +341,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         }
         __syncwarp();
     } else {
-        // epilogue: thread <-> TMEM lane (point row); two warps per lane quarter
+        // epilogue: thread <-> TMEM lane (point row); NPART warps per lane quarter, part p
+        // takes clusters cc = p, p + NPART, ... of every chunk
         const int ew = warp - EPI0;
-        const int quarter = warp & 3, half = ew >> 2;
+        const int quarter = warp & 3, part = ew >> 2;
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const uint32_t iter = *a.diter;
@@ -304,72 +353,101 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
             const int64_t i = t * BM + r;
-            float best = -INFINITY;
-            int zb = 0;
-            uint32_t w[4];
-            int wblk = -1;
+            // exact Gumbel-max with deferred draws: scores within WINDOW of the running
+            // maximum are kept as candidates (at most 4; beyond that a draw is made at
+            // once); all other clusters cannot win
+            float best = -INFINITY, smax = -INFINITY;
+            int zb = 0, cn = 0;
+            int ck0 = 0, ck1 = 0, ck2 = 0, ck3 = 0;
+            float cs0 = 0.f, cs1 = 0.f, cs2 = 0.f, cs3 = 0.f;
+            auto draw = [&](int k, float sc) {
+                uint32_t w[4];
+                key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
+                const float u = u01_f32((k & 1) ? w[2] : w[0]);
+                const float v = sc - __logf(-logf(u));
+                if (v > best || (v == best && k < zb)) {
+                    best = v;
+                    zb = k;
+                }
+            };
+            auto consider = [&](int k, float q) {
+                const float sc = ct[k] - 0.5f * q;
+                if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
+                    if (i < a.N) a.scores[i * K + k] = (double)sc;
+                }
+                if (sc > smax) {
+                    if (sc > smax + WINDOW) cn = 0;  // every earlier candidate is now out of range
+                    smax = sc;
+                }
+                if (sc > smax - WINDOW) {
+                    if (cn == 0) { ck0 = k; cs0 = sc; }
+                    else if (cn == 1) { ck1 = k; cs1 = sc; }
+                    else if (cn == 2) { ck2 = k; cs2 = sc; }
+                    else if (cn == 3) { ck3 = k; cs3 = sc; }
+                    else draw(k, sc);
+                    cn = min(cn + 1, 4);
+                }
+            };
             for (int c = 0; c < nch; ++c, ++ch) {
                 const int b = (int)(ch & 1);
                 if (!mbar_wait(&tfull[b], (uint32_t)((ch >> 1) & 1), abort)) { ok = false; break; }
                 fence_after();
                 const int nclus = min(a.NC, K - c * a.NC);
-                for (int cc = half; cc < nclus; cc += 2) {
-                    const int k = c * a.NC + cc;
-                    const float* bk = bt + (size_t)k * a.dn;
-                    float q = 0.f;
-                    const uint32_t col = tmem + lane_off + (uint32_t)(b * 256 + cc * a.dn);
-                    if (a.dn == 32) {  // the loads never pass the block's own columns
+                const uint32_t cbase = tmem + lane_off + (uint32_t)(b * 256);
+                if (a.dn == 32) {  // 32-column loads never pass the block's own columns
+                    for (int cc = part; cc < nclus; cc += NPART) {
+                        const int k = c * a.NC + cc;
                         float y[32];
-                        tmem_ld32(col, y);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float tdiff = y[j] - bk[j];
-                            q = fmaf(tdiff, tdiff, q);
-                        }
-                    } else {
+                        tmem_ld32(cbase + (uint32_t)(cc * 32), y);
+                        consider(k, sqdist32(y, bt + (size_t)k * 32));
+                    }
+                } else {
+                    for (int cc = part; cc < nclus; cc += NPART) {
+                        const int k = c * a.NC + cc;
+                        const float* bk = bt + (size_t)k * a.dn;
+                        float q0 = 0.f, q1 = 0.f;
                         for (int j0 = 0; j0 < a.dn; j0 += 8) {
                             float y[8];
-                            tmem_ld8(col + (uint32_t)j0, y);
+                            tmem_ld8(cbase + (uint32_t)(cc * a.dn + j0), y);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float tdiff = y[j] - bk[j0 + j];
-                                q = fmaf(tdiff, tdiff, q);
+                            for (int j = 0; j < 8; j += 2) {
+                                const float t0 = y[j] - bk[j0 + j], t1 = y[j + 1] - bk[j0 + j + 1];
+                                q0 = fmaf(t0, t0, q0);
+                                q1 = fmaf(t1, t1, q1);
                             }
                         }
-                    }
-                    const float sc = ct[k] - 0.5f * q;
-                    if (a.scores && i < a.N) a.scores[i * K + k] = (double)sc;
-                    if (sc + GUMBEL_MAX_F32 > best) {
-                        if ((k >> 1) != wblk) {
-                            key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
-                            wblk = k >> 1;
-                        }
-                        const float u = u01_f32((k & 1) ? w[2] : w[0]);
-                        const float v = sc - __logf(-logf(u));
-                        if (v > best) {
-                            best = v;
-                            zb = k;
-                        }
+                        consider(k, q0 + q1);
                     }
                 }
                 fence_before();
                 mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
-            // merge the two halves: the larger perturbed score wins, the lower k on a tie
+            const float lim = smax - WINDOW;
+            if (cn > 0 && cs0 > lim) draw(ck0, cs0);
+            if (cn > 1 && cs1 > lim) draw(ck1, cs1);
+            if (cn > 2 && cs2 > lim) draw(ck2, cs2);
+            if (cn > 3 && cs3 > lim) draw(ck3, cs3);
+            // merge the parts: the larger perturbed score wins, the lower k on a tie
             const int sl = (int)(it & 1);
             const uint32_t use = (uint32_t)((it >> 1) & 1);
-            if (half == 1) {
+            if (part > 0) {
                 if (!mbar_wait(&mempty[sl], use ^ 1u, abort)) { ok = false; break; }
-                mbest[sl][r] = best;
-                mz[sl][r] = zb;
+                mbest[sl][part - 1][r] = best;
+                mz[sl][part - 1][r] = zb;
                 mbar_arrive(&mfull[sl]);
             } else {
                 if (!mbar_wait(&mfull[sl], use, abort)) { ok = false; break; }
-                const float ob = mbest[sl][r];
-                const int oz = mz[sl][r];
+#pragma unroll
+                for (int p2 = 0; p2 < NPART - 1; ++p2) {
+                    const float ob = mbest[sl][p2][r];
+                    const int oz = mz[sl][p2][r];
+                    if (ob > best || (ob == best && oz < zb)) {
+                        best = ob;
+                        zb = oz;
+                    }
+                }
                 mbar_arrive(&mempty[sl]);
-                if (ob > best || (ob == best && oz < zb)) zb = oz;
                 if (i < a.N) a.z[i] = zb;
             }
         }
@@ -430,7 +508,7 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     q.NC = 256 / q.dn;
     while ((q.NC * q.dn) % 16) --q.NC;
     const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)c->K_max * (q.dn + 1) * 4 + 32 * 8 + 64;
-    const size_t limit = 227 * 1024 - 2048;  // leave room for static shared memory
+    const size_t limit = 227 * 1024 - 8192;  // leave room for the kernel's static shared memory (7 KB)
     size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * 128;
     size_t cap = std::min(want, limit - fixed);
     q.cap_rows = (int)(cap / 128 / 16 * 16);
@@ -499,13 +577,13 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
     a.overflow = c->tc_flag;
     a.derr = c->derr;
     a.scores = c->dbg_scores;
-    cudaError_t e = cudaFuncSetAttribute(tc::labels_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)q.smem);
+    auto kern = a.scores ? tc::labels_tc_kernel<2, true> : tc::labels_tc_kernel<2, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (c->N + tc::BM - 1) / tc::BM;
     const int grid = (int)std::min<int64_t>(c->num_sms, ntiles);
     prof_begin(c, "labels_tc");
-    tc::labels_tc_kernel<2><<<grid, tc::NTHREADS, q.smem, c->stream>>>(map, a);
+    kern<<<grid, tc::NTHREADS, q.smem, c->stream>>>(map, a);
     prof_end(c, "labels_tc");
     c->nlaunch += 1;
     e = cudaGetLastError();
