@@ -354,6 +354,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     } else if (c->prec == DPMM_PREC_BF16) {
         c->xdt = 2;
         c->xs = (d + 7) / 8 * 8;
+        if (c->xs < 64) c->xs = 64;  // one 128-byte TMA box per row
     } else {
         c->xdt = 1;
         c->xs = (d + 3) / 4 * 4;

@@ -277,20 +277,44 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
                     ++nsplit;
                 }
             }
+        }
+        s_K = nsplit;  // carried to the merge walk below
+        s_Knew = nrej;
+    }
+    __syncthreads();
+    // merges: for k1 in order, the first eligible k2 > k1 whose proposal is accepted
+    // (found 32 candidates at a time by warp 0; same outcome as the plain double loop)
+    __shared__ int s_nmerge;
+    if (tid < 32) {
+        int nm = 0;
+        if (a.sm_enabled) {
+            auto elig = [&](int k) { return live[k] && split_to[k] < 0 && merged_into[k] < 0 && !head[k]; };
             for (int k1 = 0; k1 < K; ++k1) {
-                if (!live[k1] || split_to[k1] >= 0 || merged_into[k1] >= 0 || head[k1]) continue;
-                for (int k2 = k1 + 1; k2 < K; ++k2) {
-                    if (!live[k2] || split_to[k2] >= 0 || merged_into[k2] >= 0 || head[k2]) continue;
-                    const int p = k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1);
-                    if (acc_merge(p)) {
-                        merged_into[k2] = k1;
-                        head[k1] = 1;
-                        ++nmerge;
-                        break;
-                    }
+                if (!elig(k1)) continue;
+                int found = -1;
+                for (int b0 = k1 + 1; b0 < K && found < 0; b0 += 32) {
+                    const int k2 = b0 + tid;
+                    const bool ok = k2 < K && elig(k2) && acc_merge(k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1));
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    if (m) found = b0 + __ffs(m) - 1;
                 }
+                if (found >= 0) {
+                    if (tid == 0) {
+                        merged_into[found] = k1;
+                        head[k1] = 1;
+                    }
+                    ++nm;
+                }
+                __syncwarp();
             }
         }
+        if (tid == 0) s_nmerge = nm;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int nsplit = s_K, nrej = s_Knew, nmerge = s_nmerge;
+        int Kc = 0;
+        for (int k = 0; k < K; ++k) Kc += live[k];
         // nage holds the old ages; the new ones go to cid (free after the proposals)
         int nid = 0;
         for (int k = 0; k < K; ++k)
@@ -398,7 +422,8 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     SMArgs s = sm_args(c);
     if (sm_enabled) {
         int items = 3 * c->K_max + c->K_max * (c->K_max - 1) / 2;
-        size_t sm = sizeof(double) * ((size_t)c->d * c->d + 4 * c->d);
+        // the Dirichlet marginal needs no matrix workspace
+        size_t sm = c->kind == DPMM_PRIOR_NIW ? sizeof(double) * ((size_t)c->d * c->d + 4 * c->d) : 0;
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(marginal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;

@@ -52,7 +52,8 @@ template <>
 __device__ inline float gmax<float>() { return GUMBEL_MAX_F32; }
 
 // ------------------------------------------------------------------ labels (simt)
-// Dynamic shared memory: CB clusters x (d*d + d + 1) T, then 256 x (d + 1) T rows.
+// Dynamic shared memory: CB clusters x (d*d + d + 1) T (d + 1 for multinomial), then
+// blockDim x (d + 1) T point rows.
 template <typename T, typename XT, bool SCORES>
 __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int xs, int64_t N, const XT* __restrict__ X,
                                                           ParamView<T> pv, const int* dK, const uint32_t* diter,
@@ -64,8 +65,11 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
     const int per = kind == DPMM_PRIOR_NIW ? d * d + d + 1 : d + 1;
     T* sx = sW + (size_t)CB * per;
     const int K = *dK;
-    const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t ntiles = (N + nt - 1) / nt;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {  // grid-stride over point tiles
+    __syncthreads();
+    const int64_t i = tile * nt + tid;
     const bool live = i < N;
     T* xr = sx + (size_t)tid * (d + 1);
     if (live)
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
     for (int k0 = 0; k0 < K; k0 += CB) {
         const int nc = min(CB, K - k0);
         __syncthreads();
-        for (int e = tid; e < nc * per; e += 256) {
+        for (int e = tid; e < nc * per; e += nt) {
             int cc = e / per, r = e % per;
             int s = 3 * (k0 + cc);
             T v;
@@ -127,6 +131,7 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
         }
     }
     if (live) z[i] = zb;
+    }
 }
 
 // ------------------------------------------------------------------ counting sort
@@ -614,6 +619,169 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
     if (cur >= 0) flush(cur);
 }
 
+// Multinomial variant (first-moment statistics only): the point's counts become a
+// float row in shared memory (x, then 1, then zeros); the current run's two
+// sub-cluster log theta vectors are staged in shared memory; each sub-cluster score is
+// a d-long dot product fed by float4 loads; each worker thread owns the counts of one
+// 4-category block for both sub-clusters.  Dynamic shared memory: P x dp rows, P ints
+// (k), P + 2 ints (runs), P bytes (h), then 2 dp + 2 floats (staged parameters), then
+// the flush buffer G x nblk x 8 floats.
+template <typename XT>
+__global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
+    if (a.gate && *a.gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int d = a.d, dp = a.L.dp, P = a.P, G = a.G, nblk = a.L.nblk;
+    float* xs = (float*)smraw;
+    int* kq = (int*)(xs + (size_t)P * dp);
+    int* runs = kq + P;
+    int* nruns = runs + P + 1;
+    unsigned char* hq = (unsigned char*)(nruns + 1);
+    float* lt0 = (float*)(smraw + (((size_t)P * dp * 4 + (2 * P + 2) * sizeof(int) + P + 15) / 16) * 16);
+    float* lt1 = lt0 + dp;
+    float* cc = lt1 + dp;
+    float* red = (float*)(((uintptr_t)(cc + 2) + 15) & ~(uintptr_t)15);
+    __shared__ int staged;
+    __shared__ int wcnt[32];
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int g = blockIdx.x;
+    const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
+    Key key{a.seed, *a.diter, 0};
+    const XT* X = (const XT*)a.X;
+    const bool worker = tid < nblk * G;
+    const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
+    const int one = d & 3;  // position of the constant 1 inside the last 4-column block
+    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+    int cur = -1;
+    if (tid == 0) staged = -1;
+
+    auto flush = [&](int k) {
+        __syncthreads();
+        if (worker) {
+            float* r = red + ((size_t)grp * nblk + myblk) * 8;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                r[u] = acc0[u];
+                r[4 + u] = acc1[u];
+            }
+        }
+        __syncthreads();
+        double* out = a.rec + (size_t)(g + k) * 2 * a.L.E;
+        for (int e = tid; e < nblk * 16; e += nt) {
+            const int b = e >> 4, q = e & 15, u = q >> 2, v = q & 3;
+            double s0 = 0.0, s1 = 0.0;
+            if (v == one)
+                for (int gg = 0; gg < G; ++gg) {
+                    s0 += (double)red[((size_t)gg * nblk + b) * 8 + u];
+                    s1 += (double)red[((size_t)gg * nblk + b) * 8 + 4 + u];
+                }
+            out[e] = s0;
+            out[a.L.E + e] = s1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc0[u] = acc1[u] = 0.f;
+    };
+
+    for (int64_t base = p0; base < p1; base += P) {
+        const int np = (int)min((int64_t)P, p1 - base);
+        __syncthreads();
+        int i = 0;
+        if (tid < np) {
+            i = a.idx[base + tid];
+            kq[tid] = a.z[i];
+            float* xr = xs + (size_t)tid * dp;
+            if constexpr (sizeof(XT) == 2) {  // 16-byte loads: 8 BF16 counts (rows are 16-byte aligned)
+                const uint4* src = (const uint4*)(X + (int64_t)i * a.xs);
+                const int nfull = d / 8;  // whole 8-count chunks inside the row's d columns
+                for (int j8 = 0; j8 < nfull; ++j8) {
+                    const uint4 q = src[j8];
+                    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+                    float f[8];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        f[2 * u] = __uint_as_float(wv[u] << 16);
+                        f[2 * u + 1] = __uint_as_float(wv[u] & 0xFFFF0000u);
+                    }
+                    *(float4*)(xr + 8 * j8) = make_float4(f[0], f[1], f[2], f[3]);
+                    *(float4*)(xr + 8 * j8 + 4) = make_float4(f[4], f[5], f[6], f[7]);
+                }
+                for (int j = 8 * nfull; j < dp; ++j)
+                    xr[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : (j == d ? 1.f : 0.f);
+            } else {
+                for (int j = 0; j < dp; ++j)
+                    xr[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : (j == d ? 1.f : 0.f);
+            }
+        }
+        __syncthreads();
+        find_runs(kq, np, runs, nruns, wcnt);
+        const int nr = *nruns;
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (a.draw && k != staged) {  // uniform: stage this cluster's two sub-clusters
+                __syncthreads();
+                for (int e = tid; e < 2 * dp; e += nt) {
+                    const int h = e / dp, j = e % dp;
+                    lt0[e] = j < d ? a.pv.lt[(size_t)(3 * k + 1 + h) * d + j] : 0.f;
+                }
+                if (tid < 2) cc[tid] = a.pv.c[3 * k + 1 + tid];
+                __syncthreads();
+                if (tid == 0) staged = k;
+            }
+            if (tid >= qs && tid < qe) {
+                int h;
+                if (a.draw) {
+                    const float4* xr4 = (const float4*)(xs + (size_t)tid * dp);
+                    const float4* l04 = (const float4*)lt0;
+                    const float4* l14 = (const float4*)lt1;
+                    float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+                    for (int j4 = 0; j4 < dp / 4; ++j4) {
+                        const float4 x = xr4[j4], u = l04[j4], w = l14[j4];
+                        s0 = fmaf(x.x, u.x, s0);
+                        t0 = fmaf(x.y, u.y, t0);
+                        s0 = fmaf(x.z, u.z, s0);
+                        t0 = fmaf(x.w, u.w, t0);
+                        s1 = fmaf(x.x, w.x, s1);
+                        t1 = fmaf(x.y, w.y, t1);
+                        s1 = fmaf(x.z, w.z, s1);
+                        t1 = fmaf(x.w, w.w, t1);
+                    }
+                    // the padding column d holds 1 and lt[d] = 0: it adds nothing
+                    uint32_t wq[4];
+                    key.block((uint32_t)i, TAG_ZBAR, 0, wq);
+                    const float vl = cc[0] + s0 + t0 + gumbel_of<float>(wq[0], wq[1]);
+                    const float vr = cc[1] + s1 + t1 + gumbel_of<float>(wq[2], wq[3]);
+                    h = vr > vl ? 1 : 0;
+                    a.zbar[i] = (uint8_t)h;
+                } else {
+                    h = a.zbar[i];
+                }
+                hq[tid] = (unsigned char)h;
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (k != cur) {
+                if (cur >= 0) flush(cur);
+                cur = k;
+            }
+            if (worker) {
+                for (int q = qs + grp; q < qe; q += G) {
+                    const float4 xj = *(const float4*)(xs + (size_t)q * dp + myblk * 4);
+                    if (hq[q]) {
+                        acc1[0] += xj.x; acc1[1] += xj.y; acc1[2] += xj.z; acc1[3] += xj.w;
+                    } else {
+                        acc0[0] += xj.x; acc0[1] += xj.y; acc0[2] += xj.z; acc0[3] += xj.w;
+                    }
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush(cur);
+}
+
 // stats[(2k + h) E + e] = sum over the CTAs g covering cluster k's run of rec[g + k]
 __global__ void combine_kernel(const double* rec, const int* starts, const int* dK, int64_t R, int E,
                                const double* shift_new, double* shift_stats, int d, const int* gate,
@@ -660,17 +828,21 @@ template <typename T, typename XT>
 static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed, const int* gate) {
     const int d = c->d;
     const size_t per = c->kind == DPMM_PRIOR_NIW ? (size_t)d * d + d + 1 : (size_t)d + 1;
-    const size_t rows = (size_t)256 * (d + 1) * sizeof(T);
     size_t budget = 200 * 1024;
+    int TB = 256;  // fewer points per CTA when the rows would not leave room for one cluster
+    while (TB > 32 && (size_t)TB * (d + 1) * sizeof(T) + per * sizeof(T) > budget / 2) TB /= 2;
+    const size_t rows = (size_t)TB * (d + 1) * sizeof(T);
     if (rows + per * sizeof(T) > budget) return cudaErrorInvalidValue;  // d too large for this kernel
     int CB = (int)std::max<size_t>(1, std::min<size_t>(32, (budget - rows) / (per * sizeof(T))));
     size_t sm = CB * per * sizeof(T) + rows;
     auto kern = c->dbg_scores ? labels_simt_kernel<T, XT, true> : labels_simt_kernel<T, XT, false>;
     cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (ea != cudaSuccess) return ea;
-    int grid = (int)((c->N + 255) / 256);
-    kern<<<grid, 256, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c), c->dK, c->diter, seed,
-                                       CB, gate, c->dbg_scores, c->z);
+    // a gated launch usually exits at once: keep its grid small and let CTAs stride
+    int64_t tiles = (c->N + TB - 1) / TB;
+    int grid = (int)(gate ? std::min<int64_t>(tiles, 4 * (int64_t)c->num_sms) : tiles);
+    kern<<<grid, TB, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c), c->dK, c->diter, seed,
+                                      CB, gate, c->dbg_scores, c->z);
     return cudaGetLastError();
 }
 
@@ -819,9 +991,52 @@ static cudaError_t substats_f32_t(dpmm_ctx* c, uint64_t seed, int draw, const in
     return cudaGetLastError();
 }
 
+template <typename XT>
+static cudaError_t substats_mult_t(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
+    const StatLayout& L = c->st;
+    int P = (int)((96 * 1024) / ((size_t)L.dp * 4));
+    P = std::max(32, std::min(256, P / 32 * 32));
+    const int G = std::max(1, 256 / L.nblk);
+    size_t head = (size_t)P * L.dp * 4 + (2 * (size_t)P + 2) * sizeof(int) + P;
+    head = (head + 15) / 16 * 16;
+    const size_t smem = head + ((size_t)2 * L.dp + 2) * 4 + 16 + (size_t)G * L.nblk * 8 * 4;
+    SubArgs<float> a;
+    a.kind = c->kind;
+    a.d = c->d;
+    a.xs = c->xs;
+    a.N = c->N;
+    a.X = c->X;
+    a.pv = pview<float>(c);
+    a.shift = c->shift32;
+    a.z = c->z;
+    a.zbar = c->zbar;
+    a.idx = c->idx;
+    a.dK = c->dK;
+    a.diter = c->diter;
+    a.gate = gate;
+    a.seed = seed;
+    a.draw = draw;
+    a.P = P;
+    a.G = G;
+    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.L = L;
+    a.rec = c->records;
+    cudaError_t ea = cudaFuncSetAttribute(substats_mult_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ea != cudaSuccess) return ea;
+    substats_mult_kernel<XT><<<c->G2, 256, smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
 static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
     prof_begin(c, draw ? "substats" : "restats");
     cudaError_t e;
+    const bool mult_fast = c->prec != DPMM_PREC_FP64_PLAIN && c->kind == DPMM_PRIOR_DIRICHLET && c->st.nblk <= 256;
+    if (mult_fast) {
+        e = c->xdt == 2 ? substats_mult_t<__nv_bfloat16>(c, seed, draw, gate) : substats_mult_t<float>(c, seed, draw, gate);
+        prof_end(c, draw ? "substats" : "restats");
+        c->nlaunch += 1;
+        return e;
+    }
     const bool fast = c->prec != DPMM_PREC_FP64_PLAIN && c->kind == DPMM_PRIOR_NIW && c->d <= 64 && c->st.nblk <= 256;
     if (fast && c->d <= 32) e = c->xdt == 2 ? substats_f32_t<32, __nv_bfloat16>(c, seed, draw, gate)
                                              : substats_f32_t<32, float>(c, seed, draw, gate);

@@ -27,12 +27,12 @@
 #include <algorithm>
 
 #include "dpmm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace dpmm {
 
 namespace tc {
 
-constexpr int BM = 128;          // points per tile (MMA M)
 constexpr int XST = 3;           // X stages
 constexpr int XBYTES = BM * 128; // one X tile: 128 rows x 128 B
 constexpr int NPART = 4;         // epilogue warps per TMEM lane quarter
@@ -43,155 +43,6 @@ constexpr int NTHREADS = 32 * (EPI0 + NEPI);
 // best score (FP32 uniforms: 16.64 + 2.82), plus one nat for rounding.
 constexpr float WINDOW = 20.5f;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t SPIN = 1u << 22;  // bounded waits (a few seconds at most)
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on timeout or when another role has aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
-    for (uint32_t it = 0; it < SPIN; ++it) {
-        if (mbar_try(b, parity)) return true;
-        if ((it & 1023u) == 1023u && *abort) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            saddr(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(saddr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     saddr(dst)),
-                 "l"((uint64_t)src), "r"(bytes), "r"(saddr(bar))
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle layout:
-// 8-row groups of 128-byte rows, 1024 bytes apart (SBO); LBO unused (1); version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-// Instruction descriptor: D FP32, A and B TF32 (kind::tf32, format 2) or BF16
-// (kind::f16, format 1), both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc(int n, int fmt) {
-    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
-}
-
-template <int FMT>
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    if constexpr (FMT == 2) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
-                tmem),
-            "l"(a), "l"(b), "r"(id), "r"(acc)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                tmem),
-            "l"(a), "l"(b), "r"(id), "r"(acc)
-            : "memory");
-    }
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// two 32-column loads, one wait
-__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
-    uint32_t r[32], u[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(ta));
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
-          "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
-          "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
-        : "r"(tb));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        va[q] = __uint_as_float(r[q]);
-        vb[q] = __uint_as_float(u[q]);
-    }
-}
-
-// squared distance of a 32-wide block to b (four independent chains)
-__device__ __forceinline__ float sqdist32(const float* y, const float* b) {
-    const float4* b4 = (const float4*)b;
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
-#pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) {
-        const float4 bb = b4[j4];
-        const float t0 = y[4 * j4] - bb.x, t1 = y[4 * j4 + 1] - bb.y, t2 = y[4 * j4 + 2] - bb.z,
-                    t3 = y[4 * j4 + 3] - bb.w;
-        q0 = fmaf(t0, t0, q0);
-        q1 = fmaf(t1, t1, q1);
-        q2 = fmaf(t2, t2, q2);
-        q3 = fmaf(t3, t3, q3);
-    }
-    return (q0 + q1) + (q2 + q3);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
-}
 
 struct Args {
     int64_t N;
@@ -485,7 +336,10 @@ __global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const fl
 }  // namespace tc
 
 // -------------------------------------------------------------------------- host
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn();
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() { return tc_encode_fn(); }
+
+PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -517,13 +371,19 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     return q;
 }
 
+bool mult_supported(const dpmm_ctx* c);
+cudaError_t mult_prepare(dpmm_ctx* c);
+cudaError_t launch_labels_mult(dpmm_ctx* c, uint64_t seed);
+
 bool tc_supported(const dpmm_ctx* c) {
-    // Gaussian, TF32 or BF16 storage, one 128-byte swizzle atom in the contraction dimension
-    return c->kind == DPMM_PRIOR_NIW && c->prec == DPMM_PREC_TF32 && c->d >= 1 && c->d <= 32 &&
-           get_encode() != nullptr;
+    if (get_encode() == nullptr) return false;
+    // Gaussian: TF32, one 128-byte swizzle atom in the contraction dimension;
+    // multinomial: BF16 counts, up to four atoms
+    return (c->kind == DPMM_PRIOR_NIW && c->prec == DPMM_PREC_TF32 && c->d >= 1 && c->d <= 32) || mult_supported(c);
 }
 
 cudaError_t tc_prepare(dpmm_ctx* c) {
+    if (c->kind == DPMM_PRIOR_DIRICHLET) return mult_supported(c) ? mult_prepare(c) : cudaSuccess;
     if (c->prec != DPMM_PREC_TF32) return cudaSuccess;
     TcCfg q = tc_cfg(c);
     const size_t bytes = (size_t)q.cap_rows * 128;
@@ -544,6 +404,7 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
 cudaError_t launch_labels_simt_gated(dpmm_ctx* c, uint64_t seed, const int* gate);
 
 cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
+    if (c->kind == DPMM_PRIOR_DIRICHLET) return launch_labels_mult(c, seed);
     TcCfg q = tc_cfg(c);
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc || !c->tc_img) return cudaErrorNotSupported;

@@ -111,3 +111,68 @@ def test_tc_chain_finds_clusters():
     purity = sum(Counter(z[y == k]).most_common(1)[0][1] for k in range(6) if (y == k).any()) / N
     assert purity > 0.95, purity
     g.close()
+
+
+# ---------------------------------------------------------------- multinomial (BF16)
+
+def _mult_setup(N, d, K, seed, K_max=64, draws=100):
+    from paper_2204_08988_gb300 import synth
+
+    X, y = synth.multinomial_mixture(N, d, K, draws, seed=seed)
+    o = O.Oracle(O.DIRICHLET, d, K_max, 3.0, beta=np.ones(d))
+    o.set_data(X.astype(np.float64))
+    zb = (np.arange(N) % 2).astype(np.uint8)
+    o.set_state(K, y, zb)
+    o.draw_params(seed)
+    p = o.params()
+    g = P.DPMM(1, d, K_max, 3.0, prec=P.PREC_BF16, beta=np.ones(d))
+    g.set_data(X)
+    g.set_state(K, y, zb)
+    g.set_params(K, p)
+    return X, y, zb, o, g, p
+
+
+@pytest.mark.parametrize("N,d,K", [(5000, 200, 10), (3001, 12, 4), (4000, 200, 50)])
+def test_mult_scores_within_budget(N, d, K):
+    """BF16 counts (exact) times log theta split into two BF16 halves, FP32 accumulation:
+    contender scores within 0.02 nat on average and 0.2 nat at worst."""
+    X, y, zb, o, g, p = _mult_setup(N, d, K, seed=N + d)
+    s_tc = g.label_scores()
+    s_64 = np.stack([p["logw"][3 * k] + X.astype(np.float64) @ p["logtheta"][3 * k] for k in range(K)], 1)
+    err = np.abs(s_tc - s_64)
+    cont = s_64 >= s_64.max(1, keepdims=True) - 20.0
+    assert err[cont].mean() < 0.02, err[cont].mean()
+    assert err[cont].max() < 0.2, err[cont].max()
+    g.close()
+
+
+def test_mult_labels_agree_with_fp64():
+    N, d, K = 20000, 200, 50
+    X, y, zb, o, g, p = _mult_setup(N, d, K, seed=3)
+    g.set_mask(2)
+    g.sweep(1, 321)
+    o.sweep(1, 321, mask=O.MASK_LABELS)
+    zo, zbo = o.labels()
+    zg, zbg = g.labels()
+    assert o.K == g.K
+    assert (zo != zg).mean() < 1e-3
+    assert (zbo != zbg).mean() < 1e-2
+    g.close()
+
+
+def test_mult_chain_finds_topics():
+    from collections import Counter
+
+    from paper_2204_08988_gb300 import synth
+
+    N, d, K = 40_000, 200, 8
+    X, y = synth.multinomial_mixture(N, d, K, 100, seed=17)
+    g = P.DPMM(1, d, 32, 10.0, prec=P.PREC_BF16, burn_out=3, beta=np.ones(d))
+    g.set_data(X)
+    g.sweep(60, 2)
+    z, _ = g.labels()
+    n, _, _ = g.stats()
+    assert n[0::3].sum() == N
+    purity = sum(Counter(z[y == k]).most_common(1)[0][1] for k in range(K) if (y == k).any()) / N
+    assert purity > 0.95, (purity, g.K)
+    g.close()
