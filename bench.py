@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
 DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32"}
 METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
+# ncu DRAM bytes (read + write) per point of the label kernel, from the capture summarised in
+# profiles/labels_tc_gauss_d32.md; must be re-taken (or removed) whenever that kernel changes
+TRAFFIC_BYTES_PER_POINT = {("labels_tc", "gauss_d32"): (256.168192e6 + 8.592640e6) / 2e6}
 WORKLOADS = {
     "gauss_d32": dict(K_max=64),
     "gauss_d2": dict(K_max=64),
@@ -257,7 +260,10 @@ def main():
             roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peak, "unit": "GB/s",
                     "peak_source": "measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
+        # DRAM bytes per launch from the ncu capture summarised in profiles/ (taken on 2 M points,
+        # scaled by the points processed); null for kernels without a current capture
+        tb = TRAFFIC_BYTES_PER_POINT.get((lk[0], a.workload))
+        roof["traffic"] = tb * N if tb else None
         roof["kernel"] = lk[0]
         roof["kernel_ms_avg"] = ms / max(launches, 1)
     gpu_launches = prof.get("all_kernels", (0, 0))[0]
