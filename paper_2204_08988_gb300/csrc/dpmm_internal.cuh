@@ -211,6 +211,9 @@ struct dpmm_ctx {
     void* tc_img = nullptr;  // tensor-core operand image of the cluster parameters
     size_t tc_img_bytes = 0;
     double* cweights = nullptr;  // K_max: pi_k of the last sweep (linear)
+    double* eps = nullptr;       // 3 K_max x d: normals of the drawn means
+    double* bart = nullptr;      // 3 K_max x d: Bartlett diagonal (chi-square roots)
+    double* lgs = nullptr;       // 3 K_max + 1: log-Gamma draws of the weights
 
     // sort / reduction scratch
     int T_tiles = 0;         // sort tiles of 256 points

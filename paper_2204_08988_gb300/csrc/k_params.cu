@@ -4,6 +4,8 @@
 // from the conjugate posterior of its sufficient statistics.
 #include <math.h>
 
+#include <algorithm>
+
 #include "dpmm_internal.cuh"
 
 namespace dpmm {
@@ -44,29 +46,81 @@ __device__ inline double block_reduce_sum(double v, double* sh) {
     return v;
 }
 
-// (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2).
-// All 3K + 1 Gamma draws in one parallel phase (draw t: t < K weight k = t, t = K the
-// leftover mass, then sub-weights (k, h) at t = K + 1 + 2k + h), then the two
-// normalisations.  Dynamic shared memory: 3 K_max + 1 doubles.
-__global__ void __launch_bounds__(1024) weights_kernel(StatView sv, const int* dK, const uint32_t* diter,
-                                                       uint64_t seed, double alpha, double* logw,
+// Every random variate of steps (a)-(d) that does not depend on a Cholesky factor,
+// one thread each, spread over the whole GPU (GB300's FP64 pipes are narrow, so FP64
+// work must be spread over many SMs):
+//   blockIdx.y < 3 K_max: slot s = blockIdx.y (NIW only): thread q < npair draws the
+//     Box-Muller pair q of the slot's PARAM stream (normals 2q, 2q + 1) into W (entry
+//     r*d + c, r < c; zero below the diagonal) or eps (normal d*d + j); thread
+//     npair + j draws the Bartlett chi-square j into bart[s][j] (as sqrt);
+//   blockIdx.y = 3 K_max: the 3K + 1 Gamma draws of steps (a), (b) into lgs.
+struct VarArgs {
+    StatView sv;
+    const int* dK;
+    const uint32_t* diter;
+    uint64_t seed;
+    double alpha, nu0;
+    int kind, Kmax, niw;
+    double* W;     // p_W
+    double* eps;   // 3 K_max x d
+    double* bart;  // 3 K_max x d
+    double* lgs;   // 3 K_max + 1
+};
+
+__global__ void variates_kernel(VarArgs a) {
+    const int K = *a.dK;
+    const int d = a.sv.L.d;
+    Key key{a.seed, *a.diter, 0};
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int)blockIdx.y == 3 * a.Kmax) {
+        const int T = 3 * K + 1;
+        if (q >= T) return;
+        double v;
+        if (q < K) v = d_log_gamma(key, (uint32_t)q, TAG_WEIGHT, 0, a.sv.count(q, -1));
+        else if (q == K) v = d_log_gamma(key, 0xFFFFFFFFu, TAG_WEIGHT, 0, a.alpha);
+        else {
+            const int k = (q - K - 1) >> 1, h = (q - K - 1) & 1;
+            v = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 64u * h, a.sv.count(k, h) + 0.5 * a.alpha);
+        }
+        a.lgs[q] = v;
+        return;
+    }
+    const int s = blockIdx.y;
+    if (!a.niw || s >= 3 * K) return;
+    const int npair = (d * d + d + 1) / 2;
+    const uint32_t NB = 64u * d;
+    if (q < npair) {
+        uint32_t w[4];
+        key.block((uint32_t)s, TAG_PARAM, NB + (uint32_t)q, w);
+        const double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
+        const double rr = sqrt(-2.0 * log(u1)), ang = 6.283185307179586 * u2;
+        double* W = a.W + (size_t)s * d * d;
+        for (int o = 0; o < 2; ++o) {
+            const int qq = 2 * q + o;
+            const double nv = o ? rr * sin(ang) : rr * cos(ang);
+            if (qq < d * d) {
+                const int r = qq / d, c = qq % d;
+                W[qq] = r < c ? nv : 0.0;
+            } else if (qq < d * d + d) {
+                a.eps[(size_t)s * d + (qq - d * d)] = nv;
+            }
+        }
+    } else if (q < npair + d) {
+        const int j = q - npair;
+        const int k = s / 3, h = s % 3 - 1;
+        const double nun = a.nu0 + a.sv.count(k, h);
+        const double df = nun - d + (j + 1);
+        const double lg = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, 0.5 * df);
+        a.bart[(size_t)s * d + j] = sqrt(2.0 * exp(lg));
+    }
+}
+
+// (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2):
+// normalisation of the Gamma draws made by variates_kernel.
+__global__ void __launch_bounds__(1024) weights_kernel(const int* dK, const double* lgs, double* logw,
                                                        double* cweights) {
-    extern __shared__ double lgs[];
     __shared__ double sh[32];
     const int K = *dK;
-    Key key{seed, *diter, 0};
-    const int T = 3 * K + 1;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        double v;
-        if (t < K) v = d_log_gamma(key, (uint32_t)t, TAG_WEIGHT, 0, sv.count(t, -1));
-        else if (t == K) v = d_log_gamma(key, 0xFFFFFFFFu, TAG_WEIGHT, 0, alpha);
-        else {
-            const int k = (t - K - 1) >> 1, h = (t - K - 1) & 1;
-            v = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 64u * h, sv.count(k, h) + 0.5 * alpha);
-        }
-        lgs[t] = v;
-    }
-    __syncthreads();
     double lmax = -INFINITY;
     for (int k = threadIdx.x; k <= K; k += blockDim.x) lmax = fmax(lmax, lgs[k]);
     lmax = block_reduce_max(lmax, sh);
@@ -95,7 +149,7 @@ struct NiwPrior {
 // B_jj^2 ~ chi^2(nu_n - d + j), j = 1..d, N(0,1) above the diagonal);
 // mu = m_n + W^-T eps / sqrt(kappa_n).  Dynamic shared memory: d*d + 4*d doubles.
 __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPrior pr, const int* dK,
-                                  const uint32_t* diter, uint64_t seed, const double* logw, double* p_mu,
+                                  const double* eps, const double* bart, const double* logw, double* p_mu,
                                   double* p_W, double* p_logdetW, double* p_c, int* derr) {
     extern __shared__ double smem[];
     const int d = sv.L.d;
@@ -110,7 +164,6 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     double* acc = Bd + d;         // d
     __shared__ double sh[32];
     __shared__ double s_n, s_kn, s_nun;
-    Key key{seed, *diter, 0};
     const int tid = threadIdx.x, nt = blockDim.x;
 
     if (tid == 0) {
@@ -130,13 +183,14 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     __syncthreads();
     // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n
     const double f = n > 0 ? pr.kappa0 * n / kn : 0.0;
+    // lower triangle only: the factorisation below reads nothing else
     for (int e = tid; e < d * d; e += nt) {
         int j = e / d, l = e % d;
-        int a = min(j, l), b = max(j, l);
+        if (l > j) continue;
         double C = 0.0;
         if (n > 0) {
-            double s1a = sv.m(k, h, a, d), s1b = sv.m(k, h, b, d);
-            C = sv.m(k, h, a, b) - s1a * s1b / n;
+            double s1a = sv.m(k, h, l, d), s1b = sv.m(k, h, j, d);
+            C = sv.m(k, h, l, j) - s1a * s1b / n;
         }
         A[e] = pr.psi0[e] + C + f * (xb[j] - pr.m0s[j]) * (xb[l] - pr.m0s[l]);
     }
@@ -152,7 +206,8 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
             A[j * d + j] = sqrt(v);
         }
         __syncthreads();
-        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] /= A[j * d + j];
+        const double rj = 1.0 / A[j * d + j];
+        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] *= rj;
         __syncthreads();
         int m = d - j - 1;
         for (int e = tid; e < m * m; e += nt) {
@@ -161,33 +216,14 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         }
         __syncthreads();
     }
-    // Bartlett diagonal (chi^2 via Gamma)
-    const uint32_t NB = 64u * d;
+    // Bartlett diagonal and the normals were drawn by variates_kernel: the normals sit in
+    // W above the diagonal (zero below), the mean's eps in eps[s], the chi-square roots
+    // in bart[s]
     double* W = p_W + (size_t)s * d * d;
     for (int j = tid; j < d; j += nt) {
-        double df = nun - d + (j + 1);
-        double lg = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, 0.5 * df);
-        Bd[j] = sqrt(2.0 * exp(lg));
-    }
-    // every normal of the slot, one Box-Muller per pair: normal q = r*d + c (r < c) goes
-    // to W[r][c], where the back substitution of column c reads it before overwriting
-    // it; normal d*d + j (the mean's eps_j) goes to acc[j]; W below the diagonal is 0
-    const int npair = (d * d + d + 1) / 2;
-    for (int pq = tid; pq < npair; pq += nt) {
-        uint32_t w[4];
-        key.block((uint32_t)s, TAG_PARAM, NB + (uint32_t)pq, w);
-        const double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
-        const double rr = sqrt(-2.0 * log(u1)), ang = 6.283185307179586 * u2;
-        for (int o = 0; o < 2; ++o) {
-            const int q = 2 * pq + o;
-            const double nv = o ? rr * sin(ang) : rr * cos(ang);
-            if (q < d * d) {
-                const int r = q / d, cidx = q % d;
-                W[q] = r < cidx ? nv : 0.0;
-            } else if (q < d * d + d) {
-                acc[q - d * d] = nv;
-            }
-        }
+        Bd[j] = bart[(size_t)s * d + j];
+        acc[j] = eps[(size_t)s * d + j];
+        xb[j] = 1.0 / A[j * d + j];  // reuse: reciprocal of U's diagonal
     }
     __syncthreads();
     // W = U^-T B, column c by back substitution (U^T upper-triangular)
@@ -195,7 +231,7 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         for (int r = c; r >= 0; --r) {
             double t = (r == c) ? Bd[c] : W[r * d + c];
             for (int m = r + 1; m <= c; ++m) t -= A[m * d + r] * W[m * d + c];
-            W[r * d + c] = t / A[r * d + r];
+            W[r * d + c] = t * xb[r];
         }
     }
     __syncthreads();
@@ -294,11 +330,19 @@ __global__ void derive_kernel(int kind, int d, int tf32, const int* dK, const do
 static StatView make_sv(dpmm_ctx* c) { return StatView{c->stats, c->st}; }
 
 cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
+    VarArgs a{make_sv(c), c->dK, c->diter, seed, c->alpha, c->nu0, c->kind, c->K_max, c->kind == DPMM_PRIOR_NIW,
+              c->p_W, c->eps, c->bart, c->lgs};
+    const int d = c->d;
+    const int per_slot = c->kind == DPMM_PRIOR_NIW ? (d * d + d + 1) / 2 + d : 0;
+    const int per = std::max(per_slot, 3 * c->K_max + 1);
+    dim3 grid((per + 127) / 128, 3 * c->K_max + 1);
+    prof_begin(c, "variates");
+    variates_kernel<<<grid, 128, 0, c->stream>>>(a);
+    prof_end(c, "variates");
     prof_begin(c, "weights");
-    weights_kernel<<<1, 1024, sizeof(double) * (3 * c->K_max + 1), c->stream>>>(make_sv(c), c->dK, c->diter, seed,
-                                                                               c->alpha, c->p_logw, c->cweights);
+    weights_kernel<<<1, 1024, 0, c->stream>>>(c->dK, c->lgs, c->p_logw, c->cweights);
     prof_end(c, "weights");
-    c->nlaunch += 1;
+    c->nlaunch += 2;
     return cudaGetLastError();
 }
 
@@ -311,9 +355,9 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         }
         NiwPrior pr{c->kappa0, c->nu0, c->center + c->d, c->center + 2 * c->d};
         prof_begin(c, "niw_params");
-        niw_params_kernel<<<3 * c->K_max, 128, sm, c->stream>>>(make_sv(c), c->shift_stats, pr, c->dK, c->diter, seed,
-                                                               c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c,
-                                                               c->derr);
+        niw_params_kernel<<<3 * c->K_max, 128, sm, c->stream>>>(make_sv(c), c->shift_stats, pr, c->dK, c->eps,
+                                                               c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW,
+                                                               c->p_c, c->derr);
         prof_end(c, "niw_params");
         c->nlaunch += 1;
     } else {
