@@ -32,7 +32,7 @@ DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32"}
 METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
 # ncu DRAM bytes (read + write) per point of the label kernel, from the capture summarised in
 # profiles/labels_tc_gauss_d32.md; must be re-taken (or removed) whenever that kernel changes
-TRAFFIC_BYTES_PER_POINT = {("labels_tc", "gauss_d32"): (256.168192e6 + 8.592640e6) / 2e6}
+TRAFFIC_BYTES_PER_POINT = {}
 WORKLOADS = {
     "gauss_d32": dict(K_max=64),
     "gauss_d2": dict(K_max=64),

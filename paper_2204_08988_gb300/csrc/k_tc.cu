@@ -4,19 +4,22 @@
 // The Gaussian log-likelihood of every point under every cluster is one stacked
 // contraction: with Lambda_k = W_k W_k^T (W_k upper-triangular), y_k = x W_k and
 // b_k = mu_k^T W_k, log N(x; mu_k, Lambda_k^-1) = c'_k - 1/2 ||y_k - b_k||^2.  So
-// Y = X [W_1 ... W_K] (N x d times d x Kd) runs as tcgen05.mma (TF32 operands,
-// FP32 accumulation in tensor memory), and the epilogue adds log pi_k and the
+// Y - B = X [W_1 ... W_K] - 1 [b_1 ... b_K] runs as tcgen05.mma (TF32 operands, FP32
+// accumulation in tensor memory): four K steps over X and one more step that
+// multiplies a constant tile of ones by -b (split as two exact TF32 values, so the
+// subtraction keeps FP32 precision).  The epilogue adds log pi_k and the
 // log-determinant (c_k), takes the squared norm of each d-wide block, and draws
 // z_i = argmax_k (s_ik + G_ik) by Gumbel-max with Philox (tag Z, block k/2, word
 // 0 or 2).  Gumbels are drawn only for clusters that can still win: a cluster whose
 // score plus the largest possible FP32 Gumbel is below the best perturbed score seen
 // so far is skipped, which leaves the argmax unchanged.
 //
-// CTA roles (320 threads, one CTA per SM, persistent over 128-point tiles):
-//   warp 0    : TMA producer (X tiles, 128 rows x 128 B, SWIZZLE_128B, 3 stages)
-//   warp 1    : TMEM allocation (512 columns) and the single-thread MMA issue
-//   warps 2-9 : epilogue, two warps per TMEM lane quarter, each taking every other
-//               cluster of a chunk; the two halves merge their argmax per point.
+// CTA roles (576 threads, one CTA per SM, persistent over 128-point tiles):
+//   warp 0     : TMA producer (X tiles, 128 rows x 128 B, SWIZZLE_128B, 3 stages)
+//   warp 1     : TMEM allocation (512 columns) and the single-thread MMA issue
+//   warps 2-17 : epilogue, four warps (parts) per TMEM lane quarter, part p taking
+//                clusters p, p + 4, ... of a chunk; the parts exchange their running
+//                maxima before drawing and then merge their argmax per point.
 // The factor image of all clusters is copied once into shared memory (pre-swizzled
 // by tc_prepare).  Accumulators are double-buffered in TMEM (2 x 256 columns).
 // Every mbarrier wait is bounded; on timeout the kernel records DPMM_ETIMEOUT,
@@ -53,8 +56,8 @@ struct Args {
     const int* dK;
     const uint32_t* diter;
     uint64_t seed;
-    const void* img;  // factor image: rows (k * dn + j) x 128 B, swizzled
-    const float* qb;  // b_k[j] = (mu_k^T W_k)_j, slot 3k
+    const void* img;  // factor image: rows (k * dn + j) x 128 B, swizzled; at cap_rows * 128 B
+                      // the -b image: rows x 32 B, no swizzle (8-row groups of 256 B)
     const float* qc;  // c_k, slot 3k
     int32_t* z;
     int* overflow;    // set to 1 when K does not fit (the CUDA-core kernel then runs)
@@ -62,15 +65,17 @@ struct Args {
     double* scores;   // optional N x K scores (test hook), else null
 };
 
-// shared memory: [X stages | factor image | b table | c table | barriers]
+// shared memory: [X stages | factor image | -b image | ones tile | c table | barriers]
 template <int FMT, bool SCORES>
 __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_constant__ CUtensorMap xmap, Args a) {
+    static_assert(FMT == 2, "the ones tile and the -b image hold TF32 values");
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char* xs = base;                                   // XST x XBYTES
     unsigned char* bs = xs + XST * XBYTES;                      // cap_rows x 128
-    float* bt = (float*)(bs + (size_t)a.cap_rows * 128);        // Kmax x dn
-    float* ct = bt + (size_t)a.Kmax * a.dn;                     // Kmax
+    unsigned char* bb = bs + (size_t)a.cap_rows * 128;          // cap_rows x 32
+    float* ones = (float*)(bb + (size_t)a.cap_rows * 32);       // BM rows x 8, no swizzle
+    float* ct = ones + BM * 8;                                  // Kmax
     uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + a.Kmax) + 7) & ~(uintptr_t)7);
     uint64_t* full = bars;            // XST
     uint64_t* empty = full + XST;     // XST
@@ -79,10 +84,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     uint64_t* bload = tempty + 2;     // 1
     uint64_t* mfull = bload + 1;      // 2: parts 1.. published their argmax
     uint64_t* mempty = mfull + 2;     // 2: part 0 consumed them
+    uint64_t* sfull = mempty + 2;     // 2: every part published its running maximum
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float mbest[2][NPART - 1][BM];
     __shared__ int mz[2][NPART - 1][BM];
+    __shared__ float msmax[2][NPART][BM];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = *a.dK;
@@ -110,6 +117,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         for (int b = 0; b < 2; ++b) {
             mbar_init(&mfull[b], (NPART - 1) * 4 * 32);
             mbar_init(&mempty[b], 4 * 32);
+            mbar_init(&sfull[b], NEPI * 32);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -120,10 +128,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // b and c tables (zero beyond d)
-    for (int e = threadIdx.x; e < K * a.dn; e += blockDim.x) {
-        int k = e / a.dn, j = e % a.dn;
-        bt[e] = j < a.d ? a.qb[(size_t)3 * k * a.d + j] : 0.f;
+    // A operand of the fifth K step: every row (1, 1, 0, ..., 0); element (m, kk) of
+    // the no-swizzle layout at (m / 8) * 256 + (kk / 4) * 128 + (m % 8) * 16 + (kk % 4) * 4
+    for (int e = threadIdx.x; e < BM * 8; e += blockDim.x) {
+        const int m = e >> 3, kk = e & 7;
+        ones[(m >> 3) * 64 + (kk >> 2) * 32 + (m & 7) * 4 + (kk & 3)] = kk < 2 ? 1.f : 0.f;
     }
     for (int k = threadIdx.x; k < K; k += blockDim.x) ct[k] = a.qc[3 * k];
     fence_before();
@@ -135,11 +144,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     if (warp == 0) {
         if (lane == 0) {
             // factor image, once
-            const uint32_t bbytes = (uint32_t)rows_pad * 128u;
-            mbar_expect_tx(bload, bbytes);
+            const uint32_t bbytes = (uint32_t)rows_pad * 128u, nbytes = (uint32_t)rows_pad * 32u;
+            mbar_expect_tx(bload, bbytes + nbytes);
             for (uint32_t off = 0; off < bbytes; off += 32768u) {
                 uint32_t n = min(32768u, bbytes - off);
                 bulk_load(bs + off, (const unsigned char*)a.img + off, n, bload);
+            }
+            const unsigned char* nsrc = (const unsigned char*)a.img + (size_t)a.cap_rows * 128;
+            for (uint32_t off = 0; off < nbytes; off += 32768u) {
+                uint32_t n = min(32768u, nbytes - off);
+                bulk_load(bb + off, nsrc + off, n, bload);
             }
             int64_t it = 0;
             bool ok = true;
@@ -175,11 +189,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                     const int nclus = min(a.NC, K - c * a.NC);
                     const int n = (nclus * a.dn + 15) / 16 * 16;
                     const uint32_t ba = saddr(bs + (size_t)c * a.NC * a.dn * 128);
+                    const uint32_t nb = saddr(bb + (size_t)c * a.NC * a.dn * 32);
                     const uint32_t id = idesc(n, FMT);
                     const int ksteps = 4;  // 128-byte rows in 32-byte MMA steps
 #pragma unroll
                     for (int kk = 0; kk < ksteps; ++kk)
                         mma<FMT>(tmem + (uint32_t)(b * 256), sdesc(xa + kk * 32), sdesc(ba + kk * 32), id, kk > 0);
+                    mma<FMT>(tmem + (uint32_t)(b * 256), sdesc_ns(saddr(ones)), sdesc_ns(nb), id, true);  // - b
                     mma_commit(&tfull[b]);
                 }
                 if (!ok) break;
@@ -250,21 +266,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                         const int k = c * a.NC + cc;
                         float y[32];
                         tmem_ld32(cbase + (uint32_t)(cc * 32), y);
-                        consider(k, sqdist32(y, bt + (size_t)k * 32));
+                        consider(k, sqsum32(y));
                     }
                 } else {
                     for (int cc = part; cc < nclus; cc += NPART) {
                         const int k = c * a.NC + cc;
-                        const float* bk = bt + (size_t)k * a.dn;
                         float q0 = 0.f, q1 = 0.f;
                         for (int j0 = 0; j0 < a.dn; j0 += 8) {
                             float y[8];
                             tmem_ld8(cbase + (uint32_t)(cc * a.dn + j0), y);
 #pragma unroll
                             for (int j = 0; j < 8; j += 2) {
-                                const float t0 = y[j] - bk[j0 + j], t1 = y[j + 1] - bk[j0 + j + 1];
-                                q0 = fmaf(t0, t0, q0);
-                                q1 = fmaf(t1, t1, q1);
+                                q0 = fmaf(y[j], y[j], q0);
+                                q1 = fmaf(y[j + 1], y[j + 1], q1);
                             }
                         }
                         consider(k, q0 + q1);
@@ -274,14 +288,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
-            const float lim = smax - WINDOW;
+            // the parts exchange their running maxima: only candidates within WINDOW of
+            // the row's overall maximum can win, so usually one part draws once.  Slot sl
+            // is reused two tiles later; every reader of it has arrived on the other
+            // slot's barrier in between, so no second barrier is needed.
+            const int sl = (int)(it & 1);
+            const uint32_t use = (uint32_t)((it >> 1) & 1);
+            msmax[sl][part][r] = smax;
+            mbar_arrive(&sfull[sl]);
+            if (!mbar_wait(&sfull[sl], use, abort)) { ok = false; break; }
+            float gmax = msmax[sl][0][r];
+#pragma unroll
+            for (int p2 = 1; p2 < NPART; ++p2) gmax = fmaxf(gmax, msmax[sl][p2][r]);
+            const float lim = gmax - WINDOW;
             if (cn > 0 && cs0 > lim) draw(ck0, cs0);
             if (cn > 1 && cs1 > lim) draw(ck1, cs1);
             if (cn > 2 && cs2 > lim) draw(ck2, cs2);
             if (cn > 3 && cs3 > lim) draw(ck3, cs3);
             // merge the parts: the larger perturbed score wins, the lower k on a tie
-            const int sl = (int)(it & 1);
-            const uint32_t use = (uint32_t)((it >> 1) & 1);
             if (part > 0) {
                 if (!mbar_wait(&mempty[sl], use ^ 1u, abort)) { ok = false; break; }
                 mbest[sl][part - 1][r] = best;
@@ -318,18 +342,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
 }
 
 // factor image: row n = k * dn + j holds W_k[l][j], l = 0..31 (zero beyond d), in the
-// 128-byte swizzle pattern: 16-byte chunk c of row n sits at chunk c ^ (n & 7).
-__global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const float* qW, int rows_cap, float* img) {
+// 128-byte swizzle pattern: 16-byte chunk c of row n sits at chunk c ^ (n & 7).  At
+// byte offset rows_cap * 128 follows the -b image (no swizzle, 32 B per row, element
+// (n, l) at (n / 8) * 256 + (l / 4) * 128 + (n % 8) * 16 + (l % 4) * 4): row n holds
+// (-b_hi, -b_lo, 0, ..., 0), where b = sum_m mu_m W_k[m][j] is formed in FP64 with
+// the factor as the tensor cores see it, b_hi = tf32(b) and b_lo = tf32(b - b_hi).
+__global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const double* pW, const double* pmu,
+                                int rows_cap, float* img) {
     const int K = *dK;
     const int rows = (K * dn + 15) / 16 * 16;
     const int64_t total = (int64_t)min(rows, rows_cap) * 32;
+    float* nb = img + (size_t)rows_cap * 32;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int n = (int)(e / 32), l = (int)(e % 32);
         const int k = n / dn, j = n % dn;
+        const bool live = k < K && k < Kmax && j < d;
+        const double* W = pW + (size_t)3 * k * d * d;
         float v = 0.f;
-        if (k < K && k < Kmax && j < d && l < d) v = round_tf32(qW[((size_t)3 * k * d + l) * d + j]);
+        if (live && l < d) v = round_tf32((float)W[(size_t)l * d + j]);
         const int chunk = (l >> 2) ^ (n & 7);
         img[(size_t)n * 32 + chunk * 4 + (l & 3)] = v;
+        if (l < 8) {
+            float bv = 0.f;
+            if (live && l < 2) {
+                const double* mu = pmu + (size_t)3 * k * d;
+                double bj = 0.0;
+                for (int m = 0; m <= j; ++m) bj += mu[m] * (double)round_tf32((float)W[(size_t)m * d + j]);
+                const float hi = round_tf32((float)bj);
+                bv = l == 0 ? -hi : -round_tf32((float)(bj - (double)hi));
+            }
+            nb[(size_t)(n >> 3) * 64 + (l >> 2) * 32 + (n & 7) * 4 + (l & 3)] = bv;
+        }
     }
 }
 
@@ -361,12 +404,13 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     q.dn = (c->d + 7) / 8 * 8;
     q.NC = 256 / q.dn;
     while ((q.NC * q.dn) % 16) --q.NC;
-    const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)c->K_max * (q.dn + 1) * 4 + 32 * 8 + 64;
-    const size_t limit = 227 * 1024 - 8192;  // leave room for the kernel's static shared memory (7 KB)
-    size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * 128;
+    const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 4 + 32 * 8 + 64;
+    const size_t limit = 227 * 1024 - 12288;  // leave room for the kernel's static shared memory (11 KB)
+    const size_t per_row = 128 + 32;          // factor row and -b row
+    size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * per_row;
     size_t cap = std::min(want, limit - fixed);
-    q.cap_rows = (int)(cap / 128 / 16 * 16);
-    q.smem = fixed + (size_t)q.cap_rows * 128;
+    q.cap_rows = (int)(cap / per_row / 16 * 16);
+    q.smem = fixed + (size_t)q.cap_rows * per_row;
     if (q.smem < 120 * 1024) q.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     return q;
 }
@@ -386,7 +430,7 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
     if (c->kind == DPMM_PRIOR_DIRICHLET) return mult_supported(c) ? mult_prepare(c) : cudaSuccess;
     if (c->prec != DPMM_PREC_TF32) return cudaSuccess;
     TcCfg q = tc_cfg(c);
-    const size_t bytes = (size_t)q.cap_rows * 128;
+    const size_t bytes = (size_t)q.cap_rows * (128 + 32);
     if (!c->tc_img || c->tc_img_bytes < bytes) {
         if (c->tc_img) cudaFree(c->tc_img);
         c->tc_img = nullptr;
@@ -395,7 +439,7 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
         c->tc_img_bytes = bytes;
         cudaMemset(c->tc_img, 0, bytes);
     }
-    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->q_W, q.cap_rows,
+    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->p_W, c->p_mu, q.cap_rows,
                                                     (float*)c->tc_img);
     c->nlaunch += 1;
     return cudaGetLastError();
@@ -432,7 +476,6 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
     a.diter = c->diter;
     a.seed = seed;
     a.img = c->tc_img;
-    a.qb = c->q_b;
     a.qc = c->q_c;
     a.z = c->z;
     a.overflow = c->tc_flag;

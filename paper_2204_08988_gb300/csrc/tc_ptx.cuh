@@ -60,6 +60,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// Shared-memory matrix descriptor, K-major operand without swizzle: 8-row x 16-byte
+// core matrices stored contiguously (128 B each); the two core matrices of a K = 8
+// (TF32) step are 128 B apart (leading-dimension offset), 8-row groups 256 B apart
+// (stride-dimension offset).
+__device__ __forceinline__ uint64_t sdesc_ns(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)0 << 61);
+}
 // Instruction descriptor: D FP32, A and B TF32 (kind::tf32, format 2) or BF16
 // (kind::f16, format 1), both K-major, M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc(int n, int fmt) {
@@ -132,19 +140,15 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* va,
     }
 }
 
-// squared distance of a 32-wide block to b (four independent chains)
-__device__ __forceinline__ float sqdist32(const float* y, const float* b) {
-    const float4* b4 = (const float4*)b;
+// squared norm of a 32-wide block (four independent chains)
+__device__ __forceinline__ float sqsum32(const float* y) {
     float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
 #pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) {
-        const float4 bb = b4[j4];
-        const float t0 = y[4 * j4] - bb.x, t1 = y[4 * j4 + 1] - bb.y, t2 = y[4 * j4 + 2] - bb.z,
-                    t3 = y[4 * j4 + 3] - bb.w;
-        q0 = fmaf(t0, t0, q0);
-        q1 = fmaf(t1, t1, q1);
-        q2 = fmaf(t2, t2, q2);
-        q3 = fmaf(t3, t3, q3);
+    for (int j = 0; j < 32; j += 4) {
+        q0 = fmaf(y[j], y[j], q0);
+        q1 = fmaf(y[j + 1], y[j + 1], q1);
+        q2 = fmaf(y[j + 2], y[j + 2], q2);
+        q3 = fmaf(y[j + 3], y[j + 3], q3);
     }
     return (q0 + q1) + (q2 + q3);
 }
