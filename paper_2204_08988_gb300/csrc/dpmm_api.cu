@@ -289,7 +289,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     A(&c->tot, sizeof(int) * (K_max + 1));
     c->records_bytes = sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
     A(&c->records, c->records_bytes);
-    A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
+    A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1 + 6 * (size_t)K_max));
     A(&c->relabel, sizeof(int) * 4 * K_max);
     A(&c->acc, sizeof(int) * ((size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
     A(&c->center, sizeof(double) * (2 * (size_t)d + (size_t)d * d));

@@ -80,8 +80,8 @@ __device__ inline double d_normal(const Key& k, uint32_t c0, uint32_t tag, uint3
     k.block(c0, tag, base + q / 2, w);
     double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
     double r = sqrt(-2.0 * log(u1));
-    double ang = 6.283185307179586 * u2;
-    return (q & 1) ? r * sin(ang) : r * cos(ang);
+    // sin / cos of 2 pi u2 as sinpi / cospi of 2 u2: no argument reduction by pi
+    return (q & 1) ? r * sinpi(2.0 * u2) : r * cospi(2.0 * u2);
 }
 
 // log of a Gamma(a, 1) variate (Marsaglia & Tsang, ACM TOMS 2000), log space.
@@ -225,7 +225,8 @@ struct dpmm_ctx {
     size_t records_bytes = 0;
 
     // split/merge scratch
-    double* Ltab = nullptr;  // 3 K_max + K_max (K_max - 1)/2 log marginals
+    double* Ltab = nullptr;  // 3 K_max + K_max (K_max - 1)/2 log marginals, 1 spare, then per slot
+                             // lgamma(n_s) and lgamma(alpha/2 + n_s) (6 K_max)
     int* relabel = nullptr;  // 4 K_max
     int* acc = nullptr;      // K_max + K_max (K_max - 1)/2 accept flags of the split/merge proposals
     double* canon = nullptr; // canonical (n, xbar, C) per cluster and sub-cluster: 3 K_max x (1 + d + d d)

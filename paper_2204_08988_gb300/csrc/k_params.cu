@@ -93,11 +93,13 @@ __global__ void variates_kernel(VarArgs a) {
         uint32_t w[4];
         key.block((uint32_t)s, TAG_PARAM, NB + (uint32_t)q, w);
         const double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
-        const double rr = sqrt(-2.0 * log(u1)), ang = 6.283185307179586 * u2;
+        const double rr = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);  // sin and cos of 2 pi u2
         double* W = a.W + (size_t)s * d * d;
         for (int o = 0; o < 2; ++o) {
             const int qq = 2 * q + o;
-            const double nv = o ? rr * sin(ang) : rr * cos(ang);
+            const double nv = o ? rr * sn : rr * cs;
             if (qq < d * d) {
                 const int r = qq / d, c = qq % d;
                 W[qq] = r < c ? nv : 0.0;
@@ -116,23 +118,25 @@ __global__ void variates_kernel(VarArgs a) {
 }
 
 // (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2):
-// normalisation of the Gamma draws made by variates_kernel.
-__global__ void __launch_bounds__(1024) weights_kernel(const int* dK, const double* lgs, double* logw,
-                                                       double* cweights) {
-    __shared__ double sh[32];
-    const int K = *dK;
+// normalisation of the Gamma draws made by variates_kernel.  One warp: a wider block
+// would only multiply the FP64 reduction work on GB300's narrow FP64 pipe.
+__global__ void __launch_bounds__(32) weights_kernel(const int* dK, const double* lgs, double* logw,
+                                                     double* cweights) {
+    const int K = *dK, lane = threadIdx.x;
     double lmax = -INFINITY;
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) lmax = fmax(lmax, lgs[k]);
-    lmax = block_reduce_max(lmax, sh);
+    for (int k = lane; k <= K; k += 32) lmax = fmax(lmax, lgs[k]);
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     double s = 0.0;
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) s += exp(lgs[k] - lmax);
-    const double lse = lmax + log(block_reduce_sum(s, sh));
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        logw[3 * k] = lgs[k] - lse;
-        cweights[k] = exp(lgs[k] - lse);
+    for (int k = lane; k <= K; k += 32) s += exp(lgs[k] - lmax);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double lse = lmax + log(s);
+    for (int k = lane; k < K; k += 32) {
+        const double lw = lgs[k] - lse;
+        logw[3 * k] = lw;
+        cweights[k] = exp(lw);
         const double gl = lgs[K + 1 + 2 * k], gr = lgs[K + 2 + 2 * k];
         const double m = fmax(gl, gr);
-        const double l2 = m + log(exp(gl - m) + exp(gr - m));
+        const double l2 = m + log1p(exp(-fabs(gl - gr)));
         logw[3 * k + 1] = gl - l2;
         logw[3 * k + 2] = gr - l2;
     }
@@ -147,55 +151,69 @@ struct NiwPrior {
 // (c), (d): (mu, Lambda) ~ NIW posterior of one slot.  Lambda = W W^T with
 // W = U^-T B (Psi_n = U U^T, B upper-triangular Bartlett factor of Wishart(nu_n, I):
 // B_jj^2 ~ chi^2(nu_n - d + j), j = 1..d, N(0,1) above the diagonal);
-// mu = m_n + W^-T eps / sqrt(kappa_n).  Dynamic shared memory: d*d + 4*d doubles.
+// mu = m_n + W^-T eps / sqrt(kappa_n).
+//
+// GB300's FP64 pipe retires about two operations per clock per SM, so the kernel keeps
+// FP64 work off the serial paths: every division becomes a reciprocal formed once,
+// the pivots use rsqrt, the triangular solve for W runs right-looking (one parallel
+// update of the rows above per step) in shared memory.  Dynamic shared memory:
+// d*d (+ d*d when W fits) + 6*d doubles.
 __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPrior pr, const int* dK,
                                   const double* eps, const double* bart, const double* logw, double* p_mu,
-                                  double* p_W, double* p_logdetW, double* p_c, int* derr) {
+                                  double* p_W, double* p_logdetW, double* p_c, int* derr, int w_in_smem) {
     extern __shared__ double smem[];
     const int d = sv.L.d;
     const int K = *dK;
     const int s = blockIdx.x;
     if (s >= 3 * K) return;
     const int k = s / 3, h = s % 3 - 1;  // h = -1: the cluster
-    double* A = smem;             // d x d: Psi_n, then its Cholesky factor U (lower)
+    double* A = smem;             // d x d: Psi_n (lower), then its Cholesky factor U
     double* mn = A + d * d;       // d
     double* xb = mn + d;          // d
-    double* Bd = xb + d;          // d: Bartlett diagonal
-    double* acc = Bd + d;         // d
+    double* Bd = xb + d;          // d: Bartlett diagonal, then v
+    double* acc = Bd + d;         // d: eps
+    double* rd = acc + d;         // d: 1 / U_jj
+    double* rw = rd + d;          // d: 1 / W_jj
+    double* Wg = p_W + (size_t)s * d * d;
+    double* W = w_in_smem ? rw + d : Wg;  // d x d working copy
     __shared__ double sh[32];
-    __shared__ double s_n, s_kn, s_nun;
+    __shared__ double s_n, s_rn, s_kn, s_nun, s_rkn;
     const int tid = threadIdx.x, nt = blockDim.x;
 
     if (tid == 0) {
-        double n = sv.count(k, h);
+        const double n = sv.count(k, h);
         s_n = n;
+        s_rn = n > 0 ? 1.0 / n : 0.0;
         s_kn = pr.kappa0 + n;
         s_nun = pr.nu0 + n;
+        s_rkn = 1.0 / s_kn;
     }
     __syncthreads();
-    const double n = s_n, kn = s_kn, nun = s_nun;
+    const double n = s_n, rn = s_rn, kn = s_kn, rkn = s_rkn;
     const double* sh_k = shift_stats + (size_t)k * d;
     for (int j = tid; j < d; j += nt) {
-        double xbar = n > 0 ? sh_k[j] + sv.m(k, h, j, d) / n : 0.0;
+        const double xbar = n > 0 ? sh_k[j] + sv.m(k, h, j, d) * rn : 0.0;
         xb[j] = xbar;
-        mn[j] = (pr.kappa0 * pr.m0s[j] + n * xbar) / kn;
+        mn[j] = (pr.kappa0 * pr.m0s[j] + n * xbar) * rkn;
+        Bd[j] = bart[(size_t)s * d + j];
+        acc[j] = eps[(size_t)s * d + j];
     }
+    if (w_in_smem)  // the normals above the diagonal (zero below), drawn by variates_kernel
+        for (int e = tid; e < d * d; e += nt) W[e] = Wg[e];
     __syncthreads();
-    // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n
-    const double f = n > 0 ? pr.kappa0 * n / kn : 0.0;
+    // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n;
     // lower triangle only: the factorisation below reads nothing else
+    const double f = n > 0 ? pr.kappa0 * n * rkn : 0.0;
     for (int e = tid; e < d * d; e += nt) {
-        int j = e / d, l = e % d;
+        const int j = e / d, l = e % d;
         if (l > j) continue;
         double C = 0.0;
-        if (n > 0) {
-            double s1a = sv.m(k, h, l, d), s1b = sv.m(k, h, j, d);
-            C = sv.m(k, h, l, j) - s1a * s1b / n;
-        }
+        if (n > 0) C = sv.m(k, h, l, j) - sv.m(k, h, l, d) * sv.m(k, h, j, d) * rn;
         A[e] = pr.psi0[e] + C + f * (xb[j] - pr.m0s[j]) * (xb[l] - pr.m0s[l]);
     }
     __syncthreads();
-    // right-looking Cholesky, A = U U^T (lower)
+    // right-looking Cholesky, A = U U^T (lower); the pivot's reciprocal square root is
+    // formed once and shared
     for (int j = 0; j < d; ++j) {
         if (tid == 0) {
             double v = A[j * d + j];
@@ -203,42 +221,45 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
                 atomicExch(derr, (int)DPMM_ENUMERIC);
                 v = 1e-300;
             }
-            A[j * d + j] = sqrt(v);
+            const double r = rsqrt(v);
+            A[j * d + j] = v * r;
+            rd[j] = r;
         }
         __syncthreads();
-        const double rj = 1.0 / A[j * d + j];
+        const double rj = rd[j];
         for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] *= rj;
         __syncthreads();
-        int m = d - j - 1;
+        const int m = d - j - 1;
         for (int e = tid; e < m * m; e += nt) {
-            int i = j + 1 + e / m, l = j + 1 + e % m;
+            const int i = j + 1 + e / m, l = j + 1 + e % m;
             if (l <= i) A[i * d + l] -= A[i * d + j] * A[l * d + j];
         }
         __syncthreads();
     }
-    // Bartlett diagonal and the normals were drawn by variates_kernel: the normals sit in
-    // W above the diagonal (zero below), the mean's eps in eps[s], the chi-square roots
-    // in bart[s]
-    double* W = p_W + (size_t)s * d * d;
-    for (int j = tid; j < d; j += nt) {
-        Bd[j] = bart[(size_t)s * d + j];
-        acc[j] = eps[(size_t)s * d + j];
-        xb[j] = 1.0 / A[j * d + j];  // reuse: reciprocal of U's diagonal
+    // U^T W = B, right-looking: after step r, row r of W (unscaled) is final and the rows
+    // above are updated with it; the rows are scaled by 1 / U_rr at the end
+    for (int j = tid; j < d; j += nt) W[j * d + j] = Bd[j];
+    __syncthreads();
+    for (int r = d - 1; r > 0; --r) {
+        const int w = d - r;  // columns c = r .. d-1
+        const double rr = rd[r];
+        for (int e = tid; e < r * w; e += nt) {
+            const int i = e / w, c = r + e % w;  // row i < r
+            W[i * d + c] -= A[r * d + i] * rr * W[r * d + c];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < d * d; e += nt) {
+        const int r = e / d, c = e % d;
+        if (c >= r) W[e] *= rd[r];
     }
     __syncthreads();
-    // W = U^-T B, column c by back substitution (U^T upper-triangular)
-    for (int c = tid; c < d; c += nt) {
-        for (int r = c; r >= 0; --r) {
-            double t = (r == c) ? Bd[c] : W[r * d + c];
-            for (int m = r + 1; m <= c; ++m) t -= A[m * d + r] * W[m * d + c];
-            W[r * d + c] = t * xb[r];
-        }
-    }
+    for (int j = tid; j < d; j += nt) rw[j] = 1.0 / W[j * d + j];
     __syncthreads();
     // W^T v = eps (forward substitution) by warp 0, lane m keeps sum_{j<m} W[j][m] v_j;
     // mu = m_n + v / sqrt(kappa_n)
-    double* mu = p_mu + (size_t)s * d;
     if (tid < 32) {
+        const int ns = (d + 31) >> 5;
         double am[8];  // m = tid + 32 i, d <= 256
 #pragma unroll
         for (int i = 0; i < 8; ++i) am[i] = 0.0;
@@ -250,19 +271,23 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
                 if (i == slot) mine = am[i];
             double vj = 0.0;
             if (tid == own) {
-                vj = (acc[j] - mine) / W[j * d + j];
+                vj = (acc[j] - mine) * rw[j];
                 Bd[j] = vj;  // reuse as v
             }
             vj = __shfl_sync(0xffffffffu, vj, own);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int m = tid + 32 * i;
-                if (m > j && m < d) am[i] += W[j * d + m] * vj;
+                if (i < ns && m > j && m < d) am[i] += W[j * d + m] * vj;
             }
         }
     }
     __syncthreads();
-    for (int j = tid; j < d; j += nt) mu[j] = mn[j] + Bd[j] / sqrt(kn);
+    double* mu = p_mu + (size_t)s * d;
+    const double rsk = rsqrt(kn);
+    for (int j = tid; j < d; j += nt) mu[j] = mn[j] + Bd[j] * rsk;
+    if (w_in_smem)
+        for (int e = tid; e < d * d; e += nt) Wg[e] = W[e];
     double ld = 0.0;
     for (int j = tid; j < d; j += nt) ld += log(W[j * d + j]);
     ld = block_reduce_sum(ld, sh);
@@ -340,7 +365,7 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
     variates_kernel<<<grid, 128, 0, c->stream>>>(a);
     prof_end(c, "variates");
     prof_begin(c, "weights");
-    weights_kernel<<<1, 1024, 0, c->stream>>>(c->dK, c->lgs, c->p_logw, c->cweights);
+    weights_kernel<<<1, 32, 0, c->stream>>>(c->dK, c->lgs, c->p_logw, c->cweights);
     prof_end(c, "weights");
     c->nlaunch += 2;
     return cudaGetLastError();
@@ -348,7 +373,10 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
 
 cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
     if (c->kind == DPMM_PRIOR_NIW) {
-        size_t sm = sizeof(double) * ((size_t)c->d * c->d + 4 * c->d);
+        const size_t dd = (size_t)c->d * c->d;
+        size_t sm = sizeof(double) * (2 * dd + 6 * c->d);
+        const int w_in_smem = sm <= 200 * 1024;
+        if (!w_in_smem) sm = sizeof(double) * (dd + 6 * c->d);
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(niw_params_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
@@ -357,7 +385,7 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         prof_begin(c, "niw_params");
         niw_params_kernel<<<3 * c->K_max, 128, sm, c->stream>>>(make_sv(c), c->shift_stats, pr, c->dK, c->eps,
                                                                c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW,
-                                                               c->p_c, c->derr);
+                                                               c->p_c, c->derr, w_in_smem);
         prof_end(c, "niw_params");
         c->nlaunch += 1;
     } else {

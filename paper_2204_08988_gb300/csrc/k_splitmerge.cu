@@ -12,6 +12,8 @@
 //              RESUB); gated: it returns at once when nothing changed.
 #include <math.h>
 
+#include <cmath>
+
 #include "dpmm_internal.cuh"
 
 namespace dpmm {
@@ -24,6 +26,7 @@ struct SMArgs {
     const double* psi0;         // d x d
     const double* beta;         // d
     double kappa0, nu0, logdet_psi0, alpha;
+    double log_alpha, lg_alpha, lg_half_alpha;  // log a, lgamma(a), lgamma(a / 2), from the host
     int kind, K_max;
     const int* dK;
 };
@@ -39,6 +42,10 @@ __device__ inline double lmvgamma(double x, int d) {
     for (int j = 1; j <= d; ++j) s += lgamma(x + 0.5 * (1 - j));
     return s;
 }
+
+// per-slot lgamma table after the log marginals: lg[2 s] = lgamma(n_s),
+// lg[2 s + 1] = lgamma(alpha / 2 + n_s)
+__host__ __device__ inline size_t lg_offset(int K_max) { return 3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1; }
 
 __device__ inline void pair_of(int p, int K, int& k1, int& k2) {
     int r = 0, off = 0;
@@ -70,6 +77,10 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         h = -1;
     }
     double* out = Ltab + (e < 3 * K ? e : 3 * a.K_max + (e - 3 * K));
+    if (e < 3 * K && (tid == 32 || tid == 33)) {  // the slot's lgamma terms for the Hastings ratios
+        const double ns = smv(a, k1, h, d, d);
+        Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
+    }
     if (a.kind == DPMM_PRIOR_DIRICHLET) {
         double sb = 0.0, sc = 0.0, acc = 0.0;
         for (int j = tid; j < d; j += nt) {
@@ -78,8 +89,6 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
             sc += c;
             acc += lgamma(a.beta[j] + c) - lgamma(a.beta[j]);
         }
-        sb = 0.0;
-        for (int j = 0; j < d; ++j) sb += a.beta[j];
         double tot = 0.0;
         // sum counts and lgamma terms over the block (fixed order)
         for (int o = 16; o > 0; o >>= 1) {
@@ -94,6 +103,8 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         __syncthreads();
         if (tid == 0) {
             double c = 0.0, l = 0.0;
+            sb = 0.0;
+            for (int j = 0; j < d; ++j) sb += a.beta[j];
             for (int w = 0; w < (nt + 31) / 32; ++w) {
                 c += shc[w];
                 l += sha[w];
@@ -103,38 +114,46 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         }
         return;
     }
-    double* A = smem;          // d x d
+    double* A = smem;          // d x d (lower triangle)
     double* xb = A + d * d;    // merged mean
     double* x1 = xb + d;
     double* x2 = x1 + d;
-    if (tid == 0) {
-        s_n1 = smv(a, k1, h, d, d);
-        s_n2 = k2 >= 0 ? smv(a, k2, -1, d, d) : 0.0;
-        s_n = s_n1 + s_n2;
+    __shared__ double s_r1, s_r2, s_rn, s_w12;
+    if (tid == 0) {  // reciprocals once: FP64 division is slow on GB300's narrow FP64 pipe
+        const double n1 = smv(a, k1, h, d, d), n2 = k2 >= 0 ? smv(a, k2, -1, d, d) : 0.0, n = n1 + n2;
+        s_n1 = n1;
+        s_n2 = n2;
+        s_n = n;
+        s_r1 = n1 > 0 ? 1.0 / n1 : 0.0;
+        s_r2 = n2 > 0 ? 1.0 / n2 : 0.0;
+        s_rn = n > 0 ? 1.0 / n : 0.0;
+        s_w12 = n1 * n2 * s_rn;
     }
     __syncthreads();
-    const double n1 = s_n1, n2 = s_n2, n = s_n;
+    const double n1 = s_n1, n2 = s_n2, n = s_n, r1 = s_r1, r2 = s_r2, rn = s_rn, w12 = s_w12;
     for (int j = tid; j < d; j += nt) {
-        double m1 = n1 > 0 ? a.shift_stats[(size_t)k1 * d + j] + smv(a, k1, h, j, d) / n1 : 0.0;
-        double m2 = (k2 >= 0 && n2 > 0) ? a.shift_stats[(size_t)k2 * d + j] + smv(a, k2, -1, j, d) / n2 : 0.0;
+        double m1 = n1 > 0 ? a.shift_stats[(size_t)k1 * d + j] + smv(a, k1, h, j, d) * r1 : 0.0;
+        double m2 = (k2 >= 0 && n2 > 0) ? a.shift_stats[(size_t)k2 * d + j] + smv(a, k2, -1, j, d) * r2 : 0.0;
         x1[j] = m1;
         x2[j] = m2;
-        xb[j] = n > 0 ? (n1 * m1 + n2 * m2) / n : 0.0;
+        xb[j] = n > 0 ? (n1 * m1 + n2 * m2) * rn : 0.0;
     }
     __syncthreads();
     const double kn = a.kappa0 + n, nun = a.nu0 + n;
     const double f = n > 0 ? a.kappa0 * n / kn : 0.0;
     for (int q = tid; q < d * d; q += nt) {
-        int j = q / d, l = q % d, lo = min(j, l), hi = max(j, l);
+        const int j = q / d, l = q % d;  // l <= j: the factorisation reads nothing else
+        if (l > j) continue;
         double C = 0.0;
-        if (n1 > 0) C += smv(a, k1, h, lo, hi) - smv(a, k1, h, lo, d) * smv(a, k1, h, hi, d) / n1;
+        if (n1 > 0) C += smv(a, k1, h, l, j) - smv(a, k1, h, l, d) * smv(a, k1, h, j, d) * r1;
         if (k2 >= 0 && n2 > 0) {
-            C += smv(a, k2, -1, lo, hi) - smv(a, k2, -1, lo, d) * smv(a, k2, -1, hi, d) / n2;
-            if (n1 > 0) C += (n1 * n2 / n) * (x1[j] - x2[j]) * (x1[l] - x2[l]);
+            C += smv(a, k2, -1, l, j) - smv(a, k2, -1, l, d) * smv(a, k2, -1, j, d) * r2;
+            if (n1 > 0) C += w12 * (x1[j] - x2[j]) * (x1[l] - x2[l]);
         }
         A[q] = a.psi0[q] + C + f * (xb[j] - a.m0s[j]) * (xb[l] - a.m0s[l]);
     }
     __syncthreads();
+    __shared__ double s_rj;
     for (int j = 0; j < d; ++j) {
         if (tid == 0) {
             double v = A[j * d + j];
@@ -142,14 +161,17 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
                 atomicExch(derr, (int)DPMM_ENUMERIC);
                 v = 1e-300;
             }
-            A[j * d + j] = sqrt(v);
+            const double r = rsqrt(v);
+            A[j * d + j] = v * r;
+            s_rj = r;
         }
         __syncthreads();
-        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] /= A[j * d + j];
+        const double rj = s_rj;
+        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] *= rj;
         __syncthreads();
-        int m = d - j - 1;
+        const int m = d - j - 1;
         for (int q = tid; q < m * m; q += nt) {
-            int i = j + 1 + q / m, l = j + 1 + q % m;
+            const int i = j + 1 + q / m, l = j + 1 + q % m;
             if (l <= i) A[i * d + l] -= A[i * d + j] * A[l * d + j];
         }
         __syncthreads();
@@ -185,14 +207,15 @@ __global__ void hastings_kernel(SMArgs a, const double* Ltab, const uint32_t* di
         for (int q = 0; q < k; ++q) c += live(q);
         return c;
     };
-    const double la = log(a.alpha), al = a.alpha;
+    const double la = a.log_alpha, al = a.alpha;
+    const double* lg = Ltab + lg_offset(a.K_max);
     if (e < K) {
         const int k = e;
-        const double nl = smv(a, k, 0, d, d), nr = smv(a, k, 1, d, d), nk = nl + nr;
+        const double nl = smv(a, k, 0, d, d), nr = smv(a, k, 1, d, d);
         int ok = 0;
         if (live(k) && nl >= 1 && nr >= 1) {
-            const double lH = la + lgamma(nl) + Ltab[3 * k + 1] + lgamma(nr) + Ltab[3 * k + 2] - lgamma(nk) -
-                              Ltab[3 * k];
+            const double lH = la + lg[2 * (3 * k + 1)] + Ltab[3 * k + 1] + lg[2 * (3 * k + 2)] + Ltab[3 * k + 2] -
+                              lg[2 * (3 * k)] - Ltab[3 * k];
             ok = log(d_uniform(key, (uint32_t)cid(k), TAG_SPLIT, 0)) < lH;
         }
         acc[k] = ok;
@@ -203,9 +226,9 @@ __global__ void hastings_kernel(SMArgs a, const double* Ltab, const uint32_t* di
         int ok = 0;
         if (live(k1) && live(k2)) {
             const double n1 = smv(a, k1, -1, d, d), n2 = smv(a, k2, -1, d, d), nm = n1 + n2;
-            const double lH = lgamma(nm) - la - lgamma(n1) - lgamma(n2) + Ltab[3 * a.K_max + p] - Ltab[3 * k1] -
-                              Ltab[3 * k2] + lgamma(al) - lgamma(al + nm) + lgamma(0.5 * al + n1) +
-                              lgamma(0.5 * al + n2) - 2.0 * lgamma(0.5 * al);
+            const double lH = lgamma(nm) - la - lg[2 * (3 * k1)] - lg[2 * (3 * k2)] + Ltab[3 * a.K_max + p] -
+                              Ltab[3 * k1] - Ltab[3 * k2] + a.lg_alpha - lgamma(al + nm) + lg[2 * (3 * k1) + 1] +
+                              lg[2 * (3 * k2) + 1] - 2.0 * a.lg_half_alpha;
             ok = log(d_uniform(key, (uint32_t)cid(k1), TAG_MERGE, (uint32_t)cid(k2))) < lH;
         }
         acc[a.K_max + p] = ok;
@@ -410,6 +433,9 @@ static SMArgs sm_args(dpmm_ctx* c) {
     a.nu0 = c->nu0;
     a.logdet_psi0 = c->logdet_psi0;
     a.alpha = c->alpha;
+    a.log_alpha = std::log(c->alpha);
+    a.lg_alpha = std::lgamma(c->alpha);
+    a.lg_half_alpha = std::lgamma(0.5 * c->alpha);
     a.kind = c->kind;
     a.K_max = c->K_max;
     a.dK = c->dK;
@@ -436,7 +462,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     if (sm_enabled) {
         const int items = c->K_max + c->K_max * (c->K_max - 1) / 2;
         prof_begin(c, "hastings");
-        hastings_kernel<<<(items + 127) / 128, 128, 0, c->stream>>>(s, c->Ltab, c->diter, seed, labels_ran ? 1 : 0,
+        hastings_kernel<<<(items + 31) / 32, 32, 0, c->stream>>>(s, c->Ltab, c->diter, seed, labels_ran ? 1 : 0,
                                                                    c->acc);
         prof_end(c, "hastings");
         c->nlaunch += 1;
