@@ -210,6 +210,7 @@ struct dpmm_ctx {
     float *q_mu = nullptr, *q_W = nullptr, *q_c = nullptr, *q_b = nullptr, *q_logtheta = nullptr;
     void* tc_img = nullptr;  // tensor-core operand image of the cluster parameters
     size_t tc_img_bytes = 0;
+    void* tcs_img = nullptr;  // tensor-core sub-cluster factor images (K_max x 10 KB)
     double* cweights = nullptr;  // K_max: pi_k of the last sweep (linear)
     double* eps = nullptr;       // 3 K_max x d: normals of the drawn means
     double* bart = nullptr;      // 3 K_max x d: Bartlett diagonal (chi-square roots)
@@ -264,6 +265,9 @@ cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed);
 cudaError_t launch_advance(dpmm_ctx* c);
 bool tc_supported(const dpmm_ctx* c);
 cudaError_t tc_prepare(dpmm_ctx* c);
+bool substats_tc_supported(const dpmm_ctx* c);
+cudaError_t substats_tc_prepare(dpmm_ctx* c);
+cudaError_t launch_substats_tc(dpmm_ctx* c, uint64_t seed, int draw, const int* gate);
 
 // profiling helpers (no-ops unless enabled)
 void prof_begin(dpmm_ctx* c, const char* name);

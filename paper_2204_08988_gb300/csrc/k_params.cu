@@ -407,6 +407,7 @@ cudaError_t launch_derive(dpmm_ctx* c) {
     c->nlaunch += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && tc_supported(c)) e = tc_prepare(c);
+    if (e == cudaSuccess && substats_tc_supported(c)) e = substats_tc_prepare(c);
     return e;
 }
 

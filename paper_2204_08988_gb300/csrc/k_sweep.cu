@@ -1038,7 +1038,8 @@ static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const
         return e;
     }
     const bool fast = c->prec != DPMM_PREC_FP64_PLAIN && c->kind == DPMM_PRIOR_NIW && c->d <= 64 && c->st.nblk <= 256;
-    if (fast && c->d <= 32) e = c->xdt == 2 ? substats_f32_t<32, __nv_bfloat16>(c, seed, draw, gate)
+    if (substats_tc_supported(c)) e = launch_substats_tc(c, seed, draw, gate);
+    else if (fast && c->d <= 32) e = c->xdt == 2 ? substats_f32_t<32, __nv_bfloat16>(c, seed, draw, gate)
                                              : substats_f32_t<32, float>(c, seed, draw, gate);
     else if (fast) e = c->xdt == 2 ? substats_f32_t<64, __nv_bfloat16>(c, seed, draw, gate)
                                    : substats_f32_t<64, float>(c, seed, draw, gate);

@@ -113,6 +113,46 @@ def test_tc_chain_finds_clusters():
     g.close()
 
 
+def _round_tf32(a):
+    """Round to nearest (ties away) to TF32, as the TF32 path stores the data."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    fin = (u & 0x7F800000) != 0x7F800000
+    r = np.where(fin, (u + np.uint32(0x1000)) & np.uint32(0xFFFFE000), u)
+    return r.view(np.float32)
+
+
+@pytest.mark.parametrize("N,d,K", [(70_001, 32, 7), (9_999, 8, 5), (12_345, 20, 4)])
+def test_tc_statistics_match_recount(N, d, K):
+    """Sub-label and statistics step on the tensor cores (hi/lo TF32 split, FP32
+    accumulation): after every sweep (including the re-count that follows accepted
+    splits and merges), counts are exact and first and second moments agree with an
+    FP64 recount of the GPU's own labels to FP32 accuracy.  Small N spreads each
+    cluster over many ranges and tiles with ragged ends."""
+    from paper_2204_08988_gb300 import synth
+
+    X, _ = synth.gaussian_mixture(N, d, K, 6.0, seed=N + 1)
+    g = P.DPMM(0, d, 32, 10.0, prec=P.PREC_TF32, burn_out=2, **_prior(d))
+    g.set_data(X)
+    # the TF32 path stores round_tf32(x - column mean) and reports moments of x
+    c = X.astype(np.float64).mean(0)
+    X64 = _round_tf32((X.astype(np.float64) - c).astype(np.float32)).astype(np.float64) + c
+    for t in range(10):
+        g.sweep(1, 41)
+        K_now = g.K
+        z, zb = g.labels()
+        n, sx, sxx = g.stats()
+        assert n[0::3].sum() == N and np.array_equal(n[0::3], n[1::3] + n[2::3])
+        for k in range(K_now):
+            for h in range(2):
+                sel = (z == k) & (zb == h)
+                assert n[3 * k + 1 + h] == sel.sum(), (t, k, h)
+                c = max(1, sel.sum())
+                assert np.allclose(sx[3 * k + 1 + h], X64[sel].sum(0), rtol=1e-5, atol=1e-3 * c ** 0.5), (t, k, h)
+                assert np.allclose(sxx[3 * k + 1 + h], X64[sel].T @ X64[sel], rtol=1e-5, atol=1e-2 * c ** 0.5), (t, k, h)
+    assert g.K > 1
+    g.close()
+
+
 # ---------------------------------------------------------------- multinomial (BF16)
 
 def _mult_setup(N, d, K, seed, K_max=64, draws=100):
