@@ -65,7 +65,7 @@ struct Args {
     double* scores;   // optional N x K scores (test hook), else null
 };
 
-// shared memory: [X stages | factor image | -b image | ones tile | c table | barriers]
+// shared memory: [X stages | factor image | -b image | ones tile | scores | c table | barriers]
 template <int FMT, bool SCORES>
 __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_constant__ CUtensorMap xmap, Args a) {
     static_assert(FMT == 2, "the ones tile and the -b image hold TF32 values");
@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     unsigned char* bs = xs + XST * XBYTES;                      // cap_rows x 128
     unsigned char* bb = bs + (size_t)a.cap_rows * 128;          // cap_rows x 32
     float* ones = (float*)(bb + (size_t)a.cap_rows * 32);       // BM rows x 8, no swizzle
-    float* ct = ones + BM * 8;                                  // Kmax
+    float* sbuf = ones + BM * 8;                                // (cap_rows / dn) clusters x BM
+    float* ct = sbuf + (size_t)(a.cap_rows / a.dn) * BM;        // Kmax
     uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + a.Kmax) + 7) & ~(uintptr_t)7);
     uint64_t* full = bars;            // XST
     uint64_t* empty = full + XST;     // XST
@@ -220,13 +221,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
             const int64_t i = t * BM + r;
-            // exact Gumbel-max with deferred draws: scores within WINDOW of the running
-            // maximum are kept as candidates (at most 4; beyond that a draw is made at
-            // once); all other clusters cannot win
-            float best = -INFINITY, smax = -INFINITY;
-            int zb = 0, cn = 0;
-            int ck0 = 0, ck1 = 0, ck2 = 0, ck3 = 0;
-            float cs0 = 0.f, cs1 = 0.f, cs2 = 0.f, cs3 = 0.f;
+            // exact Gumbel-max: every part first scores its clusters (kept in shared
+            // memory) and tracks its maximum; after the parts exchange their maxima, only
+            // clusters within WINDOW of the row's maximum can win and get a Gumbel draw
+            float best = -INFINITY, pmax = -INFINITY;
+            int zb = 0;
+            float* sr = sbuf + r;  // score of cluster k at sr[k * BM]
             auto draw = [&](int k, float sc) {
                 uint32_t w[4];
                 key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
@@ -237,23 +237,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                     zb = k;
                 }
             };
-            auto consider = [&](int k, float q) {
+            auto score = [&](int k, float q) {
                 const float sc = ct[k] - 0.5f * q;
                 if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
                     if (i < a.N) a.scores[i * K + k] = (double)sc;
                 }
-                if (sc > smax) {
-                    if (sc > smax + WINDOW) cn = 0;  // every earlier candidate is now out of range
-                    smax = sc;
-                }
-                if (sc > smax - WINDOW) {
-                    if (cn == 0) { ck0 = k; cs0 = sc; }
-                    else if (cn == 1) { ck1 = k; cs1 = sc; }
-                    else if (cn == 2) { ck2 = k; cs2 = sc; }
-                    else if (cn == 3) { ck3 = k; cs3 = sc; }
-                    else draw(k, sc);
-                    cn = min(cn + 1, 4);
-                }
+                pmax = fmaxf(pmax, sc);
+                sr[k * BM] = sc;
             };
             for (int c = 0; c < nch; ++c, ++ch) {
                 const int b = (int)(ch & 1);
@@ -263,14 +253,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 const uint32_t cbase = tmem + lane_off + (uint32_t)(b * 256);
                 if (a.dn == 32) {  // 32-column loads never pass the block's own columns
                     for (int cc = part; cc < nclus; cc += NPART) {
-                        const int k = c * a.NC + cc;
                         float y[32];
                         tmem_ld32(cbase + (uint32_t)(cc * 32), y);
-                        consider(k, sqsum32(y));
+                        score(c * a.NC + cc, sqsum32(y));
                     }
                 } else {
                     for (int cc = part; cc < nclus; cc += NPART) {
-                        const int k = c * a.NC + cc;
                         float q0 = 0.f, q1 = 0.f;
                         for (int j0 = 0; j0 < a.dn; j0 += 8) {
                             float y[8];
@@ -281,30 +269,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                                 q1 = fmaf(y[j + 1], y[j + 1], q1);
                             }
                         }
-                        consider(k, q0 + q1);
+                        score(c * a.NC + cc, q0 + q1);
                     }
                 }
                 fence_before();
                 mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
-            // the parts exchange their running maxima: only candidates within WINDOW of
-            // the row's overall maximum can win, so usually one part draws once.  Slot sl
-            // is reused two tiles later; every reader of it has arrived on the other
-            // slot's barrier in between, so no second barrier is needed.
+            // the parts exchange their maxima.  Slot sl is reused two tiles later; every
+            // reader of it has arrived on the other slot's barrier in between, so no
+            // second barrier is needed.
             const int sl = (int)(it & 1);
             const uint32_t use = (uint32_t)((it >> 1) & 1);
-            msmax[sl][part][r] = smax;
+            msmax[sl][part][r] = pmax;
             mbar_arrive(&sfull[sl]);
             if (!mbar_wait(&sfull[sl], use, abort)) { ok = false; break; }
             float gmax = msmax[sl][0][r];
 #pragma unroll
             for (int p2 = 1; p2 < NPART; ++p2) gmax = fmaxf(gmax, msmax[sl][p2][r]);
             const float lim = gmax - WINDOW;
-            if (cn > 0 && cs0 > lim) draw(ck0, cs0);
-            if (cn > 1 && cs1 > lim) draw(ck1, cs1);
-            if (cn > 2 && cs2 > lim) draw(ck2, cs2);
-            if (cn > 3 && cs3 > lim) draw(ck3, cs3);
+            // this part's candidates: the first two are drawn below together with the
+            // other lanes' (usually one draw per warp), any further one at once
+            int k0 = -1, k1 = -1;
+            float s0 = 0.f, s1 = 0.f;
+            for (int k = part; k < K; k += NPART) {
+                const float sc = sr[k * BM];
+                if (sc > lim) {
+                    if (k0 < 0) { k0 = k; s0 = sc; }
+                    else if (k1 < 0) { k1 = k; s1 = sc; }
+                    else draw(k, sc);
+                }
+            }
+            if (k0 >= 0) draw(k0, s0);
+            if (k1 >= 0) draw(k1, s1);
             // merge the parts: the larger perturbed score wins, the lower k on a tie
             if (part > 0) {
                 if (!mbar_wait(&mempty[sl], use ^ 1u, abort)) { ok = false; break; }
@@ -406,11 +403,12 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     while ((q.NC * q.dn) % 16) --q.NC;
     const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 4 + 32 * 8 + 64;
     const size_t limit = 227 * 1024 - 12288;  // leave room for the kernel's static shared memory (11 KB)
-    const size_t per_row = 128 + 32;          // factor row and -b row
+    // factor row, -b row, and each cluster's 128 scores spread over its dn rows
+    const size_t per_row = 128 + 32 + (tc::BM * 4 + q.dn - 1) / q.dn;
     size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * per_row;
     size_t cap = std::min(want, limit - fixed);
     q.cap_rows = (int)(cap / per_row / 16 * 16);
-    q.smem = fixed + (size_t)q.cap_rows * per_row;
+    q.smem = fixed + (size_t)q.cap_rows * (128 + 32) + (size_t)(q.cap_rows / q.dn) * tc::BM * 4;
     if (q.smem < 120 * 1024) q.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     return q;
 }
