@@ -83,14 +83,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     uint64_t* tfull = empty + XST;    // 2
     uint64_t* tempty = tfull + 2;     // 2
     uint64_t* bload = tempty + 2;     // 1
-    uint64_t* mfull = bload + 1;      // 2: parts 1.. published their argmax
-    uint64_t* mempty = mfull + 2;     // 2: part 0 consumed them
-    uint64_t* sfull = mempty + 2;     // 2: every part published its running maximum
+    uint64_t* sfull = bload + 1;      // 2: every part published its two best scores
+    uint64_t* qbar = sfull + 2;       // 4: the parts of a lane quarter published their draws
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ float mbest[2][NPART - 1][BM];
-    __shared__ int mz[2][NPART - 1][BM];
-    __shared__ float msmax[2][NPART][BM];
+    __shared__ float xm1[2][NPART][BM], xm2[2][NPART][BM];  // per part: best and second score
+    __shared__ int xk1[2][NPART][BM];                         // per part: cluster of the best
+    __shared__ float mbest[2][NPART][BM];                     // per part: best perturbed score
+    __shared__ int mz[2][NPART][BM];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = *a.dK;
@@ -115,11 +115,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             mbar_init(&tempty[b], NEPI * 32);
         }
         mbar_init(bload, 1);
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&mfull[b], (NPART - 1) * 4 * 32);
-            mbar_init(&mempty[b], 4 * 32);
-            mbar_init(&sfull[b], NEPI * 32);
-        }
+        for (int b = 0; b < 2; ++b) mbar_init(&sfull[b], NEPI * 32);
+        for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART * 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -218,32 +215,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         const uint32_t iter = *a.diter;
         Key key{a.seed, iter, 0};
         int64_t ch = 0, it = 0;
+        uint32_t nq = 0;  // uses of this quarter's draw barrier (the same in its four parts)
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
             const int64_t i = t * BM + r;
-            // exact Gumbel-max: every part first scores its clusters (kept in shared
-            // memory) and tracks its maximum; after the parts exchange their maxima, only
-            // clusters within WINDOW of the row's maximum can win and get a Gumbel draw
-            float best = -INFINITY, pmax = -INFINITY;
-            int zb = 0;
+            // Exact Gumbel-max.  Every part scores its clusters (kept in shared memory)
+            // and tracks its two best scores.  A cluster can win only if its score is
+            // within WINDOW of the row's best; when no other cluster is, the best one
+            // wins whatever the Gumbel values, and no draw is needed.  Otherwise each
+            // part draws for its clusters within the window and part 0 merges.
+            float m1 = -INFINITY, m2 = -INFINITY;
+            int k1 = 0;
             float* sr = sbuf + r;  // score of cluster k at sr[k * BM]
-            auto draw = [&](int k, float sc) {
-                uint32_t w[4];
-                key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
-                const float u = u01_f32((k & 1) ? w[2] : w[0]);
-                const float v = sc - __logf(-logf(u));
-                if (v > best || (v == best && k < zb)) {
-                    best = v;
-                    zb = k;
-                }
-            };
             auto score = [&](int k, float q) {
                 const float sc = ct[k] - 0.5f * q;
                 if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
                     if (i < a.N) a.scores[i * K + k] = (double)sc;
                 }
-                pmax = fmaxf(pmax, sc);
                 sr[k * BM] = sc;
+                const bool gt = sc > m1;
+                m2 = gt ? m1 : fmaxf(m2, sc);
+                k1 = gt ? k : k1;
+                m1 = gt ? sc : m1;
             };
             for (int c = 0; c < nch; ++c, ++ch) {
                 const int b = (int)(ch & 1);
@@ -276,52 +269,80 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
-            // the parts exchange their maxima.  Slot sl is reused two tiles later; every
-            // reader of it has arrived on the other slot's barrier in between, so no
-            // second barrier is needed.
+            // Slot sl is reused two tiles later; every reader of it has arrived on the
+            // other slot's barrier in between, so no second barrier is needed.
             const int sl = (int)(it & 1);
             const uint32_t use = (uint32_t)((it >> 1) & 1);
-            msmax[sl][part][r] = pmax;
+            xm1[sl][part][r] = m1;
+            xm2[sl][part][r] = m2;
+            xk1[sl][part][r] = k1;
             mbar_arrive(&sfull[sl]);
             if (!mbar_wait(&sfull[sl], use, abort)) { ok = false; break; }
-            float gmax = msmax[sl][0][r];
+            // the row's best and second-best scores (every part computes the same)
+            float g1 = xm1[sl][0][r], g2 = xm2[sl][0][r];
+            int gk = xk1[sl][0][r];
 #pragma unroll
-            for (int p2 = 1; p2 < NPART; ++p2) gmax = fmaxf(gmax, msmax[sl][p2][r]);
-            const float lim = gmax - WINDOW;
-            // this part's candidates: the first two are drawn below together with the
-            // other lanes' (usually one draw per warp), any further one at once
-            int k0 = -1, k1 = -1;
-            float s0 = 0.f, s1 = 0.f;
-            for (int k = part; k < K; k += NPART) {
-                const float sc = sr[k * BM];
-                if (sc > lim) {
-                    if (k0 < 0) { k0 = k; s0 = sc; }
-                    else if (k1 < 0) { k1 = k; s1 = sc; }
-                    else draw(k, sc);
+            for (int p2 = 1; p2 < NPART; ++p2) {
+                const float o1 = xm1[sl][p2][r], o2 = xm2[sl][p2][r];
+                const int ok1 = xk1[sl][p2][r];
+                if (o1 > g1 || (o1 == g1 && ok1 < gk)) {
+                    g2 = fmaxf(g1, o2);
+                    g1 = o1;
+                    gk = ok1;
+                } else {
+                    g2 = fmaxf(g2, o1);
                 }
             }
-            if (k0 >= 0) draw(k0, s0);
-            if (k1 >= 0) draw(k1, s1);
-            // merge the parts: the larger perturbed score wins, the lower k on a tie
-            if (part > 0) {
-                if (!mbar_wait(&mempty[sl], use ^ 1u, abort)) { ok = false; break; }
-                mbest[sl][part - 1][r] = best;
-                mz[sl][part - 1][r] = zb;
-                mbar_arrive(&mfull[sl]);
-            } else {
-                if (!mbar_wait(&mfull[sl], use, abort)) { ok = false; break; }
-#pragma unroll
-                for (int p2 = 0; p2 < NPART - 1; ++p2) {
-                    const float ob = mbest[sl][p2][r];
-                    const int oz = mz[sl][p2][r];
-                    if (ob > best || (ob == best && oz < zb)) {
-                        best = ob;
-                        zb = oz;
+            const float lim = g1 - WINDOW;
+            const bool need = !(g2 <= lim);  // another cluster might win: draw
+            if (__any_sync(0xffffffffu, need)) {  // the same answer in the four parts
+                float best = -INFINITY;
+                int zb = 0;
+                auto draw = [&](int k, float sc) {
+                    uint32_t w[4];
+                    key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
+                    const float u = u01_f32((k & 1) ? w[2] : w[0]);
+                    const float v = sc - __logf(-logf(u));
+                    if (v > best || (v == best && k < zb)) {
+                        best = v;
+                        zb = k;
                     }
+                };
+                if (need) {
+                    // the first two candidates are drawn below together with the other
+                    // lanes', any further one at once
+                    int c0 = -1, c1 = -1;
+                    float s0 = 0.f, s1 = 0.f;
+                    for (int k = part; k < K; k += NPART) {
+                        const float sc = sr[k * BM];
+                        if (sc > lim) {
+                            if (c0 < 0) { c0 = k; s0 = sc; }
+                            else if (c1 < 0) { c1 = k; s1 = sc; }
+                            else draw(k, sc);
+                        }
+                    }
+                    if (c0 >= 0) draw(c0, s0);
+                    if (c1 >= 0) draw(c1, s1);
                 }
-                mbar_arrive(&mempty[sl]);
-                if (i < a.N) a.z[i] = zb;
+                mbest[sl][part][r] = best;
+                mz[sl][part][r] = zb;
+                mbar_arrive(&qbar[quarter]);
+                if (!mbar_wait(&qbar[quarter], (uint32_t)(nq & 1), abort)) { ok = false; break; }
+                ++nq;
+                if (part == 0 && need) {
+#pragma unroll
+                    for (int p2 = 1; p2 < NPART; ++p2) {
+                        const float ob = mbest[sl][p2][r];
+                        const int oz = mz[sl][p2][r];
+                        if (ob > best || (ob == best && oz < zb)) {
+                            best = ob;
+                            zb = oz;
+                        }
+                    }
+                    gk = zb;
+                }
             }
+            if (part == 0 && i < a.N) a.z[i] = gk;
         }
         if (!ok) {
             atomicExch(a.derr, (int)DPMM_ETIMEOUT);
@@ -402,7 +423,7 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     q.NC = 256 / q.dn;
     while ((q.NC * q.dn) % 16) --q.NC;
     const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 4 + 32 * 8 + 64;
-    const size_t limit = 227 * 1024 - 12288;  // leave room for the kernel's static shared memory (11 KB)
+    const size_t limit = 227 * 1024 - 24576;  // leave room for the kernel's static shared memory (22 KB)
     // factor row, -b row, and each cluster's 128 scores spread over its dn rows
     const size_t per_row = 128 + 32 + (tc::BM * 4 + q.dn - 1) / q.dn;
     size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * per_row;
