@@ -21,10 +21,11 @@
 //           most GT tiles; the epilogue adds it into FP32 accumulators in shared memory
 //           and, after the range's last tile of the cluster, writes record g + k in
 //           FP64 (the 4 x 4 block layout the combine step sums).
-// CTA roles (480 threads, one CTA per SM, persistent):
-//   warp 0      : gather of each tile's 128 rows by cp.async (16-byte pieces, written in
-//                 the 128-byte swizzle pattern the MMA reads; completion on an mbarrier)
-//                 and the bulk copy of each new cluster's sub-cluster factor image
+// CTA roles (512 threads, one CTA per SM, persistent):
+//   warps 0, 15 : gather of each tile's 128 rows by cp.async (16-byte pieces, written in
+//                 the 128-byte swizzle pattern the MMA reads; completion on an mbarrier),
+//                 64 rows each; warp 0 also bulk-copies each new cluster's sub-cluster
+//                 factor image
 //   warp 1      : TMEM allocation (512 columns) and the single-thread score MMA issue
 //   warps 2-5   : score warps, one thread per point (TMEM lane): z-bar
 //   warps 6-13  : operand warps, lane j = feature j: the transposed hi / lo operands of
@@ -59,7 +60,8 @@ constexpr int GT = 4;                          // tiles per tensor-memory accumu
 constexpr int NS = 4, NB = 8;                  // score warps, operand warps
 constexpr int W_S = 2, W_B = 2 + NS;           // first score warp, first operand warp
 constexpr int W_T = W_B + NB;                  // statistics MMA warp
-constexpr int NTHREADS = 32 * (3 + NS + NB);
+constexpr int W_P = W_T + 1;                   // second producer warp
+constexpr int NTHREADS = 32 * (4 + NS + NB);
 constexpr uint32_t TMEM_COLS = 512;            // score 2 x 64; statistics 2 x 80 at 128, 256
 constexpr uint32_t SCORE_COL = 0, STAT_COL = 128;
 
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
     float* F = (float*)(SB + 2 * SB_BUF);                 // FR x FS accumulators (row = D row)
     uint8_t* hq = (uint8_t*)(F + FR * FS);                // 2 x BM sub-labels (2: padding row)
     __shared__ uint64_t bars[2 * XST + 15];
-    uint64_t* xfull = bars;           // XST (32 cp.async arrivals)
+    uint64_t* xfull = bars;           // XST (64 cp.async arrivals: two producer warps)
     uint64_t* xempty = bars + XST;    // XST (operand threads)
     uint64_t* pfull = bars + 2 * XST; // 2
     uint64_t* pempty = pfull + 2;     // 2 (MMA commit)
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int b = 0; b < XST; ++b) {
-            mbar_init(&xfull[b], 32);
+            mbar_init(&xfull[b], 64);
             mbar_init(&xempty[b], NB * 32);
         }
         for (int b = 0; b < 2; ++b) {
@@ -227,14 +229,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
     int cnt, k, g;
     bool newrun, last, gfirst, gend;
 
-    if (warp == 0) {
-        // ------------------------------------------------------------ producer
+    if (warp == 0 || warp == W_P) {
+        // ------------------------------------------------------------ producers
+        // Two warps gather 64 rows each; the point indices of the next tile are loaded
+        // while the current one is issued.  Warp 0 also stages the factor images.
+        const int pw = warp == 0 ? 0 : 1;
         bool ok = true;
         int it = 0, cidx = -1;
+        Tiles tn = tl;  // one tile ahead: its indices are loaded early
+        int64_t np0;
+        int ncnt, nk, ng;
+        bool nnew, nlast, ngf, nge;
+        bool have = tn.next(np0, ncnt, nk, ng, nnew, nlast, ngf, nge);
+        int pn0 = 0, pn1 = 0;  // rows 64 pw + lane and 64 pw + 32 + lane of the next tile
+        auto load_idx = [&]() {
+            const int r0 = 64 * pw + lane, r1 = r0 + 32;
+            pn0 = a.idx[np0 + (r0 < ncnt ? r0 : 0)];
+            pn1 = a.idx[np0 + (r1 < ncnt ? r1 : 0)];
+        };
+        if (have) load_idx();
         while (ok && tl.next(p0, cnt, k, g, newrun, last, gfirst, gend)) {
+            const int pt0 = pn0, pt1 = pn1;
+            have = tn.next(np0, ncnt, nk, ng, nnew, nlast, ngf, nge);
+            if (have) load_idx();
             if (newrun) {
                 ++cidx;
-                if (DRAW) {
+                if (DRAW && pw == 0) {
                     const int pb = cidx & 1;
                     if (lane == 0) {
                         ok = mbar_wait(&pempty[pb], (uint32_t)(((cidx >> 1) & 1) ^ 1), abort);
@@ -251,25 +271,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
             if (lane == 0) ok = mbar_wait(&xempty[s], (uint32_t)(((it / XST) & 1) ^ 1), abort);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
-            // lane l holds the points of rows l, l + 32, l + 64, l + 96 (padding rows
-            // repeat the first point and are masked later)
-            int pt[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = lane + 32 * u;
-                pt[u] = a.idx[p0 + (r < cnt ? r : 0)];
-            }
-            // step t copies rows 4t .. 4t + 3, eight lanes (16-byte chunks) per row
+            // step t copies rows 64 pw + 4t .. + 3, eight lanes (16-byte chunks) per row
+            // (padding rows repeat the first point and are masked later)
             unsigned char* xt = xs + (size_t)s * XBYTES;
             const int c = lane & 7;
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const int r = 4 * t + (lane >> 3);
-                int ptr = pt[0];
-#pragma unroll
-                for (int u = 1; u < 4; ++u)
-                    if ((t >> 3) == u) ptr = pt[u];
-                const int pr = __shfl_sync(0xffffffffu, ptr, r & 31);
+            for (int t = 0; t < 16; ++t) {
+                const int rr = 4 * t + (lane >> 3);  // row within this warp's 64
+                const int pr = __shfl_sync(0xffffffffu, t < 8 ? pt0 : pt1, rr & 31);
+                const int r = 64 * pw + rr;
                 cp_async16(xt + r * 128 + ((c ^ (r & 7)) << 4), a.X + (size_t)pr * 32 + c * 4);
             }
             cp_async_arrive(&xfull[s]);
