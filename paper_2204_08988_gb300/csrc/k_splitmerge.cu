@@ -248,6 +248,7 @@ struct DecArgs {
     int* counters;     // [0] splits [1] merges [2] rejected (K_max) [3] removed [4] changed
     double* shift_new; // K_max x d
     float* shift32;
+    int* derr;
 };
 
 #define DEC_KMAX 1024
@@ -354,6 +355,13 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
                 src[nid] = k;
                 ++nid;
             }
+        if (nid == 0) {  // no cluster holds a point: the statistics disagree with the labels
+            atomicExch(a.derr, (int)DPMM_ENUMERIC);
+            newid[0] = 0;
+            src[0] = 0;
+            live[0] = 1;
+            nid = 1;
+        }
         // ages: survivors one sweep older, clusters created by a split or merge start at 0
         for (int q = 0; q < nid; ++q) {
             const int k = src[q];
@@ -404,13 +412,23 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
 }
 
 __global__ void relabel_kernel(int64_t N, const int* relabel, int Kmax, const int* gate, const uint32_t* diter,
-                               uint64_t seed, int32_t* z, uint8_t* zbar) {
+                               uint64_t seed, int32_t* z, uint8_t* zbar, int* derr) {
     if (*gate == 0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int k = z[i], h = zbar[i];
+    int k = z[i];
+    const int h = zbar[i];
+    if ((unsigned)k >= (unsigned)Kmax) {  // never for consistent state: keep memory safe, report
+        atomicExch(derr, (int)DPMM_ENUMERIC);
+        k = 0;
+    }
     const int mode = relabel[2 * Kmax + k];
-    z[i] = h ? relabel[Kmax + k] : relabel[k];
+    int nz = h ? relabel[Kmax + k] : relabel[k];
+    if (nz < 0) {  // a point in a cluster counted as empty
+        atomicExch(derr, (int)DPMM_ENUMERIC);
+        nz = 0;
+    }
+    z[i] = nz;
     if (mode == 1) zbar[i] = 0;
     else if (mode == 2) zbar[i] = 1;
     else if (mode == 3) {
@@ -484,6 +502,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     a.counters = c->counters;
     a.shift_new = c->shift_new;
     a.shift32 = c->shift32;
+    a.derr = c->derr;
     prof_begin(c, "decision");
     const int dyn = 32 * 1024;
     cudaError_t ea = cudaFuncSetAttribute(decision_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
@@ -497,7 +516,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
 cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed) {
     prof_begin(c, "relabel");
     relabel_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->relabel, c->K_max, c->counters + 4,
-                                                                         c->diter, seed, c->z, c->zbar);
+                                                                         c->diter, seed, c->z, c->zbar, c->derr);
     prof_end(c, "relabel");
     c->nlaunch += 1;
     cudaError_t e = cudaGetLastError();

@@ -142,7 +142,10 @@ __global__ void hist_kernel(const int32_t* z, int64_t N, int T_tiles, int Kmax, 
     for (int k = threadIdx.x; k < Kmax; k += blockDim.x) cnt[k] = 0;
     __syncthreads();
     int64_t i = (int64_t)t * 256 + threadIdx.x;
-    if (i < N) atomicAdd(&cnt[z[i]], 1);
+    if (i < N) {
+        const int k = z[i];
+        if ((unsigned)k < (unsigned)Kmax) atomicAdd(&cnt[k], 1);  // labels are always in range
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < Kmax; k += blockDim.x) hist[(size_t)k * T_tiles + t] = cnt[k];
 }
@@ -211,8 +214,9 @@ __global__ void scatter_kernel(const int32_t* z, int64_t N, int T_tiles, const i
     __syncthreads();
     const int64_t i = (int64_t)t * 256 + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const bool live = i < N;
-    const int k = live ? z[i] : -1 - lane;  // dead lanes never match live ones
+    const int zi = i < N ? z[i] : -1;
+    const bool live = (unsigned)zi < (unsigned)Kmax;  // labels are always in range
+    const int k = live ? zi : -1 - lane;  // dead lanes never match live ones
     unsigned m = __match_any_sync(0xffffffffu, k);
     int r = __popc(m & ((1u << lane) - 1u));
     if (live && r == 0) wc[w * Kmax + k] = __popc(m);

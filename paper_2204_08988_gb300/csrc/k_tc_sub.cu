@@ -93,13 +93,14 @@ struct Args {
 struct Tiles {
     const int* st;
     int64_t N, R, pos, end;
-    int G, g, k, pk, pg, tir;
-    __device__ void init(const int* s, int64_t n, int64_t r, int G_) {
+    int G, K, g, k, pk, pg, tir;
+    __device__ void init(const int* s, int K_, int64_t n, int64_t r, int G_) {
         st = s;
+        K = K_;
         N = n;
         R = r;
         G = G_;
-        g = (int)blockIdx.x - (int)gridDim.x;
+        g = K_ >= 1 ? (int)blockIdx.x - (int)gridDim.x : G_;  // no cluster: no tile
         pos = end = 0;
         k = 0;
         pk = pg = -1;
@@ -114,8 +115,13 @@ struct Tiles {
             end = min(N, pos + R);
             k = 0;
         }
-        while ((int64_t)st[k + 1] <= pos) ++k;
+        while (k + 1 < K && (int64_t)st[k + 1] <= pos) ++k;
         const int64_t lim = min(end, (int64_t)st[k + 1]);
+        if (lim <= pos) {  // the starts do not cover the points (never for consistent state)
+            g = G;
+            pos = end = 0;
+            return false;
+        }
         cnt = (int)min((int64_t)BM, lim - pos);
         p0 = pos;
         kk = k;
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
     const uint32_t tmem = tmem_base;
     volatile int* abort = &abort_flag;
     Tiles tl;
-    tl.init(st, a.N, a.R, a.G);
+    tl.init(st, K, a.N, a.R, a.G);
     int64_t p0;
     int cnt, k, g;
     bool newrun, last, gfirst, gend;
