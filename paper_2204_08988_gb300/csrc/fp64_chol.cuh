@@ -1,0 +1,83 @@
+// fp64_chol.cuh -- FP64 building blocks of the parameter and split/merge steps: staging a
+// (sub-)cluster's statistics block in shared memory and a right-looking Cholesky
+// factorisation written for GB300's FP64 pipe (about two operations per clock per SM,
+// 64-cycle dependent latency): the only serial work per pivot is one reciprocal square
+// root; the trailing update has no square roots or divisions and issues its loads in
+// batches so that independent FMAs overlap.
+#pragma once
+#include "dpmm_internal.cuh"
+
+namespace dpmm {
+
+// out[e] = statistics entry e of slot (k, h) of the table S (E entries per sub-cluster);
+// h = -1 sums the two sub-clusters (the cluster).  Every thread of the block calls it.
+__device__ inline void stage_slot(const double* S, int E, int k, int h, double* out) {
+    const double* s0 = S + (size_t)(2 * k + (h < 0 ? 0 : h)) * E;
+    const double* s1 = S + (size_t)(2 * k + 1) * E;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) out[e] = h < 0 ? s0[e] + s1[e] : s0[e];
+}
+
+// Row i0 and column l0 (l0 <= i0) of entry e of a lower triangle enumerated row by row.
+__device__ inline void tri_index(int e, int& i0, int& l0) {
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if ((i + 1) * (i + 2) / 2 <= e) ++i;
+    if (i * (i + 1) / 2 > e) --i;
+    i0 = i;
+    l0 = e - i * (i + 1) / 2;
+}
+
+// In-place factorisation of the symmetric matrix whose lower triangle is in A (d x d,
+// row-major with row stride ld, shared memory; an odd ld keeps the column reads free of
+// bank conflicts).  Pivot j is v_j = the (j, j) entry of the Schur complement;
+// the update is A_il -= (A_ij / v_j) A_lj for j < l <= i, so column j keeps its unscaled
+// values.  On return piv[j] = v_j and rs[j] = 1 / sqrt(v_j): Psi = U U^T with
+// U_jj = sqrt(v_j), U_ij = A_ij rs[j] (i > j), and log|Psi| = sum_j log v_j.  A pivot
+// that is not positive (or NaN) sets *derr = DPMM_ENUMERIC and is replaced by 1e-300.
+// col (d doubles of shared memory) is scratch.  Every thread of the block calls it; two
+// barriers per pivot.  Each FP64 warp instruction costs the pipe about the same whether
+// or not its lanes are busy, so warp 0 forms the pivot and the scaled column (one lane
+// per row) and the update enumerates only the lower triangle, one FMA per entry.
+__device__ inline void chol_ldl(double* A, int d, int ld, double* piv, double* rs, double* col, int* derr) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < d; ++j) {
+        if (tid < 32) {
+            double v = A[j * ld + j];
+            if (!(v > 0.0)) {
+                if (tid == 0) atomicExch(derr, (int)DPMM_ENUMERIC);
+                v = 1e-300;
+            }
+            const double r = rsqrt(v), inv = r * r;
+            for (int i = j + 1 + tid; i < d; i += 32) col[i] = A[i * ld + j] * inv;
+            if (tid == 0) {
+                piv[j] = v;
+                rs[j] = r;
+            }
+        }
+        __syncthreads();
+        const int m = d - j - 1, tri = m * (m + 1) / 2;
+        for (int e0 = tid; e0 < tri; e0 += 4 * nt) {
+            double av[4], ci[4], cl[4];
+            int at[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * nt;
+                at[u] = -1;
+                if (e < tri) {
+                    int i0, l0;
+                    tri_index(e, i0, l0);
+                    const int i = j + 1 + i0, l = j + 1 + l0;
+                    at[u] = i * ld + l;
+                    av[u] = A[at[u]];
+                    ci[u] = col[i];
+                    cl[u] = A[l * ld + j];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (at[u] >= 0) A[at[u]] = fma(-ci[u], cl[u], av[u]);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace dpmm

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "dpmm_internal.cuh"
+#include "fp64_chol.cuh"
 
 namespace dpmm {
 
@@ -153,46 +154,56 @@ struct NiwPrior {
 // B_jj^2 ~ chi^2(nu_n - d + j), j = 1..d, N(0,1) above the diagonal);
 // mu = m_n + W^-T eps / sqrt(kappa_n).
 //
-// GB300's FP64 pipe retires about two operations per clock per SM, so the kernel keeps
-// FP64 work off the serial paths: every division becomes a reciprocal formed once,
-// the pivots use rsqrt, the triangular solve for W runs right-looking (one parallel
-// update of the rows above per step) in shared memory.  Dynamic shared memory:
-// d*d (+ d*d when W fits) + 6*d doubles.
+// GB300's FP64 pipe retires about two operations per clock per SM with a 64-cycle
+// dependent latency, so the kernel keeps FP64 work off the serial paths: the slot's
+// statistics are staged in shared memory, every division is a reciprocal formed once,
+// the factorisation (chol_ldl) takes one reciprocal square root per pivot, and the
+// triangular solve for W runs right-looking (one parallel update of the rows above per
+// step) in shared memory.  Dynamic shared memory: d*d + 7*d (+ E when staged) (+ d*d
+// when W fits) doubles.
 __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPrior pr, const int* dK,
                                   const double* eps, const double* bart, const double* logw, double* p_mu,
-                                  double* p_W, double* p_logdetW, double* p_c, int* derr, int w_in_smem) {
+                                  double* p_W, double* p_logdetW, double* p_c, int* derr, int w_in_smem,
+                                  int staged) {
     extern __shared__ double smem[];
-    const int d = sv.L.d;
+    const int d = sv.L.d, E = sv.L.E;
     const int K = *dK;
     const int s = blockIdx.x;
     if (s >= 3 * K) return;
     const int k = s / 3, h = s % 3 - 1;  // h = -1: the cluster
-    double* A = smem;             // d x d: Psi_n (lower), then its Cholesky factor U
-    double* mn = A + d * d;       // d
+    const int ld = d | 1;         // odd row stride: column reads without bank conflicts
+    double* A = smem;             // d x ld: Psi_n (lower), then the solve's multipliers
+    double* mn = A + d * ld;      // d
     double* xb = mn + d;          // d
     double* Bd = xb + d;          // d: Bartlett diagonal, then v
     double* acc = Bd + d;         // d: eps
     double* rd = acc + d;         // d: 1 / U_jj
     double* rw = rd + d;          // d: 1 / W_jj
+    double* piv = rw + d;         // d: pivots
+    double* S = piv + d;          // E: staged statistics
     double* Wg = p_W + (size_t)s * d * d;
-    double* W = w_in_smem ? rw + d : Wg;  // d x d working copy
+    double* W = w_in_smem ? S + (staged ? E : 0) : Wg;  // d x d working copy
     __shared__ double sh[32];
-    __shared__ double s_n, s_rn, s_kn, s_nun, s_rkn;
+    __shared__ double s_n, s_rn, s_kn, s_rkn;
     const int tid = threadIdx.x, nt = blockDim.x;
 
+    if (staged) {
+        stage_slot(sv.S, E, k, h, S);
+        __syncthreads();
+    }
+    auto M = [&](int j, int l) -> double { return staged ? S[sv.L.ent(j, l)] : sv.m(k, h, j, l); };
     if (tid == 0) {
-        const double n = sv.count(k, h);
+        const double n = M(d, d);
         s_n = n;
         s_rn = n > 0 ? 1.0 / n : 0.0;
         s_kn = pr.kappa0 + n;
-        s_nun = pr.nu0 + n;
         s_rkn = 1.0 / s_kn;
     }
     __syncthreads();
     const double n = s_n, rn = s_rn, kn = s_kn, rkn = s_rkn;
     const double* sh_k = shift_stats + (size_t)k * d;
     for (int j = tid; j < d; j += nt) {
-        const double xbar = n > 0 ? sh_k[j] + sv.m(k, h, j, d) * rn : 0.0;
+        const double xbar = n > 0 ? sh_k[j] + M(j, d) * rn : 0.0;
         xb[j] = xbar;
         mn[j] = (pr.kappa0 * pr.m0s[j] + n * xbar) * rkn;
         Bd[j] = bart[(size_t)s * d + j];
@@ -204,37 +215,22 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n;
     // lower triangle only: the factorisation below reads nothing else
     const double f = n > 0 ? pr.kappa0 * n * rkn : 0.0;
-    for (int e = tid; e < d * d; e += nt) {
-        const int j = e / d, l = e % d;
-        if (l > j) continue;
+    for (int e = tid; e < d * (d + 1) / 2; e += nt) {
+        int j, l;
+        tri_index(e, j, l);  // l <= j
         double C = 0.0;
-        if (n > 0) C = sv.m(k, h, l, j) - sv.m(k, h, l, d) * sv.m(k, h, j, d) * rn;
-        A[e] = pr.psi0[e] + C + f * (xb[j] - pr.m0s[j]) * (xb[l] - pr.m0s[l]);
+        if (n > 0) C = M(l, j) - M(l, d) * M(j, d) * rn;
+        A[j * ld + l] = pr.psi0[j * d + l] + C + f * (xb[j] - pr.m0s[j]) * (xb[l] - pr.m0s[l]);
     }
     __syncthreads();
-    // right-looking Cholesky, A = U U^T (lower); the pivot's reciprocal square root is
-    // formed once and shared
-    for (int j = 0; j < d; ++j) {
-        if (tid == 0) {
-            double v = A[j * d + j];
-            if (!(v > 0.0)) {
-                atomicExch(derr, (int)DPMM_ENUMERIC);
-                v = 1e-300;
-            }
-            const double r = rsqrt(v);
-            A[j * d + j] = v * r;
-            rd[j] = r;
-        }
-        __syncthreads();
-        const double rj = rd[j];
-        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] *= rj;
-        __syncthreads();
-        const int m = d - j - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = j + 1 + e / m, l = j + 1 + e % m;
-            if (l <= i) A[i * d + l] -= A[i * d + j] * A[l * d + j];
-        }
-        __syncthreads();
+    chol_ldl(A, d, ld, piv, rd, rw, derr);  // rw is free until the solve: scratch
+    // U_ij = A_ij / sqrt(v_j) below the diagonal (U_jj = sqrt(v_j)); the solve below
+    // needs V_ri = U_ri / U_rr = A_ri rd[i] rd[r], kept in place of A
+    for (int e = tid; e < d * (d - 1) / 2; e += nt) {
+        int r, i;
+        tri_index(e, r, i);  // i <= r
+        ++r;                 // strict lower triangle: i < r
+        A[r * ld + i] *= rd[i] * rd[r];
     }
     // U^T W = B, right-looking: after step r, row r of W (unscaled) is final and the rows
     // above are updated with it; the rows are scaled by 1 / U_rr at the end
@@ -242,10 +238,17 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     __syncthreads();
     for (int r = d - 1; r > 0; --r) {
         const int w = d - r;  // columns c = r .. d-1
-        const double rr = rd[r];
-        for (int e = tid; e < r * w; e += nt) {
-            const int i = e / w, c = r + e % w;  // row i < r
-            W[i * d + c] -= A[r * d + i] * rr * W[r * d + c];
+        const double* Wr = W + (size_t)r * d;
+        const double* Vr = A + (size_t)r * ld;
+        for (int e0 = tid; e0 < r * w; e0 += 2 * nt) {
+            const int e1 = e0 + nt;
+            const int i0 = e0 / w, c0 = r + e0 % w;  // row i < r
+            const bool two = e1 < r * w;
+            const int i1 = two ? e1 / w : i0, c1 = two ? r + e1 % w : c0;
+            const double a0 = W[i0 * d + c0], v0 = Vr[i0], w0 = Wr[c0];
+            const double a1 = W[i1 * d + c1], v1 = Vr[i1], w1 = Wr[c1];
+            W[i0 * d + c0] = fma(-v0, w0, a0);
+            if (two) W[i1 * d + c1] = fma(-v1, w1, a1);
         }
         __syncthreads();
     }
@@ -288,12 +291,12 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     for (int j = tid; j < d; j += nt) mu[j] = mn[j] + Bd[j] * rsk;
     if (w_in_smem)
         for (int e = tid; e < d * d; e += nt) Wg[e] = W[e];
-    double ld = 0.0;
-    for (int j = tid; j < d; j += nt) ld += log(W[j * d + j]);
-    ld = block_reduce_sum(ld, sh);
+    double lgd = 0.0;
+    for (int j = tid; j < d; j += nt) lgd += log(W[j * d + j]);
+    lgd = block_reduce_sum(lgd, sh);
     if (tid == 0) {
-        p_logdetW[s] = ld;
-        p_c[s] = logw[s] + ld - 0.5 * d * log(2.0 * M_PI);
+        p_logdetW[s] = lgd;
+        p_c[s] = logw[s] + lgd - 0.5 * d * 1.8378770664093453;  // log(2 pi)
     }
 }
 
@@ -373,10 +376,17 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
 
 cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
     if (c->kind == DPMM_PRIOR_NIW) {
-        const size_t dd = (size_t)c->d * c->d;
-        size_t sm = sizeof(double) * (2 * dd + 6 * c->d);
-        const int w_in_smem = sm <= 200 * 1024;
-        if (!w_in_smem) sm = sizeof(double) * (dd + 6 * c->d);
+        const size_t dd = (size_t)c->d * c->d, E = (size_t)c->st.E;
+        size_t sm = sizeof(double) * ((size_t)c->d * (c->d | 1) + 7 * c->d);
+        int staged = 0, w_in_smem = 0;
+        if (sm + sizeof(double) * E <= 200 * 1024) {
+            sm += sizeof(double) * E;
+            staged = 1;
+        }
+        if (sm + sizeof(double) * dd <= 200 * 1024) {
+            sm += sizeof(double) * dd;
+            w_in_smem = 1;
+        }
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(niw_params_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
@@ -385,7 +395,7 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         prof_begin(c, "niw_params");
         niw_params_kernel<<<3 * c->K_max, 128, sm, c->stream>>>(make_sv(c), c->shift_stats, pr, c->dK, c->eps,
                                                                c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW,
-                                                               c->p_c, c->derr, w_in_smem);
+                                                               c->p_c, c->derr, w_in_smem, staged);
         prof_end(c, "niw_params");
         c->nlaunch += 1;
     } else {

@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "dpmm_internal.cuh"
+#include "fp64_chol.cuh"
 
 namespace dpmm {
 
@@ -27,6 +28,9 @@ struct SMArgs {
     const double* beta;         // d
     double kappa0, nu0, logdet_psi0, alpha;
     double log_alpha, lg_alpha, lg_half_alpha;  // log a, lgamma(a), lgamma(a / 2), from the host
+    double lmvg_nu0;                            // sum_j lgamma(nu0 / 2 - j / 2), from the host
+    double half_d_log_kappa0;                   // d / 2 log kappa0, from the host
+    int stage;                                  // statistics blocks staged in shared memory
     int kind, K_max;
     const int* dK;
 };
@@ -114,13 +118,27 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         }
         return;
     }
-    double* A = smem;          // d x d (lower triangle)
-    double* xb = A + d * d;    // merged mean
+    const int ld = d | 1;      // odd row stride: column reads without bank conflicts
+    double* A = smem;          // d x ld (lower triangle)
+    double* xb = A + d * ld;   // merged mean
     double* x1 = xb + d;
     double* x2 = x1 + d;
+    double* piv = x2 + d;      // pivots of the factorisation
+    double* rs = piv + d;
+    double* S1 = rs + d;       // staged statistics of (k1, h) and of cluster k2 (E each)
+    double* S2 = S1 + a.L.E;
+    const bool staged = a.stage != 0;
+    if (staged) {
+        stage_slot(a.stats, a.L.E, k1, h, S1);
+        if (k2 >= 0) stage_slot(a.stats, a.L.E, k2, -1, S2);
+        __syncthreads();
+    }
+    // M[j][l] (j <= l) of the first and second statistics block
+    auto M1 = [&](int j, int l) -> double { return staged ? S1[a.L.ent(j, l)] : smv(a, k1, h, j, l); };
+    auto M2 = [&](int j, int l) -> double { return staged ? S2[a.L.ent(j, l)] : smv(a, k2, -1, j, l); };
     __shared__ double s_r1, s_r2, s_rn, s_w12;
     if (tid == 0) {  // reciprocals once: FP64 division is slow on GB300's narrow FP64 pipe
-        const double n1 = smv(a, k1, h, d, d), n2 = k2 >= 0 ? smv(a, k2, -1, d, d) : 0.0, n = n1 + n2;
+        const double n1 = M1(d, d), n2 = k2 >= 0 ? M2(d, d) : 0.0, n = n1 + n2;
         s_n1 = n1;
         s_n2 = n2;
         s_n = n;
@@ -132,8 +150,8 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     __syncthreads();
     const double n1 = s_n1, n2 = s_n2, n = s_n, r1 = s_r1, r2 = s_r2, rn = s_rn, w12 = s_w12;
     for (int j = tid; j < d; j += nt) {
-        double m1 = n1 > 0 ? a.shift_stats[(size_t)k1 * d + j] + smv(a, k1, h, j, d) * r1 : 0.0;
-        double m2 = (k2 >= 0 && n2 > 0) ? a.shift_stats[(size_t)k2 * d + j] + smv(a, k2, -1, j, d) * r2 : 0.0;
+        double m1 = n1 > 0 ? a.shift_stats[(size_t)k1 * d + j] + M1(j, d) * r1 : 0.0;
+        double m2 = (k2 >= 0 && n2 > 0) ? a.shift_stats[(size_t)k2 * d + j] + M2(j, d) * r2 : 0.0;
         x1[j] = m1;
         x2[j] = m2;
         xb[j] = n > 0 ? (n1 * m1 + n2 * m2) * rn : 0.0;
@@ -141,52 +159,33 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     __syncthreads();
     const double kn = a.kappa0 + n, nun = a.nu0 + n;
     const double f = n > 0 ? a.kappa0 * n / kn : 0.0;
-    for (int q = tid; q < d * d; q += nt) {
-        const int j = q / d, l = q % d;  // l <= j: the factorisation reads nothing else
-        if (l > j) continue;
+    for (int q0 = tid; q0 < d * (d + 1) / 2; q0 += nt) {
+        int j, l;
+        tri_index(q0, j, l);  // l <= j: the factorisation reads nothing else
+        const int q = j * ld + l;
         double C = 0.0;
-        if (n1 > 0) C += smv(a, k1, h, l, j) - smv(a, k1, h, l, d) * smv(a, k1, h, j, d) * r1;
+        if (n1 > 0) C += M1(l, j) - M1(l, d) * M1(j, d) * r1;
         if (k2 >= 0 && n2 > 0) {
-            C += smv(a, k2, -1, l, j) - smv(a, k2, -1, l, d) * smv(a, k2, -1, j, d) * r2;
+            C += M2(l, j) - M2(l, d) * M2(j, d) * r2;
             if (n1 > 0) C += w12 * (x1[j] - x2[j]) * (x1[l] - x2[l]);
         }
-        A[q] = a.psi0[q] + C + f * (xb[j] - a.m0s[j]) * (xb[l] - a.m0s[l]);
+        A[q] = a.psi0[j * d + l] + C + f * (xb[j] - a.m0s[j]) * (xb[l] - a.m0s[l]);
     }
     __syncthreads();
-    __shared__ double s_rj;
-    for (int j = 0; j < d; ++j) {
-        if (tid == 0) {
-            double v = A[j * d + j];
-            if (!(v > 0.0)) {
-                atomicExch(derr, (int)DPMM_ENUMERIC);
-                v = 1e-300;
-            }
-            const double r = rsqrt(v);
-            A[j * d + j] = v * r;
-            s_rj = r;
-        }
-        __syncthreads();
-        const double rj = s_rj;
-        for (int i = j + 1 + tid; i < d; i += nt) A[i * d + j] *= rj;
-        __syncthreads();
-        const int m = d - j - 1;
-        for (int q = tid; q < m * m; q += nt) {
-            const int i = j + 1 + q / m, l = j + 1 + q % m;
-            if (l <= i) A[i * d + l] -= A[i * d + j] * A[l * d + j];
-        }
-        __syncthreads();
-    }
-    // -(nun/2) log|Psi_n| and the multivariate-lgamma ratio, summed over j by all threads
+    chol_ldl(A, d, ld, piv, rs, x1, derr);  // x1 is free by now: scratch
+    // -(nun/2) log|Psi_n| and the multivariate-lgamma ratio (the prior's part from the
+    // host), summed over j by all threads; lane 0 of warp 0 adds log kappa_n
     double part = 0.0;
-    for (int j = tid; j < d; j += nt)
-        part += -nun * log(A[j * d + j]) + lgamma(0.5 * nun - 0.5 * j) - lgamma(0.5 * a.nu0 - 0.5 * j);
+    for (int j = tid; j < d; j += nt) part += -0.5 * nun * log(piv[j]) + lgamma(0.5 * nun - 0.5 * j);
+    if (tid == 0) part -= 0.5 * d * log(kn);
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if ((tid & 31) == 0) sh[tid >> 5] = part;
     __syncthreads();
     if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < (nt + 31) / 32; ++w) s += sh[w];
-        *out = -0.5 * n * d * log(M_PI) + s + 0.5 * a.nu0 * a.logdet_psi0 + 0.5 * d * (log(a.kappa0) - log(kn));
+        // 1.1447298858494002 = log(pi)
+        *out = -0.5 * n * d * 1.1447298858494002 + s - a.lmvg_nu0 + 0.5 * a.nu0 * a.logdet_psi0 + a.half_d_log_kappa0;
     }
 }
 
@@ -454,6 +453,10 @@ static SMArgs sm_args(dpmm_ctx* c) {
     a.log_alpha = std::log(c->alpha);
     a.lg_alpha = std::lgamma(c->alpha);
     a.lg_half_alpha = std::lgamma(0.5 * c->alpha);
+    a.lmvg_nu0 = 0.0;
+    for (int j = 0; j < c->d; ++j) a.lmvg_nu0 += std::lgamma(0.5 * c->nu0 - 0.5 * j);
+    a.half_d_log_kappa0 = 0.5 * c->d * std::log(c->kappa0);
+    a.stage = 0;
     a.kind = c->kind;
     a.K_max = c->K_max;
     a.dK = c->dK;
@@ -466,8 +469,17 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
     SMArgs s = sm_args(c);
     if (sm_enabled) {
         int items = 3 * c->K_max + c->K_max * (c->K_max - 1) / 2;
-        // the Dirichlet marginal needs no matrix workspace
-        size_t sm = c->kind == DPMM_PRIOR_NIW ? sizeof(double) * ((size_t)c->d * c->d + 4 * c->d) : 0;
+        // the Dirichlet marginal needs no matrix workspace; the NIW one stages the two
+        // statistics blocks it reads when they fit
+        size_t sm = 0;
+        if (c->kind == DPMM_PRIOR_NIW) {
+            sm = sizeof(double) * ((size_t)c->d * (c->d | 1) + 6 * c->d);
+            const size_t st = sm + sizeof(double) * 2 * (size_t)c->st.E;
+            if (st <= 160 * 1024) {
+                sm = st;
+                s.stage = 1;
+            }
+        }
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(marginal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
