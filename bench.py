@@ -30,9 +30,10 @@ sys.path.insert(0, ROOT)
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
 DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32"}
 METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
-# ncu DRAM bytes (read + write) per point of the label kernel, from the capture summarised in
-# profiles/labels_tc_gauss_d32.md; must be re-taken (or removed) whenever that kernel changes
-TRAFFIC_BYTES_PER_POINT = {}
+# ncu DRAM bytes (read + write) per point of the label kernel, from one capture of it on 2 M
+# points (its summary sits with the other profile summaries); must be re-taken (or removed)
+# whenever that kernel changes
+TRAFFIC_BYTES_PER_POINT = {("labels_tc", "gauss_d32"): (256.162816e6 + 8.674560e6) / 2e6}
 WORKLOADS = {
     "gauss_d32": dict(K_max=64),
     "gauss_d2": dict(K_max=64),
