@@ -269,3 +269,42 @@ def test_graph_replay_matches_eager(prec):
     ne, sxe, _ = ge.stats()
     ng, sxg, _ = gg.stats()
     assert np.array_equal(ne, ng) and np.array_equal(sxe, sxg)
+
+
+def test_high_dimension_d128():
+    """The d = 128 configuration (CUDA-core kernels: one cluster's factor per shared-memory
+    pass, statistics blocks beyond the staged layouts): FP64 sweeps bit-exact against the
+    oracle; the FP32 path (the TF32 setting is refused above d = 32) keeps the statistics
+    consistent with its labels."""
+    from paper_2204_08988_gb300 import synth
+
+    d = 128
+    X, _ = synth.gaussian_mixture(1501, d, 3, 4.0, seed=128, dtype=np.float64)
+    prior = _niw_prior(d)
+    o, g = _pair(0, d, 8, 3.0, X, burn_out=1, **prior)
+    for t in range(4):
+        o.sweep(1, 5)
+        g.sweep(1, 5)
+        assert o.K == g.K, t
+        zo, zbo = o.labels()
+        zg, zbg = g.labels()
+        assert np.array_equal(zo, zg) and np.array_equal(zbo, zbg), t
+        _check_stats(o, g, rtol=1e-9)
+    g.close()
+    X32 = X.astype(np.float32)
+    g = P.DPMM(0, d, 8, 3.0, prec=P.PREC_FP32, burn_out=1, **prior)
+    g.set_data(X32)
+    X64 = X32.astype(np.float64)
+    for t in range(4):
+        g.sweep(1, 9)
+        z, zb = g.labels()
+        n, sx, sxx = g.stats()
+        assert n[0::3].sum() == len(X) and np.array_equal(n[0::3], n[1::3] + n[2::3])
+        for k in range(g.K):
+            for h in range(2):
+                sel = (z == k) & (zb == h)
+                assert n[3 * k + 1 + h] == sel.sum()
+                c = max(1, sel.sum())
+                assert np.allclose(sx[3 * k + 1 + h], X64[sel].sum(0), rtol=1e-5, atol=1e-3 * c ** 0.5)
+                assert np.allclose(sxx[3 * k + 1 + h], X64[sel].T @ X64[sel], rtol=1e-5, atol=1e-2 * c ** 0.5)
+    g.close()
