@@ -7,7 +7,8 @@
 // log theta_K] (d x K).  log theta is split as hi + lo (two BF16 values, about 16
 // significant bits together) and both halves accumulate into the same FP32 tensor
 // memory columns: D = X hi + X lo.  The epilogue adds log pi_k and draws z_i by
-// exact Gumbel-max (deferred draws, as in the Gaussian kernel).  The data are read
+// exact Gumbel-max (no draw when one cluster is out of reach of all others, as in the
+// Gaussian kernel).  The data are read
 // once from HBM; the kernel is bandwidth-bound by design.
 //
 // CTA roles (192 threads, persistent): warp 0 TMA producer (X tiles of 128 rows, up to
@@ -182,46 +183,53 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
             const int b = (int)(it & 1);
             if (!mbar_wait(&tfull[b], (uint32_t)((it >> 1) & 1), abort)) { ok = false; break; }
             fence_after();
-            float best = -INFINITY, smax = -INFINITY;
-            int zb = 0, cn = 0;
-            int ck0 = 0, ck1 = 0, ck2 = 0, ck3 = 0;
-            float cs0 = 0.f, cs1 = 0.f, cs2 = 0.f, cs3 = 0.f;
+            // Exact Gumbel-max.  Pass 1 scores every cluster and keeps the two best; a
+            // cluster can win only within WINDOW of the best, so when the second best is
+            // outside it the best cluster is the label whatever the Gumbel values, and no
+            // draw is made.  Otherwise the accumulators (still held) are read again and every
+            // cluster within the window gets its draw.
+            float m1 = -INFINITY, m2 = -INFINITY;
+            int k1 = 0;
             const uint32_t iter = *a.diter;
+            const uint32_t tb = tmem + lane_off + (uint32_t)(b * 128);
             for (int k0 = 0; k0 < NB; k0 += 32) {
                 float y[32];
-                tmem_ld32(tmem + lane_off + (uint32_t)(b * 128 + k0), y);
-                // pass 1: scores and the running maximum
+                tmem_ld32(tb + (uint32_t)k0, y);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int k = k0 + j;
-                    y[j] = k < K ? ct[k] + y[j] : -INFINITY;
+                    const float sc = k < K ? ct[k] + y[j] : -INFINITY;
                     if constexpr (SCORES) {
-                        if (k < K && i < a.N) a.scores[i * K + k] = (double)y[j];
+                        if (k < K && i < a.N) a.scores[i * K + k] = (double)sc;
                     }
-                    smax = fmaxf(smax, y[j]);
+                    const bool gt = sc > m1;
+                    m2 = gt ? m1 : fmaxf(m2, sc);
+                    k1 = gt ? k : k1;
+                    m1 = gt ? sc : m1;
                 }
-                // pass 2: candidates within the Gumbel range of the maximum
+            }
+            const float lim = m1 - WINDOW;
+            const bool need = !(m2 <= lim);
+            int zb = k1;
+            if (__any_sync(0xffffffffu, need)) {
+                float best = -INFINITY;
+                int zd = 0;
+                for (int k0 = 0; k0 < NB; k0 += 32) {
+                    float y[32];
+                    tmem_ld32(tb + (uint32_t)k0, y);
+                    if (need) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float sc = y[j];
-                    if (sc > smax - WINDOW) {
-                        const int k = k0 + j;
-                        if (cn == 0) { ck0 = k; cs0 = sc; }
-                        else if (cn == 1) { ck1 = k; cs1 = sc; }
-                        else if (cn == 2) { ck2 = k; cs2 = sc; }
-                        else if (cn == 3) { ck3 = k; cs3 = sc; }
-                        else gumbel_update(a.seed, iter, (uint32_t)i, k, sc, &best, &zb);
-                        cn = min(cn + 1, 4);
+                        for (int j = 0; j < 32; ++j) {
+                            const int k = k0 + j;
+                            const float sc = k < K ? ct[k] + y[j] : -INFINITY;
+                            if (sc > lim) gumbel_update(a.seed, iter, (uint32_t)i, k, sc, &best, &zd);
+                        }
                     }
                 }
+                if (need) zb = zd;
             }
             fence_before();
             mbar_arrive(&tempty[b]);
-            const float lim = smax - WINDOW;
-            if (cn > 0 && cs0 > lim) gumbel_update(a.seed, iter, (uint32_t)i, ck0, cs0, &best, &zb);
-            if (cn > 1 && cs1 > lim) gumbel_update(a.seed, iter, (uint32_t)i, ck1, cs1, &best, &zb);
-            if (cn > 2 && cs2 > lim) gumbel_update(a.seed, iter, (uint32_t)i, ck2, cs2, &best, &zb);
-            if (cn > 3 && cs3 > lim) gumbel_update(a.seed, iter, (uint32_t)i, ck3, cs3, &best, &zb);
             if (i < a.N) a.z[i] = zb;
         }
         if (!ok) {
