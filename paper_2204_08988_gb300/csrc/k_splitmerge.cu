@@ -30,6 +30,7 @@ struct SMArgs {
     double log_alpha, lg_alpha, lg_half_alpha;  // log a, lgamma(a), lgamma(a / 2), from the host
     double lmvg_nu0;                            // sum_j lgamma(nu0 / 2 - j / 2), from the host
     double half_d_log_kappa0;                   // d / 2 log kappa0, from the host
+    double sum_beta, lg_sum_beta, sum_lg_beta;  // sum beta_j, its lgamma, sum lgamma(beta_j)
     int stage;                                  // statistics blocks staged in shared memory
     int kind, K_max;
     const int* dK;
@@ -86,12 +87,12 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
     }
     if (a.kind == DPMM_PRIOR_DIRICHLET) {
-        double sb = 0.0, sc = 0.0, acc = 0.0;
+        // the prior's terms (sum beta, lgamma(sum beta), sum lgamma(beta_j)) come from the host
+        double sc = 0.0, acc = 0.0;
         for (int j = tid; j < d; j += nt) {
             double c = smv(a, k1, h, j, d) + (k2 >= 0 ? smv(a, k2, -1, j, d) : 0.0);
-            sb += a.beta[j];
             sc += c;
-            acc += lgamma(a.beta[j] + c) - lgamma(a.beta[j]);
+            acc += lgamma(a.beta[j] + c);
         }
         double tot = 0.0;
         // sum counts and lgamma terms over the block (fixed order)
@@ -107,13 +108,11 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         __syncthreads();
         if (tid == 0) {
             double c = 0.0, l = 0.0;
-            sb = 0.0;
-            for (int j = 0; j < d; ++j) sb += a.beta[j];
             for (int w = 0; w < (nt + 31) / 32; ++w) {
                 c += shc[w];
                 l += sha[w];
             }
-            tot = l + lgamma(sb) - lgamma(sb + c);
+            tot = l - a.sum_lg_beta + a.lg_sum_beta - lgamma(a.sum_beta + c);
             *out = tot;
         }
         return;
@@ -456,6 +455,14 @@ static SMArgs sm_args(dpmm_ctx* c) {
     a.lmvg_nu0 = 0.0;
     for (int j = 0; j < c->d; ++j) a.lmvg_nu0 += std::lgamma(0.5 * c->nu0 - 0.5 * j);
     a.half_d_log_kappa0 = 0.5 * c->d * std::log(c->kappa0);
+    a.sum_beta = a.lg_sum_beta = a.sum_lg_beta = 0.0;
+    if (c->kind == DPMM_PRIOR_DIRICHLET) {
+        for (double b : c->beta) {
+            a.sum_beta += b;
+            a.sum_lg_beta += std::lgamma(b);
+        }
+        a.lg_sum_beta = std::lgamma(a.sum_beta);
+    }
     a.stage = 0;
     a.kind = c->kind;
     a.K_max = c->K_max;
