@@ -286,6 +286,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     A(&c->eps, sizeof(double) * S * d);
     A(&c->bart, sizeof(double) * S * d);
     A(&c->lgs, sizeof(double) * (S + 1));
+    A(&c->retry, sizeof(int) * S);
     A(&c->tot, sizeof(int) * (K_max + 1));
     c->records_bytes = sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
     A(&c->records, c->records_bytes);
@@ -298,6 +299,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         return DPMM_ENOMEM;
     }
     cudaMemset(c->derr, 0, sizeof(int));
+    cudaMemset(c->retry, 0, sizeof(int) * S);
     cudaMemset(c->counters, 0, sizeof(int) * 8);
     cudaMemset(c->p_logw, 0, sizeof(double) * S);
     cudaMemset(c->dK, 0, sizeof(int));
@@ -313,7 +315,7 @@ void dpmm_destroy(dpmm_ctx* c) {
     void* ps[] = {c->dK, c->diter, c->age, c->counters, c->derr, c->stats, c->shift_new, c->shift_stats,
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
-                  c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs};
+                  c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);

@@ -215,6 +215,7 @@ struct dpmm_ctx {
     double* eps = nullptr;       // 3 K_max x d: normals of the drawn means
     double* bart = nullptr;      // 3 K_max x d: Bartlett diagonal (chi-square roots)
     double* lgs = nullptr;       // 3 K_max + 1: log-Gamma draws of the weights
+    int* retry = nullptr;        // 3 K_max: slots whose FP32 parameter draw is redone in FP64
 
     // sort / reduction scratch
     int T_tiles = 0;         // sort tiles of 256 points

@@ -80,4 +80,57 @@ __device__ inline void chol_ldl(double* A, int d, int ld, double* piv, double* r
     }
 }
 
+__device__ inline float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ inline double rsqrt_t(double x) { return rsqrt(x); }
+
+// The factorisation above in working type T, for the parameter draws of the reduced-
+// precision paths (T = float) and their FP64 retry (T = double).  A pivot v_j that is not
+// above rel * dg[j] (dg: the matrix's own diagonal; rel = 0: not positive, or NaN) sets
+// *fail (shared memory) and is replaced by the smallest normal value of T, so that the
+// caller can redo the slot in FP64.  With rel = 2^-10 an FP32 factorisation is redone
+// once cancellation has taken more than 10 of the 24 bits of a pivot.
+template <typename T>
+__device__ inline void chol_ldl_t(T* A, int d, int ld, T* piv, T* rs, T* col, const T* dg, T rel, int* fail) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = 0; j < d; ++j) {
+        if (tid < 32) {
+            T v = A[j * ld + j];
+            if (!(v > (rel > T(0) ? rel * dg[j] : T(0)))) {
+                if (tid == 0) *fail = 1;
+                v = sizeof(T) == 4 ? T(1.17549435e-38f) : T(2.2250738585072014e-308);
+            }
+            const T r = rsqrt_t(v), inv = r * r;
+            for (int i = j + 1 + tid; i < d; i += 32) col[i] = A[i * ld + j] * inv;
+            if (tid == 0) {
+                piv[j] = v;
+                rs[j] = r;
+            }
+        }
+        __syncthreads();
+        const int m = d - j - 1, tri = m * (m + 1) / 2;
+        for (int e0 = tid; e0 < tri; e0 += 4 * nt) {
+            T av[4], ci[4], cl[4];
+            int at[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * nt;
+                at[u] = -1;
+                if (e < tri) {
+                    int i0, l0;
+                    tri_index(e, i0, l0);
+                    const int i = j + 1 + i0, l = j + 1 + l0;
+                    at[u] = i * ld + l;
+                    av[u] = A[at[u]];
+                    ci[u] = col[i];
+                    cl[u] = A[l * ld + j];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (at[u] >= 0) A[at[u]] = fma(-ci[u], cl[u], av[u]);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace dpmm

@@ -1,7 +1,8 @@
 // k_params.cu -- steps (a)-(d) of the sweep (Sec. 4.1, Eqs. sample_weights,
-// sample_sub_weights, sample_params, sample_sub_params) on the GPU in FP64:
-// one CTA draws the weights; one CTA per (sub-)cluster slot draws its parameters
-// from the conjugate posterior of its sufficient statistics.
+// sample_sub_weights, sample_params, sample_sub_params) on the GPU: one warp draws the
+// weights; one CTA per (sub-)cluster slot draws its parameters from the conjugate
+// posterior of its sufficient statistics (in FP64; the NIW factorisation in FP32 on the
+// reduced-precision paths, with an FP64 retry).
 #include <math.h>
 
 #include <algorithm>
@@ -157,34 +158,46 @@ struct NiwPrior {
 // GB300's FP64 pipe retires about two operations per clock per SM with a 64-cycle
 // dependent latency, so the kernel keeps FP64 work off the serial paths: the slot's
 // statistics are staged in shared memory, every division is a reciprocal formed once,
-// the factorisation (chol_ldl) takes one reciprocal square root per pivot, and the
-// triangular solve for W runs right-looking (one parallel update of the rows above per
-// step) in shared memory.  Dynamic shared memory: d*d + 7*d (+ E when staged) (+ d*d
-// when W fits) doubles.
+// the factorisation takes one reciprocal square root per pivot, and the triangular
+// solve for W runs right-looking (one parallel update of the rows above per step).
+// T is the working type of the factorisation and the solves: double on the FP64 path;
+// float on the reduced-precision paths (whose label scores are FP32 anyway), with the
+// statistics, C = S2 - S1 S1^T / n and the outputs in FP64.  A slot whose FP32
+// factorisation loses more than 10 bits of a pivot to cancellation (or meets a
+// non-positive one) is flagged in retry[] and redone by the FP64 instantiation
+// (launched with retry set, it takes only the flagged slots).
+// Dynamic shared memory: (E doubles when staged) + (d*ld + 7*d (+ d*d when W fits)) T.
+__device__ inline float log_t(float x) { return logf(x); }
+__device__ inline double log_t(double x) { return log(x); }
+
+template <typename T>
 __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPrior pr, const int* dK,
                                   const double* eps, const double* bart, const double* logw, double* p_mu,
                                   double* p_W, double* p_logdetW, double* p_c, int* derr, int w_in_smem,
-                                  int staged) {
+                                  int staged, int* retry) {
     extern __shared__ double smem[];
     const int d = sv.L.d, E = sv.L.E;
     const int K = *dK;
     const int s = blockIdx.x;
     if (s >= 3 * K) return;
+    const bool retry_pass = sizeof(T) == 8 && retry != nullptr;
+    if (retry_pass && retry[s] == 0) return;
     const int k = s / 3, h = s % 3 - 1;  // h = -1: the cluster
     const int ld = d | 1;         // odd row stride: column reads without bank conflicts
-    double* A = smem;             // d x ld: Psi_n (lower), then the solve's multipliers
-    double* mn = A + d * ld;      // d
-    double* xb = mn + d;          // d
-    double* Bd = xb + d;          // d: Bartlett diagonal, then v
-    double* acc = Bd + d;         // d: eps
-    double* rd = acc + d;         // d: 1 / U_jj
-    double* rw = rd + d;          // d: 1 / W_jj
-    double* piv = rw + d;         // d: pivots
-    double* S = piv + d;          // E: staged statistics
+    double* S = smem;             // E: staged statistics
+    T* A = (T*)(S + (staged ? E : 0));  // d x ld: Psi_n (lower), then the solve's multipliers
+    T* mn = A + d * ld;           // d
+    T* dg = mn + d;               // d: diagonal of Psi_n
+    T* Bd = dg + d;               // d: Bartlett diagonal, then v
+    T* acc = Bd + d;              // d: eps
+    T* rd = acc + d;              // d: 1 / U_jj
+    T* rw = rd + d;               // d: 1 / W_jj
+    T* piv = rw + d;              // d: pivots
     double* Wg = p_W + (size_t)s * d * d;
-    double* W = w_in_smem ? S + (staged ? E : 0) : Wg;  // d x d working copy
+    T* W = w_in_smem ? piv + d : (T*)Wg;  // d x d working copy (global only when T = double)
     __shared__ double sh[32];
     __shared__ double s_n, s_rn, s_kn, s_rkn;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, nt = blockDim.x;
 
     if (staged) {
@@ -198,32 +211,44 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         s_rn = n > 0 ? 1.0 / n : 0.0;
         s_kn = pr.kappa0 + n;
         s_rkn = 1.0 / s_kn;
+        s_fail = 0;
     }
     __syncthreads();
     const double n = s_n, rn = s_rn, kn = s_kn, rkn = s_rkn;
     const double* sh_k = shift_stats + (size_t)k * d;
     for (int j = tid; j < d; j += nt) {
         const double xbar = n > 0 ? sh_k[j] + M(j, d) * rn : 0.0;
-        xb[j] = xbar;
-        mn[j] = (pr.kappa0 * pr.m0s[j] + n * xbar) * rkn;
-        Bd[j] = bart[(size_t)s * d + j];
-        acc[j] = eps[(size_t)s * d + j];
+        mn[j] = (T)((pr.kappa0 * pr.m0s[j] + n * xbar) * rkn);
+        Bd[j] = (T)bart[(size_t)s * d + j];
+        acc[j] = (T)eps[(size_t)s * d + j];
     }
     if (w_in_smem)  // the normals above the diagonal (zero below), drawn by variates_kernel
-        for (int e = tid; e < d * d; e += nt) W[e] = Wg[e];
+        for (int e = tid; e < d * d; e += nt) W[e] = (T)Wg[e];
     __syncthreads();
-    // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n;
-    // lower triangle only: the factorisation below reads nothing else
+    // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n
+    // (in FP64: the subtraction cancels); lower triangle only: the factorisation reads
+    // nothing else
     const double f = n > 0 ? pr.kappa0 * n * rkn : 0.0;
     for (int e = tid; e < d * (d + 1) / 2; e += nt) {
         int j, l;
         tri_index(e, j, l);  // l <= j
         double C = 0.0;
         if (n > 0) C = M(l, j) - M(l, d) * M(j, d) * rn;
-        A[j * ld + l] = pr.psi0[j * d + l] + C + f * (xb[j] - pr.m0s[j]) * (xb[l] - pr.m0s[l]);
+        const double xj = n > 0 ? sh_k[j] + M(j, d) * rn : 0.0, xl = n > 0 ? sh_k[l] + M(l, d) * rn : 0.0;
+        const T a = (T)(pr.psi0[j * d + l] + C + f * (xj - pr.m0s[j]) * (xl - pr.m0s[l]));
+        A[j * ld + l] = a;
+        if (l == j) dg[j] = a;
     }
     __syncthreads();
-    chol_ldl(A, d, ld, piv, rd, rw, derr);  // rw is free until the solve: scratch
+    // rw is free until the solve: scratch
+    chol_ldl_t<T>(A, d, ld, piv, rd, rw, dg, sizeof(T) == 4 ? T(1.0 / 1024) : T(0), &s_fail);
+    if (s_fail) {
+        if (sizeof(T) == 4) {  // redo this slot in FP64
+            if (tid == 0) retry[s] = 1;
+            return;
+        }
+        if (tid == 0) atomicExch(derr, (int)DPMM_ENUMERIC);
+    }
     // U_ij = A_ij / sqrt(v_j) below the diagonal (U_jj = sqrt(v_j)); the solve below
     // needs V_ri = U_ri / U_rr = A_ri rd[i] rd[r], kept in place of A
     for (int e = tid; e < d * (d - 1) / 2; e += nt) {
@@ -238,15 +263,15 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     __syncthreads();
     for (int r = d - 1; r > 0; --r) {
         const int w = d - r;  // columns c = r .. d-1
-        const double* Wr = W + (size_t)r * d;
-        const double* Vr = A + (size_t)r * ld;
+        const T* Wr = W + (size_t)r * d;
+        const T* Vr = A + (size_t)r * ld;
         for (int e0 = tid; e0 < r * w; e0 += 2 * nt) {
             const int e1 = e0 + nt;
             const int i0 = e0 / w, c0 = r + e0 % w;  // row i < r
             const bool two = e1 < r * w;
             const int i1 = two ? e1 / w : i0, c1 = two ? r + e1 % w : c0;
-            const double a0 = W[i0 * d + c0], v0 = Vr[i0], w0 = Wr[c0];
-            const double a1 = W[i1 * d + c1], v1 = Vr[i1], w1 = Wr[c1];
+            const T a0 = W[i0 * d + c0], v0 = Vr[i0], w0 = Wr[c0];
+            const T a1 = W[i1 * d + c1], v1 = Vr[i1], w1 = Wr[c1];
             W[i0 * d + c0] = fma(-v0, w0, a0);
             if (two) W[i1 * d + c1] = fma(-v1, w1, a1);
         }
@@ -257,22 +282,22 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         if (c >= r) W[e] *= rd[r];
     }
     __syncthreads();
-    for (int j = tid; j < d; j += nt) rw[j] = 1.0 / W[j * d + j];
+    for (int j = tid; j < d; j += nt) rw[j] = T(1) / W[j * d + j];
     __syncthreads();
     // W^T v = eps (forward substitution) by warp 0, lane m keeps sum_{j<m} W[j][m] v_j;
     // mu = m_n + v / sqrt(kappa_n)
     if (tid < 32) {
         const int ns = (d + 31) >> 5;
-        double am[8];  // m = tid + 32 i, d <= 256
+        T am[8];  // m = tid + 32 i, d <= 256
 #pragma unroll
-        for (int i = 0; i < 8; ++i) am[i] = 0.0;
+        for (int i = 0; i < 8; ++i) am[i] = T(0);
         for (int j = 0; j < d; ++j) {
             const int own = j & 31, slot = j >> 5;
-            double mine = 0.0;
+            T mine = T(0);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i == slot) mine = am[i];
-            double vj = 0.0;
+            T vj = T(0);
             if (tid == own) {
                 vj = (acc[j] - mine) * rw[j];
                 Bd[j] = vj;  // reuse as v
@@ -287,16 +312,17 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     }
     __syncthreads();
     double* mu = p_mu + (size_t)s * d;
-    const double rsk = rsqrt(kn);
-    for (int j = tid; j < d; j += nt) mu[j] = mn[j] + Bd[j] * rsk;
+    const T rsk = rsqrt_t((T)kn);
+    for (int j = tid; j < d; j += nt) mu[j] = (double)(mn[j] + Bd[j] * rsk);
     if (w_in_smem)
-        for (int e = tid; e < d * d; e += nt) Wg[e] = W[e];
+        for (int e = tid; e < d * d; e += nt) Wg[e] = (double)W[e];
     double lgd = 0.0;
-    for (int j = tid; j < d; j += nt) lgd += log(W[j * d + j]);
+    for (int j = tid; j < d; j += nt) lgd += (double)log_t(W[j * d + j]);
     lgd = block_reduce_sum(lgd, sh);
     if (tid == 0) {
         p_logdetW[s] = lgd;
         p_c[s] = logw[s] + lgd - 0.5 * d * 1.8378770664093453;  // log(2 pi)
+        if (retry_pass) retry[s] = 0;
     }
 }
 
@@ -376,26 +402,41 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
 
 cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
     if (c->kind == DPMM_PRIOR_NIW) {
-        const size_t dd = (size_t)c->d * c->d, E = (size_t)c->st.E;
-        size_t sm = sizeof(double) * ((size_t)c->d * (c->d | 1) + 7 * c->d);
-        int staged = 0, w_in_smem = 0;
-        if (sm + sizeof(double) * E <= 200 * 1024) {
-            sm += sizeof(double) * E;
-            staged = 1;
-        }
-        if (sm + sizeof(double) * dd <= 200 * 1024) {
-            sm += sizeof(double) * dd;
-            w_in_smem = 1;
-        }
-        if (sm > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(niw_params_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-        }
+        const size_t dd = (size_t)c->d * c->d, E = (size_t)c->st.E, dl = (size_t)c->d * (c->d | 1);
         NiwPrior pr{c->kappa0, c->nu0, c->center + c->d, c->center + 2 * c->d};
+        // shared memory of the T instantiation: E doubles (staged), then d*ld + 7 d (+ d*d) T
+        auto plan = [&](size_t tsz, int& staged, int& w_in_smem) {
+            size_t sm = tsz * (dl + 7 * (size_t)c->d);
+            staged = w_in_smem = 0;
+            if (sm + 8 * E <= 200 * 1024) {
+                sm += 8 * E;
+                staged = 1;
+            }
+            if (sm + tsz * dd <= 200 * 1024) {
+                sm += tsz * dd;
+                w_in_smem = 1;
+            }
+            return sm;
+        };
+        int st64, w64, st32, w32;
+        const size_t sm64 = plan(8, st64, w64), sm32 = plan(4, st32, w32);
+        const bool fp32 = c->prec != DPMM_PREC_FP64_PLAIN && w32;  // FP32 needs W in shared memory
+        cudaError_t e = cudaFuncSetAttribute(niw_params_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm64);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(niw_params_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
+        if (e != cudaSuccess) return e;
         prof_begin(c, "niw_params");
-        niw_params_kernel<<<3 * c->K_max, 128, sm, c->stream>>>(make_sv(c), c->shift_stats, pr, c->dK, c->eps,
-                                                               c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW,
-                                                               c->p_c, c->derr, w_in_smem, staged);
+        if (fp32) {
+            niw_params_kernel<float><<<3 * c->K_max, 128, sm32, c->stream>>>(
+                make_sv(c), c->shift_stats, pr, c->dK, c->eps, c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW,
+                c->p_c, c->derr, w32, st32, c->retry);
+            c->nlaunch += 1;
+        }
+        // the FP64 path, or the FP64 retry of slots whose FP32 factorisation failed
+        niw_params_kernel<double><<<3 * c->K_max, 128, sm64, c->stream>>>(
+            make_sv(c), c->shift_stats, pr, c->dK, c->eps, c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c,
+            c->derr, w64, st64, fp32 ? c->retry : nullptr);
         prof_end(c, "niw_params");
         c->nlaunch += 1;
     } else {

@@ -129,6 +129,46 @@ def test_param_draws_fp64_match_oracle():
         assert np.allclose(a, b, rtol=1e-10, atol=1e-10), (key, np.abs(a - b).max())
 
 
+@pytest.mark.parametrize("prec,d", [("fp32", 8), ("tf32", 32)])
+def test_param_draws_reduced_precision(prec, d):
+    """Steps (c), (d) on the reduced-precision paths: the NIW factorisation and solves
+    run in FP32, and a slot whose pivots lose more than 10 of their 24 bits to
+    cancellation is redone in FP64.  Every slot is checked against the oracle's draw
+    from the GPU's own statistics and the same Philox stream: the well-conditioned
+    clusters to FP32 accuracy, the ill-conditioned one (two coordinates equal up to
+    1e-3 noise) to FP64 accuracy, which only the FP64 retry reaches."""
+    from paper_2204_08988_gb300 import synth
+
+    N, K, it, seed = 4000, 4, 3, 99
+    X, y = synth.gaussian_mixture(N, d, K, 5.0, seed=21)
+    X = X.astype(np.float32)
+    sel = y == 0
+    rng = np.random.default_rng(3)
+    X[sel, 0] *= 10.0  # pivot 1 of Psi_n ~ 2 against a diagonal ~ 1e4
+    X[sel, 1] = X[sel, 0] + (1e-3 * rng.standard_normal(sel.sum())).astype(np.float32)
+    prior = _niw_prior(d)
+    pr = P.PREC_FP32 if prec == "fp32" else P.PREC_TF32
+    g = P.DPMM(0, d, 16, 2.0, prec=pr, **prior)
+    g.set_data(X)
+    zb0 = (np.arange(N) % 3 == 0).astype(np.uint8)
+    g.set_state(K, y, zb0)
+    g.set_iter(it)
+    g.set_mask(1)
+    g.sweep(1, seed)
+    n, sx, sxx = g.stats()
+    pg = g.params()
+    g.close()
+    o = O.Oracle(O.NIW, d, 16, 2.0, **prior)
+    for s in range(3 * K):
+        kn, mn, nun, psin = o.niw_posterior(n[s], sx[s], sxx[s])
+        W, mu, ld = o.niw_draw(seed, it, s, kn, mn, nun, psin)
+        ew = np.abs(pg["W"][s] - W).max() / np.abs(W).max()
+        em = np.abs(pg["mu"][s] - mu).max() / (1.0 + np.abs(mu).max())
+        el = abs(pg["logdetW"][s] - ld)
+        tol = 1e-8 if s < 3 else 1e-4  # cluster 0 (slots 0-2) is the ill-conditioned one
+        assert ew < tol and em < tol and el < 100 * tol, (s, ew, em, el)
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 def test_full_sweeps_fp64_match_oracle(kind):
     """Whole sweeps (params, labels, statistics, splits, merges) from K=1."""
