@@ -27,8 +27,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
-DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32"}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3, "bf16x3": 4}
+DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32", "bf16x3": "bf16x3"}
 METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
 # ncu DRAM bytes (read + write) per point of the label kernel, from one capture of it on 2 M
 # points (its summary sits with the other profile summaries); must be re-taken (or removed)
@@ -243,12 +243,16 @@ def main():
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         if kind == 0:
             flops = 2.0 * N * d * d * Kavg  # X (N x d) times the K stacked d x d factors
-            if a.prec in ("tf32", "bf16"):
+            if a.prec in ("tf32", "bf16", "bf16x3"):
                 bf16 = peaks.get("bf16_tflops", 1900.0)
                 peak = bf16 * (1.1 / 2.25) if a.prec == "tf32" else bf16
                 roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "peak_source": ("measured bf16 x nominal tf32/bf16 ratio 1.1/2.25" if a.prec == "tf32"
                                         else "measured bf16 burst")}
+                if a.prec == "bf16x3":
+                    # issued: three BF16 products on the padded dimension plus the one-step -b product
+                    dp = 64 if d <= 64 else 128
+                    roof["issued_tflops"] = 2.0 * N * Kavg * dp * (3 * dp + 16) / avg_s / 1e12
             else:
                 # CUDA-core paths: FMA pipe peak from 152 SMs x 128 FP32 lanes x 2 flop at the max SM clock
                 peak = 152 * 128 * 2 * 2.07e9 / 1e12 if a.prec == "fp32" else 1.25

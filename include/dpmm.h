@@ -74,12 +74,20 @@ typedef enum { DPMM_F64 = 0, DPMM_F32 = 1, DPMM_BF16 = 2, DPMM_I32 = 3 } dpmm_dt
  * FP64_PLAIN: everything in FP64 on CUDA cores (the parity path).
  * FP32: FP32 CUDA cores, FP64 combine of statistics.
  * TF32 / BF16: the cluster likelihoods as one tensor-core contraction
- *   (tcgen05, FP32 accumulation), the rest as FP32. */
+ *   (tcgen05, FP32 accumulation), the rest as FP32.  TF32: Gaussian, d <= 32;
+ *   BF16: multinomial, d <= 256.
+ * BF16X3: Gaussian, d <= 128: the cluster likelihoods as a tensor-core
+ *   contraction with both operands split into two BF16 values (three products,
+ *   about 16 significant bits per operand, FP32 accumulation); sub-labels and
+ *   statistics as FP32.
+ * Every reduced precision draws the parameters with an FP32 factorisation and
+ * redoes a slot in FP64 when that factorisation loses too much to cancellation. */
 typedef enum {
     DPMM_PREC_FP64_PLAIN = 0,
     DPMM_PREC_TF32 = 1,
     DPMM_PREC_BF16 = 2,
-    DPMM_PREC_FP32 = 3
+    DPMM_PREC_FP32 = 3,
+    DPMM_PREC_BF16X3 = 4
 } dpmm_prec;
 
 /* Create a chain.  alpha > 0 is the DP concentration (Eq. DPLatentVar); d >= 1

@@ -23,7 +23,7 @@ _lib = None
 DPMM_OK, DPMM_EINVAL, DPMM_ENOMEM, DPMM_ECUDA, DPMM_ESTATE, DPMM_ENUMERIC, DPMM_ETIMEOUT = range(7)
 PRIOR_NIW, PRIOR_DIRICHLET = 0, 1
 F64, F32, BF16, I32 = 0, 1, 2, 3
-PREC_FP64_PLAIN, PREC_TF32, PREC_BF16, PREC_FP32 = 0, 1, 2, 3
+PREC_FP64_PLAIN, PREC_TF32, PREC_BF16, PREC_FP32, PREC_BF16X3 = 0, 1, 2, 3, 4
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENUMERIC", 6: "ETIMEOUT"}
 
 # every symbol include/dpmm.h declares

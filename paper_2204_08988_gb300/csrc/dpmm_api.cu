@@ -180,6 +180,7 @@ static dpmm_status upload(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_devi
     }
     if (tmp) cudaFreeAsync(tmp, c->stream);
     CK(c, e);
+    CK(c, x3_prepare_data(c));  // split-BF16 point tiles (BF16X3 only)
     return DPMM_OK;
 }
 
@@ -197,8 +198,8 @@ static dpmm_status check_derr(dpmm_ctx* c) {
 }
 
 static void free_data(dpmm_ctx* c) {
-    dfree(c->X); dfree(c->z); dfree(c->zbar); dfree(c->idx); dfree(c->hist);
-    c->X = nullptr; c->z = nullptr; c->zbar = nullptr; c->idx = nullptr; c->hist = nullptr;
+    dfree(c->X); dfree(c->z); dfree(c->zbar); dfree(c->idx); dfree(c->hist); dfree(c->x3_ximg);
+    c->X = nullptr; c->z = nullptr; c->zbar = nullptr; c->idx = nullptr; c->hist = nullptr; c->x3_ximg = nullptr;
 }
 
 static void drop_graph(dpmm_ctx* c) {
@@ -315,7 +316,7 @@ void dpmm_destroy(dpmm_ctx* c) {
     void* ps[] = {c->dK, c->diter, c->age, c->counters, c->derr, c->stats, c->shift_new, c->shift_stats,
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
-                  c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry};
+                  c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
@@ -326,13 +327,14 @@ void dpmm_destroy(dpmm_ctx* c) {
 dpmm_status dpmm_set_options(dpmm_ctx* c, dpmm_prec prec, int init_K, int burn_out, void* stream) {
     if (!c) return DPMM_EINVAL;
     drop_graph(c);
-    if (prec < DPMM_PREC_FP64_PLAIN || prec > DPMM_PREC_FP32) return fail(c, DPMM_EINVAL, "unknown precision");
+    if (prec < DPMM_PREC_FP64_PLAIN || prec > DPMM_PREC_BF16X3) return fail(c, DPMM_EINVAL, "unknown precision");
     if (init_K < 1 || init_K > c->K_max) return fail(c, DPMM_EINVAL, "init_K must be in [1, K_max]");
     if (burn_out < 0) return fail(c, DPMM_EINVAL, "burn_out must be >= 0");
     if (c->X && prec != c->prec) return fail(c, DPMM_ESTATE, "set the precision before dpmm_set_data");
     int old = c->prec;
     c->prec = prec;
-    if ((prec == DPMM_PREC_TF32 || prec == DPMM_PREC_BF16) && !tc_supported(c)) {
+    if (((prec == DPMM_PREC_TF32 || prec == DPMM_PREC_BF16) && !tc_supported(c)) ||
+        (prec == DPMM_PREC_BF16X3 && !x3_supported(c))) {
         c->prec = old;
         return fail(c, DPMM_EINVAL, "tensor-core precision not available for this prior/dimension");
     }
@@ -431,6 +433,7 @@ static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
 // the kernels of one sweep, in order, on the context's stream
 static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
     const bool tc = (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16);
+    const bool x3 = c->prec == DPMM_PREC_BF16X3;
     cudaError_t e = cudaSuccess;
     if (c->step_mask & 1u) {
         if ((e = launch_weights(c, seed)) != cudaSuccess) return e;
@@ -438,7 +441,8 @@ static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
         if ((e = launch_derive(c)) != cudaSuccess) return e;
     }
     if (c->step_mask & 2u) {
-        if ((e = tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed)) != cudaSuccess) return e;
+        e = x3 ? launch_labels_x3(c, seed) : tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed);
+        if (e != cudaSuccess) return e;
         if ((e = launch_sort(c)) != cudaSuccess) return e;
         if ((e = launch_substats(c, seed, 1)) != cudaSuccess) return e;
         if ((e = launch_combine(c)) != cudaSuccess) return e;
@@ -664,7 +668,9 @@ dpmm_status dpmm_label_scores(dpmm_ctx* c, double* scores) {
     CK(c, cudaMalloc(&zkeep, sizeof(int32_t) * c->N));
     CK(c, cudaMemcpyAsync(zkeep, c->z, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->stream));
     const bool tc = c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16;
-    cudaError_t e = tc ? launch_labels_tc(c, c->seed) : launch_labels_simt(c, c->seed);
+    cudaError_t e = c->prec == DPMM_PREC_BF16X3 ? launch_labels_x3(c, c->seed)
+                    : tc                        ? launch_labels_tc(c, c->seed)
+                                                : launch_labels_simt(c, c->seed);
     CK(c, e);
     CK(c, cudaMemcpyAsync(scores, c->dbg_scores, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(c->z, zkeep, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->stream));

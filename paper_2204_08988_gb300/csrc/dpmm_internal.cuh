@@ -211,6 +211,8 @@ struct dpmm_ctx {
     void* tc_img = nullptr;  // tensor-core operand image of the cluster parameters
     size_t tc_img_bytes = 0;
     void* tcs_img = nullptr;  // tensor-core sub-cluster factor images (K_max x 10 KB)
+    void* x3_ximg = nullptr;  // split-BF16 point tiles (BF16X3), pre-swizzled
+    void* x3_fimg = nullptr;  // split-BF16 factor image (BF16X3), K_max clusters
     double* cweights = nullptr;  // K_max: pi_k of the last sweep (linear)
     double* eps = nullptr;       // 3 K_max x d: normals of the drawn means
     double* bart = nullptr;      // 3 K_max x d: Bartlett diagonal (chi-square roots)
@@ -269,6 +271,10 @@ cudaError_t tc_prepare(dpmm_ctx* c);
 bool substats_tc_supported(const dpmm_ctx* c);
 cudaError_t substats_tc_prepare(dpmm_ctx* c);
 cudaError_t launch_substats_tc(dpmm_ctx* c, uint64_t seed, int draw, const int* gate);
+bool x3_supported(const dpmm_ctx* c);
+cudaError_t x3_prepare_data(dpmm_ctx* c);
+cudaError_t x3_prepare(dpmm_ctx* c);
+cudaError_t launch_labels_x3(dpmm_ctx* c, uint64_t seed);
 
 // profiling helpers (no-ops unless enabled)
 void prof_begin(dpmm_ctx* c, const char* name);

@@ -459,6 +459,7 @@ cudaError_t launch_derive(dpmm_ctx* c) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && tc_supported(c)) e = tc_prepare(c);
     if (e == cudaSuccess && substats_tc_supported(c)) e = substats_tc_prepare(c);
+    if (e == cudaSuccess && x3_supported(c)) e = x3_prepare(c);
     return e;
 }
 
