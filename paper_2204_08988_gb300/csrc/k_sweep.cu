@@ -623,6 +623,194 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
     if (cur >= 0) flush(cur);
 }
 
+// FP32 variant for 64 < d <= 128 (Gaussian).  Per batch of WP = 64 points (sorted by
+// cluster): each sub-cluster score is the squared norm of (x - mu_h) W_h, computed for
+// the whole batch as one register-tiled product in shared memory (warps 0-7: each
+// thread owns 8 points x 4 columns; per K step two broadcast float4 loads of
+// (x - mu)^T and one float4 of W feed 32 FMAs; W is staged once per cluster run, zero
+// below the diagonal and beyond d, so the loop needs no triangular bound).  Statistics: one 4x4 register block per
+// worker thread (nblk <= 561 workers, so every block has one owner and is written
+// straight to the records) and one accumulator set per sub-cluster (warp-uniform
+// branch on h).  Dynamic shared memory: 2 x 128 x 128 floats (W_l, W_r), 128 x WP
+// (x - mu_h)^T, WP x dp point rows, WP x 2 scores, then ints and bytes.
+constexpr int WP = 64;
+constexpr int WIDE_T = 576;
+
+template <typename XT>
+__global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float> a) {
+    if (a.gate && *a.gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int d = a.d, dp = a.L.dp, nblk = a.L.nblk;
+    float* Ws = (float*)smraw;              // 2 x 128 x 128: W_h[l][j]
+    float* Tt = Ws + 2 * 128 * 128;         // 128 x WP: (x_p - mu_h)_l at Tt[l * WP + p]
+    float* xs = Tt + 128 * WP;              // WP x dp
+    float* qv = xs + WP * dp;               // WP x 2
+    float* mus = qv + 2 * WP;               // 2 x 128
+    float* shf = mus + 256;                 // 128
+    float* cc = shf + 128;                  // 2 (+2 pad)
+    int* kq = (int*)(cc + 4);               // WP
+    int* runs = kq + WP;                    // WP + 1
+    int* nruns = runs + WP + 1;             // 1
+    unsigned char* hq = (unsigned char*)(nruns + 1);  // WP
+    __shared__ int staged;
+    __shared__ int wcnt[32];
+
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x;
+    const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
+    Key key{a.seed, *a.diter, 0};
+    const XT* X = (const XT*)a.X;
+    const bool worker = tid < nblk;
+    int jb = 0, lb = 0;
+    a.L.blk_coords(worker ? tid : 0, jb, lb);
+    float acc0[16], acc1[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc0[e] = acc1[e] = 0.f;
+    int cur = -1;
+    if (tid == 0) staged = -1;
+
+    auto flush = [&](int k) {  // every block has a single owner: no reduction
+        if (worker) {
+            double* out = a.rec + (size_t)(g + k) * 2 * a.L.E + (size_t)tid * 16;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                out[e] = (double)acc0[e];
+                out[a.L.E + e] = (double)acc1[e];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc0[e] = acc1[e] = 0.f;
+    };
+
+    for (int64_t base = p0; base < p1; base += WP) {
+        const int np = (int)min((int64_t)WP, p1 - base);
+        __syncthreads();
+        if (tid < np) kq[tid] = a.z[a.idx[base + tid]];
+        // raw rows, one warp per row (d <= 128: one float4 per lane)
+        for (int r = warp; r < np; r += nt / 32) {
+            const int i = a.idx[base + r];
+            float* xr = xs + (size_t)r * dp;
+            if constexpr (sizeof(XT) == 4) {
+                if (lane * 4 < d) *(float4*)(xr + lane * 4) = *(const float4*)(X + (int64_t)i * a.xs + lane * 4);
+            } else {
+                for (int j = lane; j < d; j += 32) xr[j] = ldx<float, XT>(X + (int64_t)i * a.xs + j);
+            }
+        }
+        __syncthreads();
+        find_runs(kq, np, runs, nruns, wcnt);
+        const int nr = *nruns;
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (k != staged) {  // uniform: stage the cluster's two sub-clusters
+                __syncthreads();
+                for (int e = tid; e < 2 * 128 * 128; e += nt) {
+                    const int h = e >> 14, l = (e >> 7) & 127, j = e & 127;
+                    const int s = 3 * k + 1 + h;
+                    Ws[e] = (j < d && l <= j) ? a.pv.W[((size_t)s * d + l) * d + j] : 0.f;
+                }
+                for (int e = tid; e < 256; e += nt) {
+                    const int h = e >> 7, j = e & 127;
+                    mus[e] = j < d ? a.pv.mu[(size_t)(3 * k + 1 + h) * d + j] : 0.f;
+                }
+                if (tid < 2) cc[tid] = a.pv.c[3 * k + 1 + tid];
+                for (int j = tid; j < 128; j += nt) shf[j] = j < d ? a.shift[(size_t)k * d + j] : 0.f;
+                __syncthreads();
+                if (tid == 0) staged = k;
+            }
+            if (a.draw) {
+                for (int h = 0; h < 2; ++h) {
+                    __syncthreads();
+                    for (int e = tid; e < 128 * WP; e += nt) {
+                        const int l = e / WP, p = e % WP;
+                        Tt[e] = (l < d && p >= qs && p < qe) ? xs[(size_t)p * dp + l] - mus[h * 128 + l] : 0.f;
+                    }
+                    __syncthreads();
+                    if (tid < 256) {  // warps 0-7: Y = (X - mu_h) W_h for the batch
+                        const int pg = tid >> 5, cg = lane;  // points 8 pg .. 8 pg + 7, columns 4 cg .. 4 cg + 3
+                        float y[8][4];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) y[u][v] = 0.f;
+                        const float* Wh = Ws + h * 128 * 128;
+                        for (int l = 0; l < d; ++l) {
+                            const float4 t0 = *(const float4*)(Tt + l * WP + pg * 8);
+                            const float4 t1 = *(const float4*)(Tt + l * WP + pg * 8 + 4);
+                            const float4 w0 = *(const float4*)(Wh + l * 128 + cg * 4);
+                            const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                            const float wv[4] = {w0.x, w0.y, w0.z, w0.w};
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                                for (int v = 0; v < 4; ++v) y[u][v] = fmaf(tv[u], wv[v], y[u][v]);
+                        }
+                        float qp[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            qp[u] = fmaf(y[u][0], y[u][0], y[u][1] * y[u][1]) + fmaf(y[u][2], y[u][2], y[u][3] * y[u][3]);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) qp[u] += __shfl_xor_sync(0xffffffffu, qp[u], o);
+                        if (cg == 0)
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) qv[(pg * 8 + u) * 2 + h] = qp[u];
+                    }
+                }
+                __syncthreads();
+            }
+            if (tid >= qs && tid < qe) {
+                const int i = a.idx[base + tid];
+                int h;
+                if (a.draw) {
+                    uint32_t w[4];
+                    key.block((uint32_t)i, TAG_ZBAR, 0, w);
+                    const float vl = cc[0] - 0.5f * qv[tid * 2] + gumbel_of<float>(w[0], w[1]);
+                    const float vr = cc[1] - 0.5f * qv[tid * 2 + 1] + gumbel_of<float>(w[2], w[3]);
+                    h = vr > vl ? 1 : 0;
+                    a.zbar[i] = (uint8_t)h;
+                } else {
+                    h = a.zbar[i];
+                }
+                hq[tid] = (unsigned char)h;
+                // the row shifted by the cluster's centre, then 1, then zeros
+                float* xr = xs + (size_t)tid * dp;
+                for (int j = 0; j < dp; ++j) xr[j] = j < d ? xr[j] - shf[j] : (j == d ? 1.f : 0.f);
+            }
+        }
+        __syncthreads();
+        for (int r = 0; r < nr; ++r) {
+            const int qs = runs[r], qe = runs[r + 1];
+            const int k = kq[qs];
+            if (k != cur) {
+                if (cur >= 0) flush(cur);
+                cur = k;
+            }
+            if (worker) {
+                for (int q = qs; q < qe; ++q) {
+                    const float* xr = xs + (size_t)q * dp;
+                    const float4 xj = *(const float4*)(xr + jb * 4);
+                    const float4 xl = *(const float4*)(xr + lb * 4);
+                    const float aj[4] = {xj.x, xj.y, xj.z, xj.w}, al[4] = {xl.x, xl.y, xl.z, xl.w};
+                    if (hq[q]) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int w2 = 0; w2 < 4; ++w2) acc1[u * 4 + w2] = fmaf(aj[u], al[w2], acc1[u * 4 + w2]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int w2 = 0; w2 < 4; ++w2) acc0[u * 4 + w2] = fmaf(aj[u], al[w2], acc0[u * 4 + w2]);
+                    }
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush(cur);
+}
+
 // Multinomial variant (first-moment statistics only): the point's counts become a
 // float row in shared memory (x, then 1, then zeros); the current run's two
 // sub-cluster log theta vectors are staged in shared memory; each sub-cluster score is
@@ -1031,6 +1219,42 @@ static cudaError_t substats_mult_t(dpmm_ctx* c, uint64_t seed, int draw, const i
     return cudaGetLastError();
 }
 
+static size_t wide_smem(const dpmm_ctx* c) {
+    return ((size_t)2 * 128 * 128 + 128 * WP + (size_t)WP * c->st.dp + 2 * WP + 256 + 128 + 4) * 4 +
+           ((size_t)2 * WP + 2) * sizeof(int) + WP + 16;
+}
+
+template <typename XT>
+static cudaError_t substats_wide_t(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
+    SubArgs<float> a;
+    a.kind = c->kind;
+    a.d = c->d;
+    a.xs = c->xs;
+    a.N = c->N;
+    a.X = c->X;
+    a.pv = pview<float>(c);
+    a.shift = c->shift32;
+    a.z = c->z;
+    a.zbar = c->zbar;
+    a.idx = c->idx;
+    a.dK = c->dK;
+    a.diter = c->diter;
+    a.gate = gate;
+    a.seed = seed;
+    a.draw = draw;
+    a.P = WP;
+    a.G = 1;
+    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.L = c->st;
+    a.rec = c->records;
+    const size_t smem = wide_smem(c);
+    cudaError_t ea = cudaFuncSetAttribute(substats_wide_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (ea != cudaSuccess) return ea;
+    substats_wide_kernel<XT><<<c->G2, WIDE_T, smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
 static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
     prof_begin(c, draw ? "substats" : "restats");
     cudaError_t e;
@@ -1047,6 +1271,8 @@ static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const
                                              : substats_f32_t<32, float>(c, seed, draw, gate);
     else if (fast) e = c->xdt == 2 ? substats_f32_t<64, __nv_bfloat16>(c, seed, draw, gate)
                                    : substats_f32_t<64, float>(c, seed, draw, gate);
+    else if (c->prec != DPMM_PREC_FP64_PLAIN && c->kind == DPMM_PRIOR_NIW && c->d <= 128 && c->st.nblk <= WIDE_T)
+        e = c->xdt == 2 ? substats_wide_t<__nv_bfloat16>(c, seed, draw, gate) : substats_wide_t<float>(c, seed, draw, gate);
     else if (c->prec == DPMM_PREC_FP64_PLAIN) e = substats_t<double, double>(c, seed, draw, gate);
     else if (c->xdt == 2) e = substats_t<float, __nv_bfloat16>(c, seed, draw, gate);
     else e = substats_t<float, float>(c, seed, draw, gate);

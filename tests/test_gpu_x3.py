@@ -101,10 +101,11 @@ def _setup_single(d):
     return x1, None, None, o, g, p
 
 
-@pytest.mark.parametrize("d", [64, 128])
+@pytest.mark.parametrize("d", [64, 99, 128])
 def test_x3_labels_agree_with_fp64(d):
     """One label and sub-label step from the same parameters and Philox keys as the
-    FP64 oracle: labels within the disagreement budget."""
+    FP64 oracle: labels within the disagreement budget (d = 99 pads the features of
+    both the tensor-core kernel and the FP32 sub-label kernel)."""
     N, K = 20_000, 12
     X, y, zb, o, g, p = _setup(N, d, K, seed=5 + d)
     g.set_mask(2)
@@ -137,11 +138,13 @@ def test_x3_chain_finds_clusters_and_keeps_statistics(d, N, K):
             n, sx, sxx = g.stats()
             assert n[0::3].sum() == N and np.array_equal(n[0::3], n[1::3] + n[2::3])
             for k in range(g.K):
-                sel = z == k
-                assert n[3 * k] == sel.sum()
-                c = max(1, sel.sum())
-                assert np.allclose(sx[3 * k], X64[sel].sum(0), rtol=1e-5, atol=1e-2 * c ** 0.5)
-                assert np.allclose(sxx[3 * k], X64[sel].T @ X64[sel], rtol=1e-5, atol=1e-1 * c ** 0.5)
+                for h in range(2):
+                    sel = (z == k) & (zb == h)
+                    s = 3 * k + 1 + h
+                    assert n[s] == sel.sum()
+                    c = max(1, sel.sum())
+                    assert np.allclose(sx[s], X64[sel].sum(0), rtol=1e-5, atol=1e-2 * c ** 0.5)
+                    assert np.allclose(sxx[s], X64[sel].T @ X64[sel], rtol=1e-5, atol=1e-1 * c ** 0.5)
     z, _ = g.labels()
     purity = sum(Counter(z[y == k]).most_common(1)[0][1] for k in range(K) if (y == k).any()) / N
     assert purity > 0.95, (purity, g.K)
