@@ -30,10 +30,16 @@ sys.path.insert(0, ROOT)
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3, "bf16x3": 4}
 DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32", "bf16x3": "bf16x3"}
 METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
-# ncu DRAM bytes (read + write) per point of the label kernel, from one capture of it on 2 M
-# points (its summary sits with the other profile summaries); must be re-taken (or removed)
-# whenever that kernel changes
-TRAFFIC_BYTES_PER_POINT = {("labels_tc", "gauss_d32"): (256.162816e6 + 8.674560e6) / 2e6}
+# ncu DRAM bytes (read + write) per launch of the label kernel, from one capture of it on a
+# smaller case (its summary sits with the other profile summaries), as (bytes per point, bytes
+# per cluster): the point part scales with N, the factor part with K.  Must be re-taken (or
+# removed) whenever that kernel changes.
+TRAFFIC_BYTES = {
+    ("labels_tc", "gauss_d32"): ((256.162816e6 + 8.674560e6) / 2e6, 0.0),
+    # 262,144 points, K = 56: 138.378752 MB read + 4.014592 MB written, of which the 56 factor
+    # images (69,632 B each, read once from DRAM, then from L2) are the cluster part
+    ("labels_x3", "gauss_d128"): ((138.378752e6 + 4.014592e6 - 56 * 69632) / 262144, 69632.0),
+}
 WORKLOADS = {
     "gauss_d32": dict(K_max=64),
     "gauss_d2": dict(K_max=64),
@@ -265,10 +271,10 @@ def main():
             roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peak, "unit": "GB/s",
                     "peak_source": "measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        # DRAM bytes per launch from the ncu capture summarised in profiles/ (taken on 2 M points,
-        # scaled by the points processed); null for kernels without a current capture
-        tb = TRAFFIC_BYTES_PER_POINT.get((lk[0], a.workload))
-        roof["traffic"] = tb * N if tb else None
+        # DRAM bytes per launch from the ncu capture summarised in profiles/ (taken on a smaller
+        # case, scaled by the points and clusters processed); null without a current capture
+        tb = TRAFFIC_BYTES.get((lk[0], a.workload))
+        roof["traffic"] = tb[0] * N + tb[1] * Kavg if tb else None
         roof["kernel"] = lk[0]
         roof["kernel_ms_avg"] = ms / max(launches, 1)
     gpu_launches = prof.get("all_kernels", (0, 0))[0]
