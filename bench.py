@@ -45,6 +45,7 @@ WORKLOADS = {
     "gauss_d2": dict(K_max=64),
     "multinomial": dict(K_max=128),
     "gauss_d128": dict(K_max=128),
+    "batched": dict(K_max=64),
 }
 
 
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--prec", default="tf32", choices=sorted(PREC))
     ap.add_argument("--burnin", type=int, default=150)
     ap.add_argument("--n", type=int, default=None, help="override N (smaller cases for profiling)")
+    ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--breakdown", action="store_true", help="add a per-kernel time table from a separate profiled pass")
@@ -147,7 +149,14 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    X, y, prior, opt = load_workload(a.workload, a.n, 0)
+    if a.workload == "batched":  # a bounded sample of the first problem
+        from paper_2204_08988_gb300 import synth
+
+        X, y, d = next(synth.batch_problems(a.problems))
+        prior = dict(kind=0, kappa0=1.0, m0=np.zeros(d), nu0=float(d + 3), psi0=np.eye(d))
+        opt = dict(alpha=10.0)
+    else:
+        X, y, prior, opt = load_workload(a.workload, a.n, 0)
     N = X.shape[0]
     vals = []
     info = None
@@ -167,10 +176,105 @@ def run_reference(a):
     print(json.dumps(out))
 
 
+def batch_prec(d):
+    """Precision of a batched problem: FP32 CUDA cores for d <= 8, TF32 tensor cores for
+    d <= 32, split BF16 tensor cores above."""
+    return "fp32" if d <= 8 else ("tf32" if d <= 32 else "bf16x3")
+
+
+def main_batched(a):
+    """All problems of the batched workload on one GPU: one chain (context) and one stream
+    per problem; a step is one sweep of every problem (dpmm_sweep_batch), timed with events
+    on a main stream that every problem stream joins."""
+    import torch
+
+    import paper_2204_08988_gb300 as P
+    from paper_2204_08988_gb300 import _build, synth
+
+    _build.build()
+    K_max = WORKLOADS["batched"]["K_max"]
+    seed = 0
+    chains, streams, sizes = [], [], []
+    for p, (X, y, d) in enumerate(synth.batch_problems(a.problems)):
+        s = torch.cuda.Stream()
+        g = P.DPMM(0, d, K_max, 10.0, prec=PREC[batch_prec(d)], init_K=1, burn_out=15, stream=s.cuda_stream,
+                   kappa0=1.0, m0=np.zeros(d), nu0=float(d + 3), psi0=np.eye(d))
+        g.set_data(X)
+        g.set_problem(p)
+        if a.init_truth:
+            g.set_state(int(y.max()) + 1, y, (np.arange(len(y)) % 2).astype(np.uint8))
+        chains.append(g)
+        streams.append(s)
+        sizes.append((len(y), d))
+    handles = [g.h for g in chains]
+    N_tot = sum(n for n, _ in sizes)
+    burn = 0 if a.init_truth else a.burnin
+    P.dpmm_sweep_batch(handles, burn + a.warmup, seed)
+    torch.cuda.synchronize()
+    main_s = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    step_ms = []
+    with Clocks(0) as clk:
+        for _ in range(a.steps):
+            with torch.cuda.stream(main_s):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(main_s)
+            for s in streams:
+                s.wait_event(e0)
+            P.dpmm_sweep_batch(handles, 1, seed)
+            for s in streams:
+                ev = torch.cuda.Event()
+                ev.record(s)
+                main_s.wait_event(ev)
+            e1.record(main_s)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    total_ms = float(sum(step_ms))
+    Ks = [g.K for g in chains]
+    value = N_tot * a.steps / (total_ms / 1e3)
+    # roofline of the batch: each problem's label-step bound max(flops / the peak of its
+    # arithmetic, bytes / HBM), summed over problems, against the measured time of a step
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = peaks.get("bf16_tflops", 1900.0) * 1e12
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    peak = {"fp32": 152 * 128 * 2 * 2.07e9, "tf32": bf16 * 1.1 / 2.25, "bf16x3": bf16 / 3.0}
+    bound_s = 0.0
+    for (n, d), K in zip(sizes, Ks):
+        flops = 2.0 * n * d * d * K
+        bound_s += max(flops / peak[batch_prec(d)], n * (4 * d + 5) / hbm)
+    roof = {"bound": "mixed", "achieved": bound_s * 1e3, "peak": total_ms / a.steps, "unit": "ms (label-step bound / step)",
+            "frac": bound_s * 1e3 / (total_ms / a.steps), "traffic": None,
+            "note": "sum over problems of max(2 N d^2 K / peak of its precision, N (4d + 5) B / HBM); "
+                    "bf16x3 counts one third of the BF16 peak (three products)"}
+    mix = {}
+    for (n, d) in sizes:
+        mix.setdefault(d, [0, 0])
+        mix[d][0] += 1
+        mix[d][1] += n
+    out = {"metric": METRIC, "value": value, "unit": "point-sweeps/s", "n_gpus": 1, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+           "config": {"workload": "batched", "problems": len(chains), "N_total": N_tot,
+                      "mix": {str(d): {"problems": c, "points": n, "prec": batch_prec(d)} for d, (c, n) in
+                              sorted(mix.items())},
+                      "K_max": K_max, "K_timed_mean": float(np.mean(Ks)), "burnin_sweeps": burn,
+                      "init": "generating labels" if a.init_truth else "K=1", "parallelism": "1gpu, one stream per problem",
+                      "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
+           "roofline": roof, "cpu_baseline": None, "e2e": None, "clocks": clk.summary(), "gpu_launches": None,
+           "step_ms": step_ms}
+    print(json.dumps(out))
+    for g in chains:
+        g.close()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batched":
+        return main_batched(a)
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -119,6 +119,24 @@ dpmm_status dpmm_update_data(dpmm_ctx* ctx, const void* X, dpmm_dtype dt, int on
  * the context's stream. */
 dpmm_status dpmm_sweep(dpmm_ctx* ctx, int iters, uint64_t seed);
 
+/* Problem id of this chain: the fourth word of every Philox counter (the paper's
+ * counters name the point or cluster, the sweep and the draw; this word keeps the
+ * random streams of independent chains apart, e.g. the problems of a batch).
+ * Default 0.  Takes effect at the next kernel, also inside an already captured
+ * sweep graph.  Synchronises. */
+dpmm_status dpmm_set_problem(dpmm_ctx* ctx, uint32_t problem);
+
+/* Batched sweeps of independent problems: `iters` sweeps of each of the n
+ * contexts, interleaved (sweep t of every context before sweep t + 1), all with
+ * Philox key `seed` (give each context its own problem id).  Each context's sweeps
+ * are queued asynchronously on its own stream as a captured graph, so contexts with
+ * distinct non-NULL streams run concurrently on the GPU and small problems fill it
+ * together.  The paper runs one problem per call and has no counterpart; the result
+ * of every context equals that of dpmm_sweep on it alone.  Returns the first
+ * failing context's status (the remaining contexts of that round are not queued);
+ * DPMM_EINVAL for a NULL array or entry, n < 0 or iters < 0. */
+dpmm_status dpmm_sweep_batch(dpmm_ctx* const* ctxs, int n, int iters, uint64_t seed);
+
 /* Labels into caller-owned host arrays of length N (z in [0, K), zbar in {0,1}).
  * Either pointer may be NULL.  Synchronises. */
 dpmm_status dpmm_get_labels(dpmm_ctx* ctx, int32_t* z, uint8_t* zbar);

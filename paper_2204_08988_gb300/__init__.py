@@ -31,7 +31,8 @@ EXPORTS = [
     "dpmm_create", "dpmm_set_options", "dpmm_set_data", "dpmm_update_data", "dpmm_sweep", "dpmm_get_labels",
     "dpmm_get_stats", "dpmm_get_info", "dpmm_get_counters", "dpmm_last_error", "dpmm_destroy",
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
-    "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores",
+    "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
+    "dpmm_sweep_batch",
 ]
 
 
@@ -81,6 +82,8 @@ def load():
             "dpmm_get_profile": ([vp, i32, vp, vp, vp, C.POINTER(i32)], i32),
             "dpmm_suffstats_noalloc": ([vp, i64, i32, vp, vp, i32, vp, vp, vp, vp], i32),
             "dpmm_label_scores": ([vp, vp], i32),
+            "dpmm_set_problem": ([vp, u32], i32),
+            "dpmm_sweep_batch": ([vp, i32, i32, u64], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -187,6 +190,18 @@ def dpmm_set_step_mask(h, mask):
 
 def dpmm_set_iter(h, it):
     _check(h, load().dpmm_set_iter(h, int(it)))
+
+
+def dpmm_set_problem(h, problem):
+    _check(h, load().dpmm_set_problem(h, int(problem)))
+
+
+def dpmm_sweep_batch(handles, iters, seed):
+    """Sweeps of several chains (their handles), interleaved; asynchronous."""
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    st = load().dpmm_sweep_batch(arr, len(handles), int(iters), int(seed))
+    if st != DPMM_OK:
+        raise DPMMError(st, "dpmm_sweep_batch failed (see the failing chain's dpmm_last_error)")
 
 
 def dpmm_set_params(h, K, logw, mu=None, W=None, logdetW=None, logtheta=None):
@@ -299,6 +314,9 @@ class DPMM:
 
     def set_iter(self, it):
         dpmm_set_iter(self.h, it)
+
+    def set_problem(self, problem):
+        dpmm_set_problem(self.h, problem)
 
     def set_params(self, K, p):
         if self.kind == PRIOR_NIW:

@@ -264,7 +264,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     bool ok = true;
     auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
     A(&c->dK, sizeof(int));
-    A(&c->diter, sizeof(uint32_t));
+    A(&c->diter, 2 * sizeof(uint32_t));  // [sweep index, problem id]
     A(&c->age, sizeof(int) * K_max);
     A(&c->counters, sizeof(int) * 8);
     A(&c->derr, sizeof(int));
@@ -300,6 +300,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         return DPMM_ENOMEM;
     }
     cudaMemset(c->derr, 0, sizeof(int));
+    cudaMemset(c->diter, 0, 2 * sizeof(uint32_t));
     cudaMemset(c->retry, 0, sizeof(int) * S);
     cudaMemset(c->counters, 0, sizeof(int) * 8);
     cudaMemset(c->p_logw, 0, sizeof(double) * S);
@@ -369,6 +370,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     }
     const size_t esz = c->xdt == 0 ? 8 : (c->xdt == 1 ? 4 : 2);
     c->T_tiles = (int)((N + 255) / 256);
+    c->Gr = (int)std::min<int64_t>(c->G2, std::max<int64_t>(1, (N + 511) / 512));
     bool ok = true;
     auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
     A(&c->X, (size_t)N * c->xs * esz);
@@ -491,6 +493,25 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
         }
     }
     c->seed = seed;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_set_problem(dpmm_ctx* c, uint32_t problem) {
+    if (!c) return DPMM_EINVAL;
+    CK(c, cudaMemcpyAsync(c->diter + 1, &problem, sizeof(problem), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_sweep_batch(dpmm_ctx* const* ctxs, int n, int iters, uint64_t seed) {
+    if (!ctxs || n < 0 || iters < 0) return DPMM_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return DPMM_EINVAL;
+    for (int it = 0; it < iters; ++it)
+        for (int i = 0; i < n; ++i) {
+            const dpmm_status s = dpmm_sweep(ctxs[i], 1, seed);
+            if (s != DPMM_OK) return s;
+        }
     return DPMM_OK;
 }
 

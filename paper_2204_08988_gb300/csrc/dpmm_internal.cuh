@@ -189,7 +189,7 @@ struct dpmm_ctx {
     int32_t* z = nullptr;
     uint8_t* zbar = nullptr;
     int* dK = nullptr;        // device: current K
-    uint32_t* diter = nullptr;// device: sweep counter
+    uint32_t* diter = nullptr;// device: [sweep counter, problem id] (Philox counter words c1, c3)
     int* age = nullptr;       // device, K_max
     int* counters = nullptr;  // device, 8
     int* derr = nullptr;      // device error word
@@ -224,7 +224,8 @@ struct dpmm_ctx {
     int* hist = nullptr;     // K_max x T_tiles
     int* tot = nullptr;      // K_max + 1: totals, then starts
     int* idx = nullptr;      // N: points sorted by cluster
-    int G2 = 0;              // CTAs of the sub-label/statistics kernel
+    int G2 = 0;              // most ranges of the sub-label/statistics step (records capacity)
+    int Gr = 1;              // ranges used for the current data: about one per 512 points, at most G2
     double* records = nullptr;  // (G2 + K_max) x 2 x E
     size_t records_bytes = 0;
 

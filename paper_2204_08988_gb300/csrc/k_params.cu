@@ -72,7 +72,7 @@ struct VarArgs {
 __global__ void variates_kernel(VarArgs a) {
     const int K = *a.dK;
     const int d = a.sv.L.d;
-    Key key{a.seed, *a.diter, 0};
+    Key key{a.seed, a.diter[0], a.diter[1]};
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if ((int)blockIdx.y == 3 * a.Kmax) {
         const int T = 3 * K + 1;
@@ -335,7 +335,7 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
     const int s = blockIdx.x;
     if (s >= 3 * K) return;
     const int k = s / 3, h = s % 3 - 1;
-    Key key{seed, *diter, 0};
+    Key key{seed, diter[0], diter[1]};
     double* lt = p_logtheta + (size_t)s * d;
     double mx = -INFINITY;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {

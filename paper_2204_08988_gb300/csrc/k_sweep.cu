@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
     T* xr = sx + (size_t)tid * (d + 1);
     if (live)
         for (int j = 0; j < d; ++j) xr[j] = ldx<T, XT>(X + i * xs + j);
-    Key key{seed, *diter, 0};
+    Key key{seed, diter[0], diter[1]};
     T best = -INFINITY;
     int zb = 0;
     uint32_t w[4];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(MAXT) substats_kernel(SubArgs<T> a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, *a.diter, 0};
+    Key key{a.seed, a.diter[0], a.diter[1]};
     const XT* X = (const XT*)a.X;
 
     // register block of this thread
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, *a.diter, 0};
+    Key key{a.seed, a.diter[0], a.diter[1]};
     const XT* X = (const XT*)a.X;
     const bool worker = tid < nblk * G;
     const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float>
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, *a.diter, 0};
+    Key key{a.seed, a.diter[0], a.diter[1]};
     const XT* X = (const XT*)a.X;
     const bool worker = tid < nblk;
     int jb = 0, lb = 0;
@@ -838,7 +838,7 @@ __global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, *a.diter, 0};
+    Key key{a.seed, a.diter[0], a.diter[1]};
     const XT* X = (const XT*)a.X;
     const bool worker = tid < nblk * G;
     const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
@@ -996,10 +996,11 @@ __global__ void combine_kernel(const double* rec, const int* starts, const int* 
 }
 
 // initial labels: K = init_K, z uniform over K, z-bar a fair coin (tag INIT, c1 = 0)
-__global__ void init_labels_kernel(int64_t N, int initK, uint64_t seed, int32_t* z, uint8_t* zbar) {
+__global__ void init_labels_kernel(int64_t N, int initK, uint64_t seed, const uint32_t* diter, int32_t* z,
+                                   uint8_t* zbar) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    Key key{seed, 0, 0};
+    Key key{seed, 0, diter[1]};
     uint32_t w[4];
     key.block((uint32_t)i, TAG_INIT, 0, w);
     int k = (int)(u01_f64(w[0], w[1]) * initK);
@@ -1127,24 +1128,24 @@ static cudaError_t substats_t(dpmm_ctx* c, uint64_t seed, int draw, const int* g
     a.draw = draw;
     a.P = q.P;
     a.G = q.G;
-    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.R = (c->N + c->Gr - 1) / c->Gr;
     a.L = c->st;
     a.rec = c->records;
     if (q.BT <= 256) {
         cudaError_t ea = cudaFuncSetAttribute(substats_kernel<T, XT, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
         if (ea != cudaSuccess) return ea;
-        substats_kernel<T, XT, 256><<<c->G2, q.BT, q.smem, c->stream>>>(a);
+        substats_kernel<T, XT, 256><<<c->Gr, q.BT, q.smem, c->stream>>>(a);
     } else {
         cudaError_t ea = cudaFuncSetAttribute(substats_kernel<T, XT, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem);
         if (ea != cudaSuccess) return ea;
-        substats_kernel<T, XT, 1024><<<c->G2, q.BT, q.smem, c->stream>>>(a);
+        substats_kernel<T, XT, 1024><<<c->Gr, q.BT, q.smem, c->stream>>>(a);
     }
     return cudaGetLastError();
 }
 
 static cudaError_t combine_impl(dpmm_ctx* c, const int* gate) {
     dim3 grid((c->st.E + 255) / 256, 2 * c->K_max);
-    int64_t R = (c->N + c->G2 - 1) / c->G2;
+    int64_t R = (c->N + c->Gr - 1) / c->Gr;
     combine_kernel<<<grid, 256, 0, c->stream>>>(c->records, c->tot, c->dK, R, c->st.E, c->shift_new, c->shift_stats,
                                                 c->d, gate, c->stats);
     return cudaGetLastError();
@@ -1173,13 +1174,13 @@ static cudaError_t substats_f32_t(dpmm_ctx* c, uint64_t seed, int draw, const in
     a.draw = draw;
     a.P = q.P;
     a.G = q.G;
-    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.R = (c->N + c->Gr - 1) / c->Gr;
     a.L = c->st;
     a.rec = c->records;
     cudaError_t ea = cudaFuncSetAttribute(substats_f32_kernel<DV, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)q.smem);
     if (ea != cudaSuccess) return ea;
-    substats_f32_kernel<DV, XT><<<c->G2, q.BT, q.smem, c->stream>>>(a);
+    substats_f32_kernel<DV, XT><<<c->Gr, q.BT, q.smem, c->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1210,12 +1211,12 @@ static cudaError_t substats_mult_t(dpmm_ctx* c, uint64_t seed, int draw, const i
     a.draw = draw;
     a.P = P;
     a.G = G;
-    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.R = (c->N + c->Gr - 1) / c->Gr;
     a.L = L;
     a.rec = c->records;
     cudaError_t ea = cudaFuncSetAttribute(substats_mult_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ea != cudaSuccess) return ea;
-    substats_mult_kernel<XT><<<c->G2, 256, smem, c->stream>>>(a);
+    substats_mult_kernel<XT><<<c->Gr, 256, smem, c->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1244,14 +1245,14 @@ static cudaError_t substats_wide_t(dpmm_ctx* c, uint64_t seed, int draw, const i
     a.draw = draw;
     a.P = WP;
     a.G = 1;
-    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.R = (c->N + c->Gr - 1) / c->Gr;
     a.L = c->st;
     a.rec = c->records;
     const size_t smem = wide_smem(c);
     cudaError_t ea = cudaFuncSetAttribute(substats_wide_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);
     if (ea != cudaSuccess) return ea;
-    substats_wide_kernel<XT><<<c->G2, WIDE_T, smem, c->stream>>>(a);
+    substats_wide_kernel<XT><<<c->Gr, WIDE_T, smem, c->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1308,7 +1309,8 @@ cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate) {
 
 cudaError_t launch_init_labels(dpmm_ctx* c, uint64_t seed) {
     c->nlaunch += 1;
-    init_labels_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->init_K, seed, c->z, c->zbar);
+    init_labels_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->init_K, seed, c->diter, c->z,
+                                                                                c->zbar);
     return cudaGetLastError();
 }
 

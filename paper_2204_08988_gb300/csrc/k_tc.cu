@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const uint32_t iter = *a.diter;
-        Key key{a.seed, iter, 0};
+        Key key{a.seed, iter, a.diter[1]};
         int64_t ch = 0, it = 0;
         uint32_t nq = 0;  // uses of this quarter's draw barrier (the same in its four parts)
         bool ok = true;

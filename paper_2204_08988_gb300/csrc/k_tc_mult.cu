@@ -51,9 +51,10 @@ struct Args {
 };
 
 // one Gumbel-max draw (kept out of line: the unrolled epilogue must stay small)
-__device__ __noinline__ void gumbel_update(uint64_t seed, uint32_t iter, uint32_t i, int k, float sc, float* best,
+__device__ __noinline__ void gumbel_update(uint64_t seed, uint32_t iter, uint32_t prob, uint32_t i, int k, float sc,
+                                           float* best,
                                            int* zb) {
-    Key key{seed, iter, 0};
+    Key key{seed, iter, prob};
     uint32_t w[4];
     key.block(i, TAG_Z, (uint32_t)(k >> 1), w);
     const float u = u01_f32((k & 1) ? w[2] : w[0]);
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
             // cluster within the window gets its draw.
             float m1 = -INFINITY, m2 = -INFINITY;
             int k1 = 0;
-            const uint32_t iter = *a.diter;
+            const uint32_t iter = a.diter[0], prob = a.diter[1];
             const uint32_t tb = tmem + lane_off + (uint32_t)(b * 128);
             for (int k0 = 0; k0 < NB; k0 += 32) {
                 float y[32];
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
                         for (int j = 0; j < 32; ++j) {
                             const int k = k0 + j;
                             const float sc = k < K ? ct[k] + y[j] : -INFINITY;
-                            if (sc > lim) gumbel_update(a.seed, iter, (uint32_t)i, k, sc, &best, &zd);
+                            if (sc > lim) gumbel_update(a.seed, iter, prob, (uint32_t)i, k, sc, &best, &zd);
                         }
                     }
                 }

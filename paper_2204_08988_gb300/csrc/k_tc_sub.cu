@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
         // ------------------------------------------------------------ score warps
         const int q = warp & 3, r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        Key key{a.seed, *a.diter, 0};
+        Key key{a.seed, a.diter[0], a.diter[1]};
         float c0 = 0.f, c1 = 0.f;
         bool ok = true;
         int it = 0;
@@ -619,8 +619,8 @@ cudaError_t launch_substats_tc(dpmm_ctx* c, uint64_t seed, int draw, const int* 
     if (draw && !c->tcs_img) return cudaErrorNotSupported;
     tcs::Args a;
     a.N = c->N;
-    a.G = c->G2;
-    a.R = (c->N + c->G2 - 1) / c->G2;
+    a.G = c->Gr;
+    a.R = (c->N + c->Gr - 1) / c->Gr;
     a.d = c->d;
     a.dK = c->dK;
     a.starts = c->tot;
@@ -639,7 +639,7 @@ cudaError_t launch_substats_tc(dpmm_ctx* c, uint64_t seed, int draw, const int* 
     auto kern = draw ? tcs::substats_tc_kernel<true> : tcs::substats_tc_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcs::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(c->num_sms, c->G2);
+    const int grid = std::min(c->num_sms, c->Gr);
     kern<<<grid, tcs::NTHREADS, tcs::SMEM_BYTES, c->stream>>>(a);
     return cudaGetLastError();
 }

@@ -12,7 +12,10 @@ Workloads (sizes as the benchmark uses them):
   multinomial: d=200, N=1e6 count vectors of 100 draws, 50 topics with
                probabilities Dir(0.1 * 1), weights Dir(1); int32.
   gauss_d128 : d=128, N=1e7, 64 clusters, weights Dir(1), means N(0, 16 I),
-               covariances Wishart(I, d+2); BF16 storage.
+               covariances Wishart(I, d+2); FP32.
+  batched    : 512 independent mixtures, N log-uniform on [1e3, 1e6] (about 7.4e7
+               points in all), d drawn from {2, 8, 32, 64}, true K uniform on {2..30},
+               generated as gauss_d32; FP32 (batch_problems).
 """
 from __future__ import annotations
 
@@ -98,3 +101,18 @@ def workload(name, N=None, seed=None):
         prior = dict(kind=0, kappa0=1.0, m0=np.zeros(128), nu0=131.0, psi0=np.eye(128))
         return X, y, prior, dict(alpha=100.0)
     raise KeyError(name)
+
+
+def batch_problems(n_problems=512, seed=1005, N_min=1_000, N_max=1_000_000, dims=(2, 8, 32, 64)):
+    """The batched workload, one problem at a time: (X, y, d) with N log-uniform on
+    [N_min, N_max], d drawn from dims and the true K uniform on {2..30}; each problem is
+    generated like gauss_d32 (weights Dir(1), means N(0, 25 I), covariances Wishart(I, d+2))
+    with its own seed.  Prior per problem: NIW kappa0 = 1, m0 = 0, nu0 = d + 3, Psi0 = I;
+    alpha = 10."""
+    rng = np.random.default_rng(seed)
+    Ns = np.exp(rng.uniform(np.log(N_min), np.log(N_max), n_problems)).astype(np.int64)
+    ds = rng.choice(np.asarray(dims), n_problems)
+    Ks = rng.integers(2, 31, n_problems)
+    for p in range(n_problems):
+        X, y = gaussian_mixture(int(Ns[p]), int(ds[p]), int(Ks[p]), 5.0, seed=seed * 1000 + p)
+        yield X, y, int(ds[p])
