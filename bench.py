@@ -233,6 +233,21 @@ def main_batched(a):
     total_ms = float(sum(step_ms))
     Ks = [g.K for g in chains]
     value = N_tot * a.steps / (total_ms / 1e3)
+    breakdown = None
+    if a.breakdown:  # separate pass: events around every kernel of every chain, summed by kernel
+        for g in chains:
+            P.dpmm_profile(g.h, 1)
+        P.dpmm_sweep_batch(handles, a.steps, seed)
+        acc = {}
+        for g, (n, d) in zip(chains, sizes):
+            for k, (cnt, ms) in P.dpmm_get_profile(g.h).items():
+                if k == "all_kernels":
+                    continue
+                key = "%s@d%d" % (k, d)
+                acc.setdefault(key, 0.0)
+                acc[key] += ms / a.steps
+            P.dpmm_profile(g.h, 0)
+        breakdown = {k: round(v, 4) for k, v in sorted(acc.items(), key=lambda x: -x[1])}
     # roofline of the batch: each problem's label-step bound max(flops / the peak of its
     # arithmetic, bytes / HBM), summed over problems, against the measured time of a step
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -261,9 +276,12 @@ def main_batched(a):
                               sorted(mix.items())},
                       "K_max": K_max, "K_timed_mean": float(np.mean(Ks)), "burnin_sweeps": burn,
                       "init": "generating labels" if a.init_truth else "K=1", "parallelism": "1gpu, one stream per problem",
+                      "device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                       "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
            "roofline": roof, "cpu_baseline": None, "e2e": None, "clocks": clk.summary(), "gpu_launches": None,
            "step_ms": step_ms}
+    if breakdown is not None:
+        out["breakdown_stream_ms_per_step"] = breakdown
     print(json.dumps(out))
     for g in chains:
         g.close()
@@ -274,6 +292,10 @@ def main():
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
+        # one hardware work queue per stream (up to 32) instead of the default 8, so that
+        # the problems' streams do not serialise behind each other; read when the CUDA
+        # context is created, which has not happened yet
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
         return main_batched(a)
     import torch
 
