@@ -11,9 +11,11 @@
 // Gaussian kernel).  The data are read
 // once from HBM; the kernel is bandwidth-bound by design.
 //
-// CTA roles (192 threads, persistent): warp 0 TMA producer (X tiles of 128 rows, up to
-// four 128-byte K atoms, 2 stages), warp 1 TMEM owner and MMA issuer, warps 2-5
-// epilogue (one per TMEM lane quarter).  All waits are bounded.
+// CTA roles (192 threads, persistent): warp 0 TMA producer (X tiles of 128 rows as up to
+// four 128-byte K atoms, each atom its own stage of an 8-slot ring, so that up to
+// 128 KB of X are in flight per SM), warp 1 TMEM owner and MMA issuer (per atom: the
+// hi and the lo products, then the atom's slot is released), warps 2-5 epilogue (one
+// per TMEM lane quarter).  All waits are bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -28,7 +30,7 @@ namespace tcm {
 
 using namespace tc;
 
-constexpr int XST = 2;
+constexpr int XS = 8;              // X atom slots
 constexpr int ATOM = BM * 128;    // one K atom of an X tile: 128 rows x 128 B (64 BF16)
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 256;  // two 128-column accumulators
@@ -69,13 +71,13 @@ template <bool SCORES>
 __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_constant__ CUtensorMap xmap, Args a) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char* xs = base;                                              // XST x NA x ATOM
-    unsigned char* bs = xs + (size_t)XST * a.NA * ATOM;                    // 2 x NA x cap_rows x 128
+    unsigned char* xs = base;                                              // XS x ATOM
+    unsigned char* bs = xs + (size_t)XS * ATOM;                            // 2 x NA x cap_rows x 128
     float* ct = (float*)(bs + (size_t)2 * a.NA * a.cap_rows * 128);        // Kmax
     uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + a.Kmax) + 7) & ~(uintptr_t)7);
     uint64_t* full = bars;
-    uint64_t* empty = full + XST;
-    uint64_t* tfull = empty + XST;
+    uint64_t* empty = full + XS;
+    uint64_t* tfull = empty + XS;
     uint64_t* tempty = tfull + 2;
     uint64_t* bload = tempty + 2;
     __shared__ uint32_t tmem_base;
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
     const int64_t ntiles = (a.N + BM - 1) / BM;
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < XST; ++s) {
+        for (int s = 0; s < XS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -125,38 +127,40 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
             for (int q = 0; q < 2 * a.NA; ++q)
                 bulk_load(bs + (size_t)q * a.cap_rows * 128, (const unsigned char*)a.img + (size_t)q * a.cap_rows * 128,
                           rb, bload);
-            int64_t it = 0;
+            uint32_t ac = 0;  // atoms issued
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-                const int s = (int)(it % XST);
-                if (!mbar_wait(&empty[s], (uint32_t)(((it / XST) & 1) ^ 1), abort)) { ok = false; break; }
-                mbar_expect_tx(&full[s], (uint32_t)(a.NA * ATOM));
-                for (int at = 0; at < a.NA; ++at)
-                    tma_load_2d(xs + ((size_t)s * a.NA + at) * ATOM, &xmap, 64 * at, (int)(t * BM), &full[s]);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int at = 0; at < a.NA; ++at, ++ac) {
+                    const int s = (int)(ac % XS);
+                    if (!mbar_wait(&empty[s], ((ac / XS) & 1u) ^ 1u, abort)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], (uint32_t)ATOM);
+                    tma_load_2d(xs + (size_t)s * ATOM, &xmap, 64 * at, (int)(t * BM), &full[s]);
+                }
             }
             if (!ok) {
                 atomicExch(a.derr, (int)DPMM_ETIMEOUT);
                 *abort = 1;
             }
             mbar_wait(bload, 0, abort);
-            for (int64_t j = (it > XST ? it - XST : 0); j < it; ++j)
-                mbar_wait(&full[(int)(j % XST)], (uint32_t)((j / XST) & 1), abort);
+            for (uint32_t j = (ac > (uint32_t)XS ? ac - XS : 0); j < ac; ++j)
+                mbar_wait(&full[j % XS], (j / XS) & 1u, abort);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(bload, 0, abort);
             int64_t it = 0;
+            uint32_t ac = 0;  // atoms consumed
             const uint32_t id = idesc(NB, 1);  // BF16 x BF16 -> FP32
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-                const int s = (int)(it % XST);
                 const int b = (int)(it & 1);
-                if (!mbar_wait(&full[s], (uint32_t)((it / XST) & 1), abort)) { ok = false; break; }
                 if (!mbar_wait(&tempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), abort)) { ok = false; break; }
-                fence_after();
                 uint32_t acc = 0;
-                for (int half = 0; half < 2; ++half)
-                    for (int at = 0; at < a.NA; ++at) {
-                        const uint32_t xa = saddr(xs + ((size_t)s * a.NA + at) * ATOM);
+                for (int at = 0; at < a.NA; ++at, ++ac) {
+                    const int s = (int)(ac % XS);
+                    if (!mbar_wait(&full[s], (ac / XS) & 1u, abort)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t xa = saddr(xs + (size_t)s * ATOM);
+                    for (int half = 0; half < 2; ++half) {
                         const uint32_t ba = saddr(bs + ((size_t)half * a.NA + at) * a.cap_rows * 128);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
@@ -164,8 +168,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
                             acc = 1;
                         }
                     }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
                 mma_commit(&tfull[b]);
-                mma_commit(&empty[s]);
             }
             if (!ok) {
                 atomicExch(a.derr, (int)DPMM_ETIMEOUT);
@@ -189,8 +195,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
             // outside it the best cluster is the label whatever the Gumbel values, and no
             // draw is made.  Otherwise the accumulators (still held) are read again and every
             // cluster within the window gets its draw.
-            float m1 = -INFINITY, m2 = -INFINITY;
-            int k1 = 0;
+            // four independent best/second-best trackers (cluster k in tracker k % 4), merged
+            // at the end: a quarter of the dependent chain of one running maximum
+            float t1[4], t2[4];
+            int tk[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                t1[c] = t2[c] = -INFINITY;
+                tk[c] = c;
+            }
             const uint32_t iter = a.diter[0], prob = a.diter[1];
             const uint32_t tb = tmem + lane_off + (uint32_t)(b * 128);
             for (int k0 = 0; k0 < NB; k0 += 32) {
@@ -198,15 +211,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
                 tmem_ld32(tb + (uint32_t)k0, y);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int k = k0 + j;
+                    const int k = k0 + j, c = j & 3;
                     const float sc = k < K ? ct[k] + y[j] : -INFINITY;
                     if constexpr (SCORES) {
                         if (k < K && i < a.N) a.scores[i * K + k] = (double)sc;
                     }
-                    const bool gt = sc > m1;
-                    m2 = gt ? m1 : fmaxf(m2, sc);
-                    k1 = gt ? k : k1;
-                    m1 = gt ? sc : m1;
+                    const bool gt = sc > t1[c];
+                    t2[c] = gt ? t1[c] : fmaxf(t2[c], sc);
+                    tk[c] = gt ? k : tk[c];
+                    t1[c] = gt ? sc : t1[c];
+                }
+            }
+            float m1 = t1[0], m2 = t2[0];
+            int k1 = tk[0];
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {  // ties keep the lower cluster index
+                if (t1[c] > m1 || (t1[c] == m1 && tk[c] < k1)) {
+                    m2 = fmaxf(m1, t2[c]);
+                    m1 = t1[c];
+                    k1 = tk[c];
+                } else {
+                    m2 = fmaxf(m2, t1[c]);
                 }
             }
             const float lim = m1 - WINDOW;
@@ -280,7 +305,7 @@ struct MultCfg {
 static MultCfg mult_cfg(const dpmm_ctx* c) {
     MultCfg q;
     q.NA = (c->d + 63) / 64;
-    const size_t fixed = 1024 + (size_t)tcm::XST * q.NA * tcm::ATOM + (size_t)c->K_max * 4 + 16 * 8 + 64;
+    const size_t fixed = 1024 + (size_t)tcm::XS * tcm::ATOM + (size_t)c->K_max * 4 + (2 * tcm::XS + 5) * 8 + 64;
     const size_t limit = 227 * 1024 - 4096;
     const size_t per_row = (size_t)2 * q.NA * 128;
     int cap = (int)((limit - fixed) / per_row);
