@@ -2,8 +2,8 @@
 // (sub-)cluster's statistics block in shared memory and a right-looking Cholesky
 // factorisation written for GB300's FP64 pipe (about two operations per clock per SM,
 // 64-cycle dependent latency): the only serial work per pivot is one reciprocal square
-// root; the trailing update has no square roots or divisions and issues its loads in
-// batches so that independent FMAs overlap.
+// root; the trailing update (balanced row pairs) has no square roots or divisions in its
+// indexing and issues its loads in batches so that independent FMAs overlap.
 #pragma once
 #include "dpmm_internal.cuh"
 
@@ -26,6 +26,48 @@ __device__ inline void tri_index(int e, int& i0, int& l0) {
     l0 = e - i * (i + 1) / 2;
 }
 
+// Trailing update of pivot j: A_il -= col_i A_lj for j < l <= i < d.  Rows are taken in
+// pairs (j + 1 + p, d - 1 - p), which together hold m + 1 entries (m = d - j - 1), so every
+// pair carries the same work; each pair is split over S threads (entries s, s + S, ...,
+// consecutive threads on consecutive columns of a row), and each thread keeps four
+// entries' loads in flight.  No index needs a square root or a division.  Every entry
+// gets the single FMA fma(-col_i, A_lj, A_il), as in any enumeration order.
+template <typename T>
+__device__ inline void chol_update(T* A, int d, int ld, int j, const T* col) {
+    const int m = d - j - 1;
+    if (m <= 0) return;
+    const int np = (m + 1) >> 1, nt = blockDim.x;
+    int S = nt / np;
+    S = S < 1 ? 1 : (S > 8 ? 8 : S);
+    for (int w = threadIdx.x; w < np * S; w += nt) {
+        const int p = w / S, s = w - p * S;
+        const int r1 = j + 1 + p, r2 = d - 1 - p;
+        const int n1 = r1 - j, n = r2 > r1 ? n1 + (r2 - j) : n1;
+        const T c1 = col[r1], c2 = col[r2];
+        for (int e0 = s; e0 < n; e0 += 4 * S) {
+            T av[4], cl[4];
+            int at[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * S;
+                at[u] = -1;
+                if (e < n) {
+                    const bool first = e < n1;
+                    const int i = first ? r1 : r2, l = j + 1 + (first ? e : e - n1);
+                    at[u] = i * ld + l;
+                    av[u] = A[at[u]];
+                    cl[u] = A[l * ld + j];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * S;
+                if (at[u] >= 0) A[at[u]] = fma(-(e < n1 ? c1 : c2), cl[u], av[u]);
+            }
+        }
+    }
+}
+
 // In-place factorisation of the symmetric matrix whose lower triangle is in A (d x d,
 // row-major with row stride ld, shared memory; an odd ld keeps the column reads free of
 // bank conflicts).  Pivot j is v_j = the (j, j) entry of the Schur complement;
@@ -36,7 +78,7 @@ __device__ inline void tri_index(int e, int& i0, int& l0) {
 // col (d doubles of shared memory) is scratch.  Every thread of the block calls it; two
 // barriers per pivot.  Each FP64 warp instruction costs the pipe about the same whether
 // or not its lanes are busy, so warp 0 forms the pivot and the scaled column (one lane
-// per row) and the update enumerates only the lower triangle, one FMA per entry.
+// per row) and the update touches only the lower triangle, one FMA per entry.
 __device__ inline void chol_ldl(double* A, int d, int ld, double* piv, double* rs, double* col, int* derr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = 0; j < d; ++j) {
@@ -54,28 +96,7 @@ __device__ inline void chol_ldl(double* A, int d, int ld, double* piv, double* r
             }
         }
         __syncthreads();
-        const int m = d - j - 1, tri = m * (m + 1) / 2;
-        for (int e0 = tid; e0 < tri; e0 += 4 * nt) {
-            double av[4], ci[4], cl[4];
-            int at[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * nt;
-                at[u] = -1;
-                if (e < tri) {
-                    int i0, l0;
-                    tri_index(e, i0, l0);
-                    const int i = j + 1 + i0, l = j + 1 + l0;
-                    at[u] = i * ld + l;
-                    av[u] = A[at[u]];
-                    ci[u] = col[i];
-                    cl[u] = A[l * ld + j];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (at[u] >= 0) A[at[u]] = fma(-ci[u], cl[u], av[u]);
-        }
+        chol_update<double>(A, d, ld, j, col);
         __syncthreads();
     }
 }
@@ -107,28 +128,7 @@ __device__ inline void chol_ldl_t(T* A, int d, int ld, T* piv, T* rs, T* col, co
             }
         }
         __syncthreads();
-        const int m = d - j - 1, tri = m * (m + 1) / 2;
-        for (int e0 = tid; e0 < tri; e0 += 4 * nt) {
-            T av[4], ci[4], cl[4];
-            int at[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * nt;
-                at[u] = -1;
-                if (e < tri) {
-                    int i0, l0;
-                    tri_index(e, i0, l0);
-                    const int i = j + 1 + i0, l = j + 1 + l0;
-                    at[u] = i * ld + l;
-                    av[u] = A[at[u]];
-                    ci[u] = col[i];
-                    cl[u] = A[l * ld + j];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (at[u] >= 0) A[at[u]] = fma(-ci[u], cl[u], av[u]);
-        }
+        chol_update<T>(A, d, ld, j, col);
         __syncthreads();
     }
 }
