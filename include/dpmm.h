@@ -104,14 +104,18 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
 dpmm_status dpmm_set_options(dpmm_ctx* ctx, dpmm_prec prec, int init_K, int burn_out, void* cuda_stream);
 
 /* Data: N x d row-major of type dt.  The library copies and converts it into its
- * own device buffer (FP64 for FP64_PLAIN, FP32 for FP32/TF32, BF16 for BF16;
+ * own device buffer (FP64 for FP64_PLAIN, FP32 for FP32/TF32/BF16X3, BF16 for BF16;
  * Gaussian data is centred by its mean, an exact reparameterisation undone in
- * every output).  Resets the chain: the labels are drawn at the next sweep.
+ * every output).  X is device memory (on_device = 1) or host memory: page-locked
+ * host memory is read in place by the conversion kernels, pageable memory is first
+ * staged in device memory.  Resets the chain: the labels are drawn at the next sweep.
  * Errors: DPMM_EINVAL (N < 1, NULL X, type not allowed for the prior). */
 dpmm_status dpmm_set_data(dpmm_ctx* ctx, const void* X, int64_t N, dpmm_dtype dt, int on_device);
 
 /* Replace the values of the data (same N, d, dtype) and keep the chain's state.
- * Used for streaming data and for end-to-end timing with host-resident inputs. */
+ * Used for streaming data and for end-to-end timing with host-resident inputs.
+ * Asynchronous on the context's stream: a host buffer must keep its values until
+ * the next synchronising call (e.g. dpmm_get_labels). */
 dpmm_status dpmm_update_data(dpmm_ctx* ctx, const void* X, dpmm_dtype dt, int on_device);
 
 /* Run `iters` sweeps (Sec. 4.1) with Philox key `seed`.  The sweep counter

@@ -167,9 +167,17 @@ static dpmm_status upload(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_devi
     const void* src = X;
     void* tmp = nullptr;
     if (!on_device) {
-        CK(c, cudaMallocAsync(&tmp, bytes, c->stream));
-        CK(c, cudaMemcpyAsync(tmp, X, bytes, cudaMemcpyHostToDevice, c->stream));
-        src = tmp;
+        // page-locked host memory is read by the conversion kernels in place (one pass over
+        // the interconnect, no staging copy); pageable memory is staged in device memory
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, X) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+            src = at.devicePointer;
+        } else {
+            cudaGetLastError();
+            CK(c, cudaMallocAsync(&tmp, bytes, c->stream));
+            CK(c, cudaMemcpyAsync(tmp, X, bytes, cudaMemcpyHostToDevice, c->stream));
+            src = tmp;
+        }
     }
     cudaError_t e;
     switch (dt) {
