@@ -91,11 +91,13 @@ typedef enum {
 } dpmm_prec;
 
 /* Create a chain.  alpha > 0 is the DP concentration (Eq. DPLatentVar); d >= 1
- * the dimension; K_max >= 1 the capacity for clusters (a split that would exceed
- * it is rejected and counted, Sec. 4.1 "Propose and accept splits").
- * Errors: DPMM_EINVAL for invalid hyper-parameters (kappa0 <= 0, nu0 <= d - 1,
- * Psi0 not SPD, beta_j <= 0, alpha <= 0, d < 1, K_max < 1), DPMM_ECUDA without a
- * usable device.  *out is NULL on error. */
+ * the dimension (at most 256 for the NIW prior, 4092 for the Dirichlet prior);
+ * 1 <= K_max <= 1000 the capacity for clusters (a split that would exceed it is
+ * rejected and counted, Sec. 4.1 "Propose and accept splits").
+ * Errors: DPMM_EINVAL for invalid hyper-parameters or sizes (kappa0 <= 0,
+ * nu0 <= d - 1, Psi0 not symmetric positive definite, beta_j <= 0, alpha <= 0, d or
+ * K_max out of range), DPMM_ECUDA without a usable sm_103 device, DPMM_ENOMEM when
+ * the device tables (O(K_max d^2) doubles) do not fit.  *out is NULL on error. */
 dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max, dpmm_ctx** out);
 
 /* Options; call before dpmm_set_data.  init_K: clusters at start (Sec. 3.4
@@ -140,6 +142,14 @@ dpmm_status dpmm_set_problem(dpmm_ctx* ctx, uint32_t problem);
  * failing context's status (the remaining contexts of that round are not queued);
  * DPMM_EINVAL for a NULL array or entry, n < 0 or iters < 0. */
 dpmm_status dpmm_sweep_batch(dpmm_ctx* const* ctxs, int n, int iters, uint64_t seed);
+
+/* Failure-detection check (no counterpart in the paper): runs one kernel whose
+ * bounded mbarrier wait cannot complete (nothing arrives on the barrier), with the
+ * same bounded wait every tensor-core kernel uses.  The wait gives up after its poll
+ * or cycle limit (about one second) and the kernel records DPMM_ETIMEOUT in the
+ * context's device error word, which this call reads and clears.  Returns
+ * DPMM_ETIMEOUT when the mechanism works; the context stays usable.  Synchronises. */
+dpmm_status dpmm_check_wait_timeout(dpmm_ctx* ctx);
 
 /* Labels into caller-owned host arrays of length N (z in [0, K), zbar in {0,1}).
  * Either pointer may be NULL.  Synchronises. */

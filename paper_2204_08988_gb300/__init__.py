@@ -32,7 +32,7 @@ EXPORTS = [
     "dpmm_get_stats", "dpmm_get_info", "dpmm_get_counters", "dpmm_last_error", "dpmm_destroy",
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
     "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
-    "dpmm_sweep_batch",
+    "dpmm_sweep_batch", "dpmm_check_wait_timeout",
 ]
 
 
@@ -84,6 +84,7 @@ def load():
             "dpmm_label_scores": ([vp, vp], i32),
             "dpmm_set_problem": ([vp, u32], i32),
             "dpmm_sweep_batch": ([vp, i32, i32, u64], i32),
+            "dpmm_check_wait_timeout": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -106,9 +107,10 @@ def _check(h, st):
 # ------------------------------------------------------------- C-named wrappers
 def dpmm_create(kind, d, K_max, alpha, kappa0=1.0, m0=None, nu0=None, psi0=None, beta=None):
     L = load()
-    m0 = np.ascontiguousarray(np.zeros(d) if m0 is None else m0, dtype=np.float64)
-    psi0 = np.ascontiguousarray(np.eye(d) if psi0 is None else psi0, dtype=np.float64)
-    beta = np.ascontiguousarray(np.ones(d) if beta is None else beta, dtype=np.float64)
+    niw = kind == PRIOR_NIW  # the prior's unused fields get a one-element placeholder
+    m0 = np.ascontiguousarray((np.zeros(d) if niw else np.zeros(1)) if m0 is None else m0, dtype=np.float64)
+    psi0 = np.ascontiguousarray((np.eye(d) if niw else np.ones(1)) if psi0 is None else psi0, dtype=np.float64)
+    beta = np.ascontiguousarray((np.ones(d) if not niw else np.ones(1)) if beta is None else beta, dtype=np.float64)
     pr = _Prior(kind, float(kappa0), m0.ctypes.data, float(d + 3 if nu0 is None else nu0), psi0.ctypes.data,
                 beta.ctypes.data)
     h = C.c_void_p()
@@ -194,6 +196,11 @@ def dpmm_set_iter(h, it):
 
 def dpmm_set_problem(h, problem):
     _check(h, load().dpmm_set_problem(h, int(problem)))
+
+
+def dpmm_check_wait_timeout(h):
+    """Status of the bounded-wait check (DPMM_ETIMEOUT when device waits end as designed)."""
+    return int(load().dpmm_check_wait_timeout(h))
 
 
 def dpmm_sweep_batch(handles, iters, seed):

@@ -504,6 +504,12 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
     return DPMM_OK;
 }
 
+dpmm_status dpmm_check_wait_timeout(dpmm_ctx* c) {
+    if (!c) return DPMM_EINVAL;
+    CK(c, launch_wait_selftest(c));
+    return check_derr(c);
+}
+
 dpmm_status dpmm_set_problem(dpmm_ctx* c, uint32_t problem) {
     if (!c) return DPMM_EINVAL;
     CK(c, cudaMemcpyAsync(c->diter + 1, &problem, sizeof(problem), cudaMemcpyHostToDevice, c->stream));

@@ -276,6 +276,7 @@ bool x3_supported(const dpmm_ctx* c);
 cudaError_t x3_prepare_data(dpmm_ctx* c);
 cudaError_t x3_prepare(dpmm_ctx* c);
 cudaError_t launch_labels_x3(dpmm_ctx* c, uint64_t seed);
+cudaError_t launch_wait_selftest(dpmm_ctx* c);
 
 // profiling helpers (no-ops unless enabled)
 void prof_begin(dpmm_ctx* c, const char* name);

@@ -9,7 +9,8 @@ namespace dpmm {
 namespace tc {
 
 constexpr int BM = 128;                 // points per tile (MMA M)
-constexpr uint32_t SPIN = 1u << 22;     // bounded waits (a few seconds at most)
+constexpr uint32_t SPIN = 1u << 22;     // bounded waits: at most this many polls ...
+constexpr long long WAIT_CYCLES = 1ll << 31;  // ... and at most this many SM cycles (about 1 s)
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -31,11 +32,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false on timeout or when another role has aborted
+// bounded wait; false on timeout or when another role has aborted.  The SM clock bounds
+// the wall time whatever the hardware's suspension inside one try_wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
     for (uint32_t it = 0; it < SPIN; ++it) {
         if (mbar_try(b, parity)) return true;
         if ((it & 1023u) == 1023u && *abort) return false;
+        if (clock64() - t0 > WAIT_CYCLES) return false;
     }
     return false;
 }
