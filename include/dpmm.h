@@ -143,6 +143,22 @@ dpmm_status dpmm_set_problem(dpmm_ctx* ctx, uint32_t problem);
  * DPMM_EINVAL for a NULL array or entry, n < 0 or iters < 0. */
 dpmm_status dpmm_sweep_batch(dpmm_ctx* const* ctxs, int n, int iters, uint64_t seed);
 
+/* Checkpoint and resume.  A checkpoint holds everything the next sweep reads, taken
+ * at a sweep boundary: K, the sweep counter, the problem id, the labels z and zbar,
+ * the cluster ages (split eligibility, Sec. 3.4 burn_out), the sufficient-statistics
+ * table with its per-cluster reference shift, and the last weights and split/merge
+ * counters.  The parameters are redrawn from the statistics at every sweep (Sec. 4.1
+ * steps (a)-(d)) and the random streams are counter-based, so loading a checkpoint
+ * into a context with the same prior kind, d, N and data (dpmm_set_data first)
+ * continues the chain exactly as if it had never stopped (default step mask).
+ * The checkpoint is one host byte buffer of dpmm_checkpoint_size bytes (it grows
+ * with K), owned by the caller.  Errors: DPMM_ESTATE without a chain (save) or data
+ * (load); DPMM_EINVAL for a short buffer, a buffer that is not a checkpoint, one of
+ * another prior, dimension or N, or labels out of range.  All three synchronise. */
+dpmm_status dpmm_checkpoint_size(dpmm_ctx* ctx, size_t* bytes);
+dpmm_status dpmm_save_checkpoint(dpmm_ctx* ctx, void* buf, size_t bytes);
+dpmm_status dpmm_load_checkpoint(dpmm_ctx* ctx, const void* buf, size_t bytes);
+
 /* Failure-detection check (no counterpart in the paper): runs one kernel whose
  * bounded mbarrier wait cannot complete (nothing arrives on the barrier), with the
  * same bounded wait every tensor-core kernel uses.  The wait gives up after its poll

@@ -32,7 +32,8 @@ EXPORTS = [
     "dpmm_get_stats", "dpmm_get_info", "dpmm_get_counters", "dpmm_last_error", "dpmm_destroy",
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
     "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
-    "dpmm_sweep_batch", "dpmm_check_wait_timeout",
+    "dpmm_sweep_batch", "dpmm_check_wait_timeout", "dpmm_checkpoint_size", "dpmm_save_checkpoint",
+    "dpmm_load_checkpoint",
 ]
 
 
@@ -85,6 +86,9 @@ def load():
             "dpmm_set_problem": ([vp, u32], i32),
             "dpmm_sweep_batch": ([vp, i32, i32, u64], i32),
             "dpmm_check_wait_timeout": ([vp], i32),
+            "dpmm_checkpoint_size": ([vp, C.POINTER(C.c_size_t)], i32),
+            "dpmm_save_checkpoint": ([vp, vp, C.c_size_t], i32),
+            "dpmm_load_checkpoint": ([vp, vp, C.c_size_t], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -196,6 +200,20 @@ def dpmm_set_iter(h, it):
 
 def dpmm_set_problem(h, problem):
     _check(h, load().dpmm_set_problem(h, int(problem)))
+
+
+def dpmm_save_checkpoint(h):
+    """The chain's checkpoint as bytes."""
+    n = C.c_size_t()
+    _check(h, load().dpmm_checkpoint_size(h, C.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(h, load().dpmm_save_checkpoint(h, _p(buf), n.value))
+    return buf.tobytes()
+
+
+def dpmm_load_checkpoint(h, data):
+    buf = np.frombuffer(data, dtype=np.uint8).copy()
+    _check(h, load().dpmm_load_checkpoint(h, _p(buf), buf.size))
 
 
 def dpmm_check_wait_timeout(h):
@@ -324,6 +342,12 @@ class DPMM:
 
     def set_problem(self, problem):
         dpmm_set_problem(self.h, problem)
+
+    def checkpoint(self):
+        return dpmm_save_checkpoint(self.h)
+
+    def restore(self, data):
+        dpmm_load_checkpoint(self.h, data)
 
     def set_params(self, K, p):
         if self.kind == PRIOR_NIW:

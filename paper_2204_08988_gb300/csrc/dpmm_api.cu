@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dpmm_internal.cuh"
 
 using namespace dpmm;
@@ -19,7 +21,11 @@ static bool prof_on(const dpmm_ctx* c, const char* name) {
     return c->profiling == 1 || (c->profiling == 2 && strncmp(name, "labels", 6) == 0);
 }
 
+// Every kernel group is also an NVTX range (named after the step) on the host thread that
+// enqueues it, for timeline and ncu --nvtx filtering; ranges are recorded when the sweep is
+// enqueued eagerly or captured, not when a captured graph is replayed.
 void prof_begin(dpmm_ctx* c, const char* name) {
+    nvtxRangePushA(name);
     if (!prof_on(c, name)) return;
     Profile* p = nullptr;
     for (auto& q : c->prof)
@@ -36,6 +42,7 @@ void prof_begin(dpmm_ctx* c, const char* name) {
 }
 
 void prof_end(dpmm_ctx* c, const char* name) {
+    nvtxRangePop();
     if (!prof_on(c, name)) return;
     for (auto& q : c->prof)
         if (q.name == name) {
@@ -501,6 +508,120 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
         }
     }
     c->seed = seed;
+    return DPMM_OK;
+}
+
+// ---- checkpoint: [header | z (N int32) | zbar (N bytes) | ages (K int32) | counters
+// (8 int32) | statistics (2K x E doubles) | shift (K x d doubles) | weights (K doubles)],
+// every array padded to a multiple of 8 bytes
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version;
+    int32_t kind, d, E;
+    int64_t N;
+    int32_t K;
+    uint32_t iter, problem;
+    int32_t pad;
+};
+static const uint64_t CKPT_MAGIC = 0x54504b434d4d5044ull;  // "DPMMCKPT"
+
+static size_t ckpt_bytes(const dpmm_ctx* c, int K) {
+    auto up8 = [](size_t b) { return (b + 7) / 8 * 8; };
+    return sizeof(CkptHeader) + up8((size_t)c->N * 4) + up8((size_t)c->N) + up8((size_t)K * 4) + 8 * 4 +
+           8 * ((size_t)2 * K * c->st.E + (size_t)K * c->d + K);
+}
+
+static dpmm_status ckpt_state(dpmm_ctx* c) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X || !c->initialized) return fail(c, DPMM_ESTATE, "no chain to checkpoint");
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_checkpoint_size(dpmm_ctx* c, size_t* bytes) {
+    dpmm_status st = ckpt_state(c);
+    if (st != DPMM_OK) return st;
+    if (!bytes) return fail(c, DPMM_EINVAL, "null output");
+    int K = 0;
+    CK(c, cudaMemcpyAsync(&K, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *bytes = ckpt_bytes(c, K);
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_save_checkpoint(dpmm_ctx* c, void* buf, size_t bytes) {
+    dpmm_status st = ckpt_state(c);
+    if (st != DPMM_OK) return st;
+    CkptHeader h{};
+    uint32_t it[2] = {0, 0};
+    CK(c, cudaMemcpyAsync(&h.K, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(it, c->diter, sizeof(it), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (!buf || bytes < ckpt_bytes(c, h.K)) return fail(c, DPMM_EINVAL, "checkpoint buffer too small");
+    h.magic = CKPT_MAGIC;
+    h.version = 1;
+    h.kind = c->kind;
+    h.d = c->d;
+    h.E = c->st.E;
+    h.N = c->N;
+    h.iter = it[0];
+    h.problem = it[1];
+    unsigned char* q = (unsigned char*)buf;
+    memcpy(q, &h, sizeof(h));
+    q += sizeof(h);
+    const int K = h.K;
+    auto D2H = [&](void* dst, const void* src, size_t n, size_t padded) {
+        if (n) CK(c, cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream));
+        if (padded > n) memset((unsigned char*)dst + n, 0, padded - n);
+        q += padded;
+        return DPMM_OK;
+    };
+    auto up8 = [](size_t b) { return (b + 7) / 8 * 8; };
+    const void* src[7] = {c->z, c->zbar, c->age, c->counters, c->stats, c->shift_stats, c->cweights};
+    const size_t len[7] = {(size_t)c->N * 4, (size_t)c->N, (size_t)K * 4, 8 * 4, (size_t)2 * K * c->st.E * 8,
+                           (size_t)K * c->d * 8, (size_t)K * 8};
+    for (int a = 0; a < 7; ++a)
+        if ((st = D2H(q, src[a], len[a], up8(len[a]))) != DPMM_OK) return st;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_derr(c);
+}
+
+dpmm_status dpmm_load_checkpoint(dpmm_ctx* c, const void* buf, size_t bytes) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
+    CkptHeader h{};
+    if (!buf || bytes < sizeof(h)) return fail(c, DPMM_EINVAL, "checkpoint too short");
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != CKPT_MAGIC || h.version != 1) return fail(c, DPMM_EINVAL, "not a checkpoint of this format");
+    if (h.kind != c->kind || h.d != c->d || h.E != c->st.E || h.N != c->N)
+        return fail(c, DPMM_EINVAL, "checkpoint of another prior, dimension or data size");
+    if (h.K < 1 || h.K > c->K_max || bytes < ckpt_bytes(c, h.K))
+        return fail(c, DPMM_EINVAL, "checkpoint size or K out of range");
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+    const unsigned char* q = (const unsigned char*)buf + sizeof(h);
+    const int K = h.K;
+    auto up8 = [](size_t b) { return (b + 7) / 8 * 8; };
+    auto H2D = [&](void* dst, size_t n, size_t padded) {
+        if (n) CK(c, cudaMemcpy(dst, q, n, cudaMemcpyHostToDevice));
+        q += padded;
+        return DPMM_OK;
+    };
+    // labels out of range would be used as addresses by the sort: check them on the host
+    const int32_t* zh = (const int32_t*)q;
+    for (int64_t i = 0; i < c->N; ++i)
+        if (zh[i] < 0 || zh[i] >= K) return fail(c, DPMM_EINVAL, "checkpoint label out of range");
+    const uint32_t it[2] = {h.iter, h.problem};
+    CK(c, cudaMemcpy(c->dK, &h.K, sizeof(int), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->diter, it, sizeof(it), cudaMemcpyHostToDevice));
+    void* dst[7] = {c->z, c->zbar, c->age, c->counters, c->stats, c->shift_stats, c->cweights};
+    const size_t len[7] = {(size_t)c->N * 4, (size_t)c->N, (size_t)K * 4, 8 * 4, (size_t)2 * K * c->st.E * 8,
+                           (size_t)K * c->d * 8, (size_t)K * 8};
+    for (int a = 0; a < 7; ++a) {
+        const dpmm_status st = H2D(dst[a], len[a], up8(len[a]));
+        if (st != DPMM_OK) return st;
+    }
+    c->initialized = true;
+    c->h_iter = h.iter;
     return DPMM_OK;
 }
 
