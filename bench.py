@@ -176,6 +176,20 @@ def run_reference(a):
     print(json.dumps(out))
 
 
+def job_rate(local_ms, n_points, steps, world, dist=None):
+    """Whole-job rate over `world` replicas that each swept n_points `steps` times: the
+    slowest rank's time (max over ranks through the process group) bounds the job.
+    Returns (point-sweeps per second, max milliseconds)."""
+    ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * n_points * steps / (ms / 1e3), ms
+
+
 def batch_prec(d):
     """Precision of a batched problem: FP32 CUDA cores for d <= 8, TF32 tensor cores for
     d <= 32, split BF16 tensor cores above."""
@@ -358,11 +372,7 @@ def main():
     total_ms = float(sum(step_ms))
     prof = P.dpmm_get_profile(g.h)
     P.dpmm_profile(g.h, 0)
-    if dist:
-        t = torch.tensor([total_ms])
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * N * a.steps / (total_ms / 1e3)
+    value, total_ms = job_rate(total_ms, N, a.steps, world, dist)
 
     # roofline of the dominant kernel: the label step
     lk = [k for k in prof if k.startswith("labels")]

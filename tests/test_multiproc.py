@@ -1,0 +1,48 @@
+"""The multi-replica timing of bench.py on CPU: two gloo ranks (127.0.0.1), each with its
+own local time; the job rate uses the slowest rank's time and the total points of all
+replicas, the same on every rank."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, local_ms, out):
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        value, ms = bench.job_rate(local_ms[rank], 1000, 5, world, dist)
+        out[rank] = (value, ms)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_job_rate_takes_the_slowest_rank():
+    world, port = 2, _free_port()
+    local_ms = [40.0, 50.0]
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, port, local_ms, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        value, ms = res[r]
+        assert ms == pytest.approx(50.0)
+        assert value == pytest.approx(world * 1000 * 5 / 0.050)
+
+
+def test_job_rate_single_process():
+    import bench
+
+    value, ms = bench.job_rate(20.0, 100, 4, 1)
+    assert ms == 20.0 and value == pytest.approx(100 * 4 / 0.020)
