@@ -624,11 +624,13 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
 }
 
 // FP32 variant for 64 < d <= 128 (Gaussian).  Per batch of WP = 64 points (sorted by
-// cluster): each sub-cluster score is the squared norm of (x - mu_h) W_h, computed for
-// the whole batch as one register-tiled product in shared memory (warps 0-7: each
-// thread owns 8 points x 4 columns; per K step two broadcast float4 loads of
-// (x - mu)^T and one float4 of W feed 32 FMAs; W is staged once per cluster run, zero
-// below the diagonal and beyond d, so the loop needs no triangular bound).  Statistics: one 4x4 register block per
+// cluster): each sub-cluster score is the squared norm of (x - mu_h) W_h
+// = (x - shift) W_h - bh, with bh = (mu_h - shift)^T W_h formed once per cluster run and
+// shift the cluster's statistics centre; both products run at once over the shifted rows
+// (warps 0-7 sub-cluster 0, warps 8-15 sub-cluster 1; each thread owns 8 points x 4
+// columns; per K step two broadcast float4 loads of (x - shift)^T and one float4 of W
+// feed 32 FMAs; W is staged once per cluster run, zero below the diagonal and beyond d,
+// so the loop needs no triangular bound).  Statistics: one 4x4 register block per
 // worker thread (nblk <= 561 workers, so every block has one owner and is written
 // straight to the records) and one accumulator set per sub-cluster (warp-uniform
 // branch on h).  Dynamic shared memory: 2 x 128 x 128 floats (W_l, W_r), 128 x WP
@@ -642,11 +644,12 @@ __global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float>
     extern __shared__ __align__(16) unsigned char smraw[];
     const int d = a.d, dp = a.L.dp, nblk = a.L.nblk;
     float* Ws = (float*)smraw;              // 2 x 128 x 128: W_h[l][j]
-    float* Tt = Ws + 2 * 128 * 128;         // 128 x WP: (x_p - mu_h)_l at Tt[l * WP + p]
+    float* Tt = Ws + 2 * 128 * 128;         // 128 x WP: (x_p - shift)_l at Tt[l * WP + p]
     float* xs = Tt + 128 * WP;              // WP x dp
     float* qv = xs + WP * dp;               // WP x 2
     float* mus = qv + 2 * WP;               // 2 x 128
-    float* shf = mus + 256;                 // 128
+    float* bh = mus + 256;                  // 2 x 128
+    float* shf = bh + 256;                  // 128
     float* cc = shf + 128;                  // 2 (+2 pad)
     int* kq = (int*)(cc + 4);               // WP
     int* runs = kq + WP;                    // WP + 1
@@ -716,47 +719,72 @@ __global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float>
                 if (tid < 2) cc[tid] = a.pv.c[3 * k + 1 + tid];
                 for (int j = tid; j < 128; j += nt) shf[j] = j < d ? a.shift[(size_t)k * d + j] : 0.f;
                 __syncthreads();
+                // bh[h][j] = sum_l (mu_h - shift)_l W_h[l][j]: the products below run on the
+                // shifted rows x - shift, so y_h = (x - shift) W_h - bh
+                for (int e = tid; e < 256; e += nt) {
+                    const int h = e >> 7, j = e & 127;
+                    const float* Wh = Ws + h * 128 * 128;
+                    float b = 0.f;
+                    for (int l = 0; l < d; ++l) b = fmaf(mus[h * 128 + l] - shf[l], Wh[l * 128 + j], b);
+                    bh[e] = b;
+                }
+                __syncthreads();
                 if (tid == 0) staged = k;
             }
+            // the run's rows shifted by the cluster's centre, then 1, then zeros (the
+            // statistics read them too)
+            for (int e = tid; e < (qe - qs) * dp; e += nt) {
+                const int q = qs + e / dp, j = e % dp;
+                float* xr = xs + (size_t)q * dp;
+                xr[j] = j < d ? xr[j] - shf[j] : (j == d ? 1.f : 0.f);
+            }
             if (a.draw) {
-                for (int h = 0; h < 2; ++h) {
-                    __syncthreads();
-                    for (int e = tid; e < 128 * WP; e += nt) {
-                        const int l = e / WP, p = e % WP;
-                        Tt[e] = (l < d && p >= qs && p < qe) ? xs[(size_t)p * dp + l] - mus[h * 128 + l] : 0.f;
-                    }
-                    __syncthreads();
-                    if (tid < 256) {  // warps 0-7: Y = (X - mu_h) W_h for the batch
-                        const int pg = tid >> 5, cg = lane;  // points 8 pg .. 8 pg + 7, columns 4 cg .. 4 cg + 3
-                        float y[8][4];
+                __syncthreads();
+                for (int e = tid; e < 128 * WP; e += nt) {
+                    const int l = e / WP, p = e % WP;
+                    Tt[e] = (l < d && p >= qs && p < qe) ? xs[(size_t)p * dp + l] : 0.f;
+                }
+                __syncthreads();
+                if (tid < 512) {  // warps 0-7: sub-cluster 0, warps 8-15: sub-cluster 1
+                    const int h = warp >> 3;
+                    const int pg = warp & 7, cg = lane;  // points 8 pg .. 8 pg + 7, columns 4 cg .. 4 cg + 3
+                    float y[8][4];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) y[u][v] = 0.f;
+                    const float* Wh = Ws + h * 128 * 128;
+                    for (int l = 0; l < d; ++l) {
+                        const float4 t0 = *(const float4*)(Tt + l * WP + pg * 8);
+                        const float4 t1 = *(const float4*)(Tt + l * WP + pg * 8 + 4);
+                        const float4 w0 = *(const float4*)(Wh + l * 128 + cg * 4);
+                        const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                        const float wv[4] = {w0.x, w0.y, w0.z, w0.w};
 #pragma unroll
                         for (int u = 0; u < 8; ++u)
 #pragma unroll
-                            for (int v = 0; v < 4; ++v) y[u][v] = 0.f;
-                        const float* Wh = Ws + h * 128 * 128;
-                        for (int l = 0; l < d; ++l) {
-                            const float4 t0 = *(const float4*)(Tt + l * WP + pg * 8);
-                            const float4 t1 = *(const float4*)(Tt + l * WP + pg * 8 + 4);
-                            const float4 w0 = *(const float4*)(Wh + l * 128 + cg * 4);
-                            const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-                            const float wv[4] = {w0.x, w0.y, w0.z, w0.w};
+                            for (int v = 0; v < 4; ++v) y[u][v] = fmaf(tv[u], wv[v], y[u][v]);
+                    }
+                    const float4 b4 = *(const float4*)(bh + h * 128 + cg * 4);
+                    const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+                    float qp[8];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u)
+                    for (int u = 0; u < 8; ++u) {
+                        float s0 = 0.f;
 #pragma unroll
-                                for (int v = 0; v < 4; ++v) y[u][v] = fmaf(tv[u], wv[v], y[u][v]);
+                        for (int v = 0; v < 4; ++v) {
+                            const float t = y[u][v] - bv[v];
+                            s0 = fmaf(t, t, s0);
                         }
-                        float qp[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            qp[u] = fmaf(y[u][0], y[u][0], y[u][1] * y[u][1]) + fmaf(y[u][2], y[u][2], y[u][3] * y[u][3]);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) qp[u] += __shfl_xor_sync(0xffffffffu, qp[u], o);
-                        if (cg == 0)
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) qv[(pg * 8 + u) * 2 + h] = qp[u];
+                        qp[u] = s0;
                     }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) qp[u] += __shfl_xor_sync(0xffffffffu, qp[u], o);
+                    if (cg == 0)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) qv[(pg * 8 + u) * 2 + h] = qp[u];
                 }
                 __syncthreads();
             }
@@ -774,9 +802,6 @@ __global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float>
                     h = a.zbar[i];
                 }
                 hq[tid] = (unsigned char)h;
-                // the row shifted by the cluster's centre, then 1, then zeros
-                float* xr = xs + (size_t)tid * dp;
-                for (int j = 0; j < dp; ++j) xr[j] = j < d ? xr[j] - shf[j] : (j == d ? 1.f : 0.f);
             }
         }
         __syncthreads();
@@ -1221,7 +1246,7 @@ static cudaError_t substats_mult_t(dpmm_ctx* c, uint64_t seed, int draw, const i
 }
 
 static size_t wide_smem(const dpmm_ctx* c) {
-    return ((size_t)2 * 128 * 128 + 128 * WP + (size_t)WP * c->st.dp + 2 * WP + 256 + 128 + 4) * 4 +
+    return ((size_t)2 * 128 * 128 + 128 * WP + (size_t)WP * c->st.dp + 2 * WP + 256 + 256 + 128 + 4) * 4 +
            ((size_t)2 * WP + 2) * sizeof(int) + WP + 16;
 }
 
