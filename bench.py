@@ -39,6 +39,8 @@ TRAFFIC_BYTES = {
     # 262,144 points, K = 56: 138.378752 MB read + 4.014592 MB written, of which the 56 factor
     # images (69,632 B each, read once from DRAM, then from L2) are the cluster part
     ("labels_x3", "gauss_d128"): ((138.378752e6 + 4.014592e6 - 56 * 69632) / 262144, 69632.0),
+    # 1 M points: 400.153856 MB read + 6.711808 MB written (the log theta image is a few KB)
+    ("labels_tc_mult", "multinomial"): ((400.153856e6 + 6.711808e6) / 1e6, 0.0),
 }
 WORKLOADS = {
     "gauss_d32": dict(K_max=64),

@@ -385,7 +385,10 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     }
     const size_t esz = c->xdt == 0 ? 8 : (c->xdt == 1 ? 4 : 2);
     c->T_tiles = (int)((N + 255) / 256);
-    c->Gr = (int)std::min<int64_t>(c->G2, std::max<int64_t>(1, (N + 511) / 512));
+    // ranges of the statistics step: about one per 512 points, at most 2 x SMs (the CUDA-core
+    // kernels run two CTAs per SM) or 1 x SMs for the tensor-core kernel (one CTA per SM: one
+    // long range per CTA fills its pipeline once)
+    c->Gr = (int)std::min<int64_t>(substats_tc_supported(c) ? c->num_sms : c->G2, std::max<int64_t>(1, (N + 511) / 512));
     bool ok = true;
     auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
     A(&c->X, (size_t)N * c->xs * esz);
