@@ -192,6 +192,38 @@ def job_rate(local_ms, n_points, steps, world, dist=None):
     return world * n_points * steps / (ms / 1e3), ms
 
 
+def launch_floor(kernels, step_ms, reps=50):
+    """Replay time of a captured CUDA graph of `kernels` trivial kernels: the launch floor a
+    step of that many kernels cannot go below (what bounds the small, latency-bound
+    configurations)."""
+    import torch
+
+    if kernels < 1:
+        return None
+    t = torch.zeros(1, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            t.add_(1.0)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(kernels):
+            t.add_(1.0)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for _ in range(reps):
+            g.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"kernels_per_step": kernels, "empty_graph_replay_ms": ms, "frac_of_step": ms / step_ms}
+
+
 def batch_prec(d):
     """Precision of a batched problem: FP32 CUDA cores for d <= 8, TF32 tensor cores for
     d <= 32, split BF16 tensor cores above."""
@@ -416,6 +448,7 @@ def main():
         roof["kernel"] = lk[0]
         roof["kernel_ms_avg"] = ms / max(launches, 1)
     gpu_launches = prof.get("all_kernels", (0, 0))[0]
+    floor = launch_floor(gpu_launches // max(a.steps, 1), total_ms / a.steps)
 
     breakdown = None
     if a.breakdown:  # separate pass, events around every kernel (not the timed steps)
@@ -466,7 +499,7 @@ def main():
                           "prec": a.prec, "burnin_sweeps": a.burnin, "init": "generating labels" if a.init_truth else "K=1", "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-               "gpu_launches": gpu_launches, "step_ms": step_ms}
+               "gpu_launches": gpu_launches, "launch_floor": floor, "step_ms": step_ms}
         if breakdown is not None:
             out["breakdown"] = breakdown
         print(json.dumps(out))
