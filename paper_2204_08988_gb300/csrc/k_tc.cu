@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     uint64_t* tfull = empty + XST;    // 2
     uint64_t* tempty = tfull + 2;     // 2
     uint64_t* bload = tempty + 2;     // 1
-    uint64_t* sfull = bload + 1;      // 2: every part published its two best scores
-    uint64_t* qbar = sfull + 2;       // 4: the parts of a lane quarter published their draws
+    uint64_t* sfull = bload + 1;      // 2 x 4 (slot, lane quarter): the parts published their two best
+    uint64_t* qbar = sfull + 8;       // 4: the parts of a lane quarter published their draws
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float xm1[2][NPART][BM], xm2[2][NPART][BM];  // per part: best and second score
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             mbar_init(&tempty[b], NEPI * 32);
         }
         mbar_init(bload, 1);
-        for (int b = 0; b < 2; ++b) mbar_init(&sfull[b], NEPI * 32);
+        for (int b = 0; b < 8; ++b) mbar_init(&sfull[b], NPART * 32);  // a quarter's rows only
         for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART * 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             xm1[sl][part][r] = m1;
             xm2[sl][part][r] = m2;
             xk1[sl][part][r] = k1;
-            mbar_arrive(&sfull[sl]);
-            if (!mbar_wait(&sfull[sl], use, abort)) { ok = false; break; }
+            mbar_arrive(&sfull[sl * 4 + quarter]);
+            if (!mbar_wait(&sfull[sl * 4 + quarter], use, abort)) { ok = false; break; }
             // the row's best and second-best scores (every part computes the same)
             float g1 = xm1[sl][0][r], g2 = xm2[sl][0][r];
             int gk = xk1[sl][0][r];
