@@ -35,7 +35,7 @@ METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one
 # per cluster): the point part scales with N, the factor part with K.  Must be re-taken (or
 # removed) whenever that kernel changes.
 TRAFFIC_BYTES = {
-    ("labels_tc", "gauss_d32"): ((256.162816e6 + 8.674560e6) / 2e6, 0.0),
+    ("labels_tc", "gauss_d32"): ((256.261120e6 + 9.003008e6) / 2e6, 0.0),
     # 262,144 points, K = 56: 138.378752 MB read + 4.014592 MB written, of which the 56 factor
     # images (69,632 B each, read once from DRAM, then from L2) are the cluster part
     ("labels_x3", "gauss_d128"): ((138.378752e6 + 4.014592e6 - 56 * 69632) / 262144, 69632.0),
