@@ -80,7 +80,7 @@ __device__ inline void chol_update(T* A, int d, int ld, int j, const T* col) {
 // or not its lanes are busy, so warp 0 forms the pivot and the scaled column (one lane
 // per row) and the update touches only the lower triangle, one FMA per entry.
 __device__ inline void chol_ldl(double* A, int d, int ld, double* piv, double* rs, double* col, int* derr) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x;
     for (int j = 0; j < d; ++j) {
         if (tid < 32) {
             double v = A[j * ld + j];
@@ -112,7 +112,7 @@ __device__ inline double rsqrt_t(double x) { return rsqrt(x); }
 // once cancellation has taken more than 10 of the 24 bits of a pivot.
 template <typename T>
 __device__ inline void chol_ldl_t(T* A, int d, int ld, T* piv, T* rs, T* col, const T* dg, T rel, int* fail) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x;
     for (int j = 0; j < d; ++j) {
         if (tid < 32) {
             T v = A[j * ld + j];
