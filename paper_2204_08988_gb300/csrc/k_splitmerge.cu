@@ -284,7 +284,7 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
             merged_into[k] = -1;
             head[k] = 0;
         }
-        int nsplit = 0, nmerge = 0, nrej = 0;
+        int nsplit = 0, nrej = 0;
         if (a.sm_enabled) {
             int S = Kc;
             for (int k = 0; k < K; ++k) {

@@ -58,7 +58,7 @@ constexpr int SB_BUF = (HP / 32) * SB_ROWS * 128;
 constexpr int FR = 65, FS = 81;                // accumulator rows (D rows 0..64), row stride
 constexpr int GT = 4;                          // tiles per tensor-memory accumulation group
 constexpr int NS = 4, NB = 8;                  // score warps, operand warps
-constexpr int W_S = 2, W_B = 2 + NS;           // first score warp, first operand warp
+constexpr int W_B = 2 + NS;                    // first operand warp (the score warps are 2 .. 1 + NS)
 constexpr int W_T = W_B + NB;                  // statistics MMA warp
 constexpr int W_P = W_T + 1;                   // second producer warp
 constexpr int NTHREADS = 32 * (4 + NS + NB);
