@@ -1,7 +1,7 @@
 """Checkpoint and resume through the C ABI: a chain stopped at a sweep boundary and
 restored into a fresh context (same prior, data and options) continues bit for bit as
-the uninterrupted chain, in FP64, TF32 and BF16 (multinomial); bad checkpoints are
-refused."""
+the uninterrupted chain, in FP64, TF32, BF16X3 (d = 96) and BF16 (multinomial); bad
+checkpoints are refused."""
 import numpy as np
 import pytest
 
@@ -33,6 +33,9 @@ def _case(name):
     if name == "tf32":
         X, _ = synth.gaussian_mixture(20_001, 32, 5, 6.0, seed=22)
         return X, 0, P.PREC_TF32, dict(kappa0=1.0, m0=np.zeros(32), nu0=35.0, psi0=np.eye(32))
+    if name == "bf16x3":
+        X, _ = synth.gaussian_mixture(20_001, 96, 4, 6.0, seed=24)
+        return X, 0, P.PREC_BF16X3, dict(kappa0=1.0, m0=np.zeros(96), nu0=99.0, psi0=np.eye(96))
     X, _ = synth.multinomial_mixture(20_001, 64, 5, 60, seed=23)
     return X, 1, P.PREC_BF16, dict(beta=np.ones(64))
 
@@ -53,7 +56,7 @@ def _same(a, b):
     assert a[6] == b[6]
 
 
-@pytest.mark.parametrize("name", ["fp64", "tf32", "bf16"])
+@pytest.mark.parametrize("name", ["fp64", "tf32", "bf16x3", "bf16"])
 def test_resume_continues_the_chain_exactly(name):
     X, kind, pr, prior = _case(name)
     seed = 77

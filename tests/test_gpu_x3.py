@@ -66,10 +66,12 @@ def _fp64_scores(X, p, K):
     return out
 
 
-@pytest.mark.parametrize("N,d,K", [(3001, 128, 7), (1000, 64, 5), (2049, 100, 9), (777, 20, 3), (1, 128, 1)])
+@pytest.mark.parametrize("N,d,K", [(3001, 128, 7), (1000, 64, 5), (2049, 100, 9), (777, 20, 3), (1, 128, 1),
+                                   (4001, 128, 40)])
 def test_x3_scores_within_budget(N, d, K):
     """Every cluster score of every point (including the padded rows of the last tile
-    pair, the padded features d < 64 or 128, K = 1 and N = 1) against FP64."""
+    pair, the padded features d < 64 or 128, K = 1 and N = 1, and K = 40 clusters
+    streamed through the factor stages and TMEM buffers many times) against FP64."""
     if N < K:
         pytest.skip("needs a point per cluster")
     X, y, zb, o, g, p = _setup(max(N, 1), d, K, seed=N + d) if N > 1 else _setup_single(d)
