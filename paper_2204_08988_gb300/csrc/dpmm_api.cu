@@ -72,7 +72,11 @@ template <typename P>
 static cudaError_t dalloc(P** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    return cudaMalloc((void**)p, bytes);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    // every buffer starts zeroed: no kernel result may depend on what the allocator
+    // returned (the caller synchronises the device before the buffers are used)
+    if (e == cudaSuccess) e = cudaMemset((void*)*p, 0, bytes);
+    return e;
 }
 
 static void dfree(void* p) {
@@ -321,6 +325,11 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     cudaMemset(c->p_logw, 0, sizeof(double) * S);
     cudaMemset(c->dK, 0, sizeof(int));
     cudaMemset(c->center, 0, sizeof(double) * (2 * (size_t)d + (size_t)d * d));
+    // the memsets above run on the legacy stream; the context's stream may not wait for it
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        dpmm_destroy(c);
+        return DPMM_ECUDA;
+    }
     *out = c;
     return DPMM_OK;
 }
@@ -400,6 +409,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
         free_data(c);
         return fail(c, DPMM_ENOMEM, "device allocation for the data failed");
     }
+    CK(c, cudaDeviceSynchronize());  // the zeroing memsets ran on the legacy stream
     // centring (Gaussian, reduced precision): computed on the device from the input
     std::vector<double> cen((size_t)2 * d + (size_t)d * d, 0.0);
     CK(c, cudaMemcpyAsync(c->center, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice, c->stream));

@@ -456,7 +456,10 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
         cudaError_t e = cudaMalloc(&c->tc_img, bytes);
         if (e != cudaSuccess) return e;
         c->tc_img_bytes = bytes;
-        cudaMemset(c->tc_img, 0, bytes);
+        // on the context's stream: a memset on the legacy stream is not ordered with the
+        // image kernel below when the context's stream does not block on it
+        e = cudaMemsetAsync(c->tc_img, 0, bytes, c->stream);
+        if (e != cudaSuccess) return e;
     }
     tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->p_W, c->p_mu, q.cap_rows,
                                                     (float*)c->tc_img);
@@ -482,6 +485,7 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     if (!c->tc_flag) {
         cudaError_t e = cudaMalloc(&c->tc_flag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->tc_flag, 0, sizeof(int), c->stream);
         if (e != cudaSuccess) return e;
     }
     tc::Args a;

@@ -355,6 +355,7 @@ cudaError_t launch_labels_mult(dpmm_ctx* c, uint64_t seed) {
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     if (!c->tc_flag) {
         cudaError_t e = cudaMalloc(&c->tc_flag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->tc_flag, 0, sizeof(int), c->stream);
         if (e != cudaSuccess) return e;
     }
     tcm::Args a;
