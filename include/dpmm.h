@@ -14,9 +14,10 @@
  *
  * Conventions
  *  - The caller owns every buffer it passes; the library never keeps a caller
- *    pointer after a call returns.  Host buffers are plain CPU memory; where a
- *    call takes `on_device`, a non-zero value means the pointer is device memory
- *    of the context's device.
+ *    pointer after a call returns, except that dpmm_update_data reads page-locked
+ *    host input asynchronously, until the next synchronising call.  Host buffers
+ *    are CPU memory (pageable or page-locked); where a call takes `on_device`, a
+ *    non-zero value means the pointer is device memory of the context's device.
  *  - All work is ordered on the stream given to dpmm_set_options (default: the
  *    legacy default stream).  Calls that return data to the host synchronise that
  *    stream; dpmm_sweep does not.
