@@ -92,7 +92,7 @@ typedef enum {
 } dpmm_prec;
 
 /* Create a chain.  alpha > 0 is the DP concentration (Eq. DPLatentVar); d >= 1
- * the dimension (at most 256 for the NIW prior, 4092 for the Dirichlet prior);
+ * the dimension (at most 160 for the NIW prior, 4092 for the Dirichlet prior);
  * 1 <= K_max <= 1000 the capacity for clusters (a split that would exceed it is
  * rejected and counted, Sec. 4.1 "Propose and accept splits").
  * Errors: DPMM_EINVAL for invalid hyper-parameters or sizes (kappa0 <= 0,

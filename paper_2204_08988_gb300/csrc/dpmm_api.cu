@@ -237,7 +237,9 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     if (!prior || d < 1 || K_max < 1 || K_max > 1000 || !(alpha > 0.0)) return DPMM_EINVAL;
     double ld0 = 0.0;
     if (prior->kind == DPMM_PRIOR_NIW) {
-        if (!prior->m0 || !prior->psi0 || !(prior->kappa0 > 0.0) || !(prior->nu0 > d - 1.0) || d > 256)
+        // d <= 160: the factorisations of the parameter and split/merge steps hold a d x d
+        // FP64 matrix in one CTA's shared memory
+        if (!prior->m0 || !prior->psi0 || !(prior->kappa0 > 0.0) || !(prior->nu0 > d - 1.0) || d > 160)
             return DPMM_EINVAL;
         for (int i = 0; i < d; ++i)
             for (int j = 0; j < d; ++j)

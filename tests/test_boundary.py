@@ -36,7 +36,8 @@ def _create(**kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(alpha=0.0), dict(alpha=-1.0), dict(d=0), dict(K_max=0), dict(kappa0=0.0), dict(nu0=1.0),
+    dict(alpha=0.0), dict(alpha=-1.0), dict(d=0), dict(K_max=0), dict(K_max=1001), dict(kappa0=0.0), dict(nu0=1.0),
+    dict(d=161, nu0=170.0),
     dict(psi0=np.array([[1.0, 2.0], [2.0, 1.0]])), dict(psi0=np.array([[1.0, 0.5], [0.4, 1.0]])),
 ])
 def test_invalid_niw_hyperparameters_rejected(lib, bad):
