@@ -26,6 +26,7 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))  # synth.py: the seeded input generators
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3, "bf16x3": 4}
 DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32", "bf16x3": "bf16x3"}
@@ -64,6 +65,8 @@ def parse():
     ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain arm on the same state")
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--breakdown", action="store_true", help="add a per-kernel time table from a separate profiled pass")
     ap.add_argument("--init-truth", action="store_true",
                     help="start the chain from the generating labels instead of a burn-in from K=1 (profiling runs)")
@@ -113,7 +116,7 @@ class Clocks:
 
 
 def load_workload(name, n, seed_offset):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     base = {"gauss_d2": 1001, "gauss_d32": 1002, "multinomial": 1003, "gauss_d128": 1004}[name]
     X, y, prior, opt = synth.workload(name, N=n, seed=base + seed_offset)
@@ -152,7 +155,7 @@ def run_reference(a):
     if rank != 0:
         return
     if a.workload == "batched":  # a bounded sample of the first problem
-        from paper_2204_08988_gb300 import synth
+        import synth
 
         X, y, d = next(synth.batch_problems(a.problems))
         prior = dict(kind=0, kappa0=1.0, m0=np.zeros(d), nu0=float(d + 3), psi0=np.eye(d))
@@ -172,7 +175,8 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-sweeps/s", "n_gpus": a.gpus,
            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * N / v, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": a.workload, "N": N, "d": int(X.shape[1]), "sample": sample},
+           "config": {"workload": a.workload, "N": N, "d": int(X.shape[1]), "sample": sample,
+                      "ms_per_step": "extrapolated: N / value, the sample's rate applied to all N points"},
            "cpu_baseline": {"value": v, "unit": "point-sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "point-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -237,7 +241,8 @@ def main_batched(a):
     import torch
 
     import paper_2204_08988_gb300 as P
-    from paper_2204_08988_gb300 import _build, synth
+    import synth
+    from paper_2204_08988_gb300 import _build
 
     _build.build()
     K_max = WORKLOADS["batched"]["K_max"]
@@ -380,6 +385,9 @@ def main():
         a.burnin = 0
     g.sweep(a.burnin, seed)
     K0 = g.K
+    # the timed sweeps are what a user runs: the captured sweep graph, replayed, no
+    # events inside it; dpmm_profile(0) only resets the library's launch counter here
+    P.dpmm_profile(g.h, 0)
     g.sweep(a.warmup, seed)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -388,25 +396,39 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    P.dpmm_profile(g.h, 2)  # events around the label kernel only
-    Ks = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    barrier()
-    with Clocks(local) as clk:
-        for s in range(a.steps):
+    def timed_steps(chain, steps, clocks=None):
+        Ks_, ev_ = [], [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                        for _ in range(steps)]
+        for s in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()  # L2 flush, outside the timed events
-                ev[s][0].record(stream)
-            g.sweep(1, seed)
+                ev_[s][0].record(stream)
+            chain.sweep(1, seed)
             with torch.cuda.stream(stream):
-                ev[s][1].record(stream)
-            Ks.append(g.K)  # synchronises, outside the events
+                ev_[s][1].record(stream)
+            Ks_.append(chain.K)  # synchronises, outside the events
+        return [b.elapsed_time(e) for b, e in ev_], Ks_
+
+    P.dpmm_profile(g.h, 0)
+    barrier()
+    with Clocks(local) as clk:
+        step_ms, Ks = timed_steps(g, a.steps)
         barrier()
-    step_ms = [b.elapsed_time(e) for b, e in ev]
     total_ms = float(sum(step_ms))
+    gpu_launches = P.dpmm_get_profile(g.h).get("all_kernels", (0, 0))[0]
+    value, total_ms = job_rate(total_ms, N, a.steps, world, dist)
+
+    # the label kernel's mean launch time, from a separate pass of the same number of sweeps
+    # with CUDA events around that kernel only (those sweeps run eagerly, not replayed)
+    P.dpmm_profile(g.h, 2)
+    timed_steps(g, a.steps)
     prof = P.dpmm_get_profile(g.h)
     P.dpmm_profile(g.h, 0)
-    value, total_ms = job_rate(total_ms, N, a.steps, world, dist)
+    Kavg = float(np.mean(Ks))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
     # roofline of the dominant kernel: the label step
     lk = [k for k in prof if k.startswith("labels")]
@@ -414,14 +436,10 @@ def main():
     if lk:
         launches, ms = prof[lk[0]]
         avg_s = ms / max(launches, 1) / 1e3
-        Kavg = float(np.mean(Ks))
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         if kind == 0:
             flops = 2.0 * N * d * d * Kavg  # X (N x d) times the K stacked d x d factors
             if a.prec in ("tf32", "bf16", "bf16x3"):
-                bf16 = peaks.get("bf16_tflops", 1900.0)
-                peak = bf16 * (1.1 / 2.25) if a.prec == "tf32" else bf16
+                peak = bf16_peak * (1.1 / 2.25) if a.prec == "tf32" else bf16_peak
                 roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "peak_source": ("measured bf16 x nominal tf32/bf16 ratio 1.1/2.25" if a.prec == "tf32"
                                         else "measured bf16 burst")}
@@ -437,8 +455,7 @@ def main():
                         else "fp64: nominal 1.25 TFLOP/s"}
         else:
             bytes_ = N * d * (2 if a.prec == "bf16" else 4) + 4 * N
-            peak = peaks.get("hbm_gbs", 6800.0)
-            roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+            roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "peak_source": "measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         # DRAM bytes per launch from the ncu capture summarised in profiles/ (taken on a smaller
@@ -447,7 +464,24 @@ def main():
         roof["traffic"] = tb[0] * N + tb[1] * Kavg if tb else None
         roof["kernel"] = lk[0]
         roof["kernel_ms_avg"] = ms / max(launches, 1)
-    gpu_launches = prof.get("all_kernels", (0, 0))[0]
+        roof["kernel_timing"] = "CUDA events around the kernel on its stream, separate pass of %d sweeps" % a.steps
+        # the whole sweep against its own bound: algorithmic work per point per sweep (Gaussian:
+        # d^2 (2K + 5) flop -- cluster scores 2 d^2 K, sub-cluster scores 4 d^2, statistics d^2 --
+        # and d x 4 + 5 bytes; multinomial: d x 2 + 5 bytes) at the peak of the path's arithmetic
+        step_s = total_ms / a.steps / 1e3
+        if kind == 0:
+            sw_flops = N * d * d * (2.0 * Kavg + 5.0)
+            sw_bytes = N * (4.0 * d + 5.0)
+            t_bound = max(sw_flops / (roof["peak"] * 1e12) if roof["unit"] == "TFLOP/s" else 0.0,
+                          sw_bytes / (hbm_peak * 1e9))
+            roof["sweep"] = {"flop": sw_flops, "bytes": sw_bytes, "bound_ms": t_bound * 1e3,
+                             "achieved": sw_flops / step_s / 1e12, "unit": "TFLOP/s"}
+        else:
+            sw_bytes = N * (2.0 * d + 5.0)
+            t_bound = sw_bytes / (hbm_peak * 1e9)
+            roof["sweep"] = {"bytes": sw_bytes, "bound_ms": t_bound * 1e3, "achieved": sw_bytes / step_s / 1e9,
+                             "unit": "GB/s"}
+        roof["sweep_frac"] = t_bound / step_s
     floor = launch_floor(gpu_launches // max(a.steps, 1), total_ms / a.steps)
 
     breakdown = None
@@ -458,6 +492,28 @@ def main():
         bd = P.dpmm_get_profile(g.h)
         P.dpmm_profile(g.h, 0)
         breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in bd.items() if k != "all_kernels"}
+
+    # the FP64-plain GPU sweep on the same state: a second chain on the same data, in FP64
+    # on CUDA cores (the parity path), started from this chain's current labels, so both
+    # arms time sweeps at the same number of clusters
+    fp64 = None
+    est_s = 2.0 * N * d * d * Kavg / 1e12 if kind == 0 else 2.0 * N * d * Kavg / 1e12
+    if a.prec != "fp64" and not a.no_fp64 and world == 1 and est_s < 2.0:
+        z_now, zb_now = g.labels()
+        K_now = g.K
+        g64 = P.DPMM(kind, d, K_max, opt["alpha"], prec=PREC["fp64"], init_K=1, burn_out=15,
+                     stream=stream.cuda_stream, **kw)
+        with torch.cuda.stream(stream):
+            g64.set_data(Xd)
+        g64.set_state(K_now, z_now, zb_now)
+        g64.sweep(2, seed)  # warm-up (the second sweep captures the graph)
+        ms64, K64 = timed_steps(g64, a.fp64_steps)
+        v64 = N * len(ms64) / (sum(ms64) / 1e3)
+        fp64 = {"value": v64, "unit": "point-sweeps/s", "ms_per_step": float(np.mean(ms64)), "steps": len(ms64),
+                "K_start": K_now, "K_timed": K64, "speedup": value / v64,
+                "note": "FP64-plain GPU sweep from the timed chain's labels (same data, same K), graph replay, "
+                        "L2 flushed between steps"}
+        g64.close()
 
     # end to end through the C ABI: pinned host X in, labels out, every step
     e2e = None
@@ -499,7 +555,9 @@ def main():
                           "prec": a.prec, "burnin_sweeps": a.burnin, "init": "generating labels" if a.init_truth else "K=1", "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-               "gpu_launches": gpu_launches, "launch_floor": floor, "step_ms": step_ms}
+               "gpu_launches": gpu_launches, "launch_floor": floor, "fp64_plain": fp64, "step_ms": step_ms,
+               "timing": "CUDA events around each replayed sweep graph on the library's stream; no events "
+                         "inside the timed sweeps"}
         if breakdown is not None:
             out["breakdown"] = breakdown
         print(json.dumps(out))

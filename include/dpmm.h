@@ -220,19 +220,24 @@ dpmm_status dpmm_set_iter(dpmm_ctx* ctx, uint32_t iter);
 
 /* Kernel timing.  enable = 1 brackets every kernel launch of the sweep with CUDA
  * events on the context's stream; enable = 2 only the label-step kernel; 0 turns
- * it off.  Each call resets the records.  dpmm_get_profile returns, for up to
- * `cap` entries, the kernel name, its launches and summed device time (ms) since
- * the reset, then one entry "all_kernels" whose launch count is every kernel the
- * library launched since the reset; *count is the number of entries.  Synchronises. */
+ * it off.  While timing is on, sweeps are launched eagerly (no graph replay).  Each
+ * call resets the records.  dpmm_get_profile returns, for up to `cap` entries, the
+ * kernel name, its launches and summed device time (ms) since the reset, then one
+ * entry "all_kernels" whose launch count is every kernel the library launched since
+ * the reset (kernels of a replayed sweep graph included); *count is the number of
+ * entries.  Synchronises. */
 dpmm_status dpmm_profile(dpmm_ctx* ctx, int enable);
 dpmm_status dpmm_get_profile(dpmm_ctx* ctx, int cap, const char** names, int* launches, double* ms, int* count);
 
 /* ---- allocation-free statistics (no counterpart in the paper) ---- */
 
-/* Sufficient statistics of given labels without allocating any memory: for callers
- * that cannot call cudaMalloc where they need this (code running inside a stream
- * capture for a CUDA graph, or an application that partitions device memory up
- * front with its own allocator and forbids allocation afterwards).
+/* Sufficient statistics of given labels without allocating any memory.  The paper
+ * has no counterpart.  It serves callers that cannot allocate device memory where they
+ * need the statistics: applications that reserve the GPU's memory up front in their own
+ * pool and forbid any later cudaMalloc (a serving process that owns all of HBM, a host
+ * framework whose plug-ins must not allocate), and latency-critical code that must not
+ * take the implicit device-wide synchronisation a cudaMalloc or cudaFree can cause.
+ * The call makes no cudaMalloc, cudaFree or other allocating call.
  *
  * Inputs, all device memory of the current device: X (N x d row-major FP32), z[N]
  * in [0, K) and zbar[N] in {0, 1}.  Outputs, device memory of length 2K, 2K x d and
@@ -243,11 +248,15 @@ dpmm_status dpmm_get_profile(dpmm_ctx* ctx, int cap, const char** names, int* la
  *
  * Limits: 1 <= d <= 32, 1 <= K <= 16, N >= 1; anything else returns DPMM_EINVAL
  * before any work.  Scratch is a fixed 5.6 MiB array inside the library's device
- * image (held by every GPU that loads the library until the process exits); the
- * first call on each device looks up its address (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  All calls on a device share the
- * array: calls whose kernels overlap on the GPU (other streams, other threads) race
- * and give wrong results; serialise them.  Returns DPMM_ECUDA on a CUDA error. */
+ * image (held by every GPU that loads the library until the process exits).  The
+ * first call on each device (and in each CUDA context) looks up the array's address
+ * (cudaGetSymbolAddress) with that device current, so make that first call before any
+ * stream capture.  After cudaDeviceReset the next call looks the address up again
+ * only if the context handle changed; call it once outside any capture after a reset.
+ * All calls on a device share the array and every call overwrites it (it keeps the
+ * last call's contents; each call clears what it accumulates into): calls whose kernels
+ * overlap on the GPU (other streams, other threads) race and give wrong results;
+ * serialise them.  Returns DPMM_ECUDA when a launch fails. */
 dpmm_status dpmm_suffstats_noalloc(const float* X, int64_t N, int d, const int32_t* z, const uint8_t* zbar,
                                    int K, double* n_out, double* sx_out, double* sxx_out, void* stream);
 

@@ -81,6 +81,7 @@ def lib():
             L.orc_niw_draw.argtypes = [vp, u64, u32, u32, u32, d, vp, d, vp, vp, vp, vp]
             L.orc_dirichlet_draw.argtypes = [vp, u64, u32, u32, u32, vp, vp]
             L.orc_label_probe.argtypes = [vp, u64, u32, u32, vp, vp]
+            L.orc_label_probe_points.argtypes = [vp, u64, u32, u32, vp, i64, vp, vp]
             _lib = L
     return _lib
 
@@ -198,6 +199,15 @@ class Oracle:
         z = np.empty(self.N, np.int32)
         zb = np.empty(self.N, np.uint8)
         lib().orc_label_probe(self.h, seed, it, problem, _p(z), _p(zb))
+        return z, zb
+
+    def label_probe_points(self, seed, it, idx, problem=0):
+        """label_probe for the points idx only (global indices; same random streams)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        assert idx.size == 0 or (idx.min() >= 0 and idx.max() < self.N)
+        z = np.empty(idx.size, np.int32)
+        zb = np.empty(idx.size, np.uint8)
+        lib().orc_label_probe_points(self.h, seed, it, problem, _p(idx), idx.size, _p(z), _p(zb))
         return z, zb
 
     def counters(self):

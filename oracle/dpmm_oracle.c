@@ -510,29 +510,34 @@ static double orc_loglik(const orc_state* o, int s, const double* x)
 /* Gumbel-max draw: argmax_k (score_k + G_k), G_k = -log(-log u_k). */
 static double orc_gumbel(double u) { return -log(-log(u)); }
 
-/* Steps (e) and (f) of Sec. 4.1: cluster labels, then sub-cluster labels. */
-static void orc_draw_labels(orc_state* o, uint64_t seed, uint32_t problem)
+/* Steps (e) and (f) of Sec. 4.1 for point i: its cluster label, then its sub-cluster
+ * label, each a Gumbel-max draw over log pi + log f with uniforms keyed by the point. */
+static void orc_label_point(const orc_state* o, const orc_key* key, int64_t i, int32_t* zi, uint8_t* zbi)
 {
     int d = o->d, K = o->K;
-    orc_key key = {seed, o->iter, problem};
-    for (int64_t i = 0; i < o->N; ++i) {
-        const double* x = o->X + i * d;
-        double best = -INFINITY;
-        int zb = 0;
-        for (int k = 0; k < K; ++k) {
-            uint32_t w[4];
-            orc_block(&key, (uint32_t)i, ORC_Z, (uint32_t)(k / 2), w);
-            double u = (k % 2 == 0) ? orc_u01(w[0], w[1]) : orc_u01(w[2], w[3]);
-            double v = o->logw[3 * k] + orc_loglik(o, 3 * k, x) + orc_gumbel(u);
-            if (v > best) { best = v; zb = k; }
-        }
-        o->z[i] = zb;
+    const double* x = o->X + i * d;
+    double best = -INFINITY;
+    int zb = 0;
+    for (int k = 0; k < K; ++k) {
         uint32_t w[4];
-        orc_block(&key, (uint32_t)i, ORC_ZBAR, 0, w);
-        double vl = o->logw[3 * zb + 1] + orc_loglik(o, 3 * zb + 1, x) + orc_gumbel(orc_u01(w[0], w[1]));
-        double vr = o->logw[3 * zb + 2] + orc_loglik(o, 3 * zb + 2, x) + orc_gumbel(orc_u01(w[2], w[3]));
-        o->zbar[i] = (vr > vl) ? 1 : 0;
+        orc_block(key, (uint32_t)i, ORC_Z, (uint32_t)(k / 2), w);
+        double u = (k % 2 == 0) ? orc_u01(w[0], w[1]) : orc_u01(w[2], w[3]);
+        double v = o->logw[3 * k] + orc_loglik(o, 3 * k, x) + orc_gumbel(u);
+        if (v > best) { best = v; zb = k; }
     }
+    *zi = zb;
+    uint32_t w[4];
+    orc_block(key, (uint32_t)i, ORC_ZBAR, 0, w);
+    double vl = o->logw[3 * zb + 1] + orc_loglik(o, 3 * zb + 1, x) + orc_gumbel(orc_u01(w[0], w[1]));
+    double vr = o->logw[3 * zb + 2] + orc_loglik(o, 3 * zb + 2, x) + orc_gumbel(orc_u01(w[2], w[3]));
+    *zbi = (vr > vl) ? 1 : 0;
+}
+
+/* Steps (e) and (f) of Sec. 4.1 for every point. */
+static void orc_draw_labels(orc_state* o, uint64_t seed, uint32_t problem)
+{
+    orc_key key = {seed, o->iter, problem};
+    for (int64_t i = 0; i < o->N; ++i) orc_label_point(o, &key, i, &o->z[i], &o->zbar[i]);
 }
 
 static void orc_compact(orc_state* o, const int* dead);
@@ -753,4 +758,14 @@ void orc_label_probe(orc_state* o, uint64_t seed, uint32_t iter, uint32_t proble
     o->z = zk;
     o->zbar = zbk;
     o->iter = keep;
+}
+
+/* The same labels as orc_label_probe, for the listed points only (idx[0..n), global
+ * point indices, so the random streams are those of the whole data set).  Used where
+ * the data set is too large for the whole label step to run in seconds. */
+void orc_label_probe_points(const orc_state* o, uint64_t seed, uint32_t iter, uint32_t problem, const int64_t* idx,
+                            int64_t n, int32_t* z, uint8_t* zbar)
+{
+    orc_key key = {seed, iter, problem};
+    for (int64_t q = 0; q < n; ++q) orc_label_point(o, &key, idx[q], &z[q], &zbar[q]);
 }

@@ -268,11 +268,36 @@ def dpmm_get_profile(h):
 
 
 def dpmm_suffstats_noalloc(X, z, zbar, K, n_out, sx_out, sxx_out, stream=None):
-    """Statistics of given labels with no allocation (CUDA tensors in and out)."""
+    """Statistics of given labels with no allocation (CUDA tensors in and out).
+
+    X is N x d float32, z int32[N], zbar uint8[N]; the outputs are float64 with at
+    least 2K, 2K*d and 2K*d*d elements.  All must be contiguous and on the current
+    device.  The call is ordered on `stream` (a cudaStream_t handle), by default on
+    torch's current stream."""
+    import torch
+
+    if X.dim() != 2:
+        raise ValueError("X must be N x d")
     N, d = X.shape
+    dev = torch.cuda.current_device()
+    want = [(X, torch.float32, "X", None), (z, torch.int32, "z", N), (zbar, torch.uint8, "zbar", N),
+            (n_out, torch.float64, "n_out", 2 * K), (sx_out, torch.float64, "sx_out", 2 * K * d),
+            (sxx_out, torch.float64, "sxx_out", 2 * K * d * d)]
+    for t, dt, name, numel in want:
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError("%s must be a CUDA tensor on the current device" % name)
+        if t.dtype != dt:
+            raise ValueError("%s must be %s, not %s" % (name, dt, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if numel is not None and t.numel() < numel:
+            raise ValueError("%s needs at least %d elements" % (name, numel))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
     st = load().dpmm_suffstats_noalloc(C.c_void_p(X.data_ptr()), int(N), int(d), C.c_void_p(z.data_ptr()),
                                        C.c_void_p(zbar.data_ptr()), int(K), C.c_void_p(n_out.data_ptr()),
-                                       C.c_void_p(sx_out.data_ptr()), C.c_void_p(sxx_out.data_ptr()), stream)
+                                       C.c_void_p(sx_out.data_ptr()), C.c_void_p(sxx_out.data_ptr()),
+                                       C.c_void_p(stream))
     _check(None, st)
 
 

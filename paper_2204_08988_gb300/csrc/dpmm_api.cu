@@ -208,8 +208,10 @@ static dpmm_status check_derr(dpmm_ctx* c) {
     CK(c, cudaMemcpyAsync(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (h != 0) {
-        int z = 0;
-        cudaMemcpy(c->derr, &z, sizeof(int), cudaMemcpyHostToDevice);
+        // cleared on the context's stream, so that the clear is ordered before any later
+        // kernel of this chain (which may set the word again)
+        cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
+        cudaStreamSynchronize(c->stream);
         return fail(c, (dpmm_status)h, h == DPMM_ENUMERIC ? "non-positive-definite scale matrix or NaN seen on the device"
                                                          : "device error");
     }
@@ -499,6 +501,7 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
     for (int it = 0; it < iters; ++it) {
         if (graphs && c->graph && c->graph_seed == seed && c->graph_mask == c->step_mask) {
             CK(c, cudaGraphLaunch(c->graph, c->stream));
+            c->nlaunch += c->graph_kernels;
             continue;
         }
         CK(c, enqueue_sweep(c, seed));
@@ -506,7 +509,10 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
             drop_graph(c);
             cudaGraph_t g = nullptr;
             CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = c->nlaunch;
             cudaError_t e = enqueue_sweep(c, seed);
+            c->graph_kernels = c->nlaunch - before;
+            c->nlaunch = before;  // captured, not launched
             cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
             if (e == cudaSuccess && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&c->graph, g, 0);
             if (g) cudaGraphDestroy(g);
@@ -616,8 +622,11 @@ dpmm_status dpmm_load_checkpoint(dpmm_ctx* c, const void* buf, size_t bytes) {
     const unsigned char* q = (const unsigned char*)buf + sizeof(h);
     const int K = h.K;
     auto up8 = [](size_t b) { return (b + 7) / 8 * 8; };
+    // every copy is ordered on the context's stream (a legacy-stream copy is not ordered
+    // with a non-blocking stream); the stream is synchronised before returning because the
+    // caller's buffer only has to stay valid for the duration of this call
     auto H2D = [&](void* dst, size_t n, size_t padded) {
-        if (n) CK(c, cudaMemcpy(dst, q, n, cudaMemcpyHostToDevice));
+        if (n) CK(c, cudaMemcpyAsync(dst, q, n, cudaMemcpyHostToDevice, c->stream));
         q += padded;
         return DPMM_OK;
     };
@@ -626,15 +635,19 @@ dpmm_status dpmm_load_checkpoint(dpmm_ctx* c, const void* buf, size_t bytes) {
     for (int64_t i = 0; i < c->N; ++i)
         if (zh[i] < 0 || zh[i] >= K) return fail(c, DPMM_EINVAL, "checkpoint label out of range");
     const uint32_t it[2] = {h.iter, h.problem};
-    CK(c, cudaMemcpy(c->dK, &h.K, sizeof(int), cudaMemcpyHostToDevice));
-    CK(c, cudaMemcpy(c->diter, it, sizeof(it), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpyAsync(c->dK, &h.K, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->diter, it, sizeof(it), cudaMemcpyHostToDevice, c->stream));
     void* dst[7] = {c->z, c->zbar, c->age, c->counters, c->stats, c->shift_stats, c->cweights};
     const size_t len[7] = {(size_t)c->N * 4, (size_t)c->N, (size_t)K * 4, 8 * 4, (size_t)2 * K * c->st.E * 8,
                            (size_t)K * c->d * 8, (size_t)K * 8};
     for (int a = 0; a < 7; ++a) {
         const dpmm_status st = H2D(dst[a], len[a], up8(len[a]));
-        if (st != DPMM_OK) return st;
+        if (st != DPMM_OK) {
+            cudaStreamSynchronize(c->stream);
+            return st;
+        }
     }
+    CK(c, cudaStreamSynchronize(c->stream));
     c->initialized = true;
     c->h_iter = h.iter;
     return DPMM_OK;
@@ -854,7 +867,9 @@ dpmm_status dpmm_label_scores(dpmm_ctx* c, double* scores) {
 
 dpmm_status dpmm_profile(dpmm_ctx* c, int enable) {
     if (!c) return DPMM_EINVAL;
-    drop_graph(c);
+    // profiled sweeps run eagerly (events between the launches); a captured graph is kept
+    // when the mode does not change, so that resetting the counters leaves replay as it was
+    if (enable != c->profiling) drop_graph(c);
     CK(c, cudaStreamSynchronize(c->stream));
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);

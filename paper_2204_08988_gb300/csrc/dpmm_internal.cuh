@@ -246,6 +246,7 @@ struct dpmm_ctx {
     uint64_t graph_seed = 0;
     unsigned graph_mask = 0;
     bool use_graph = true;
+    int64_t graph_kernels = 0;  // kernel nodes of the captured sweep
 
     // profiling: 0 off, 1 every kernel, 2 only the label kernel
     int profiling = 0;

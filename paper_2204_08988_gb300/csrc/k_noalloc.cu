@@ -1,13 +1,17 @@
 // k_noalloc.cu -- sufficient statistics of given labels without any allocation.
 //
-// For callers that cannot call cudaMalloc at the point where they need the
-// statistics (for example code running inside a stream that is being captured into a
-// CUDA graph, or an application whose memory is partitioned up front by its own
-// allocator), this entry point computes, for every sub-cluster (k, h), the count,
-// the sum of x and the sum of x x^T of the points labelled (z = k, zbar = h), using
-// only the caller's buffers and a fixed scratch array that lives in this library's
-// device image.  The scratch (NA_G x 2 NA_KMAX x NA_EMAX doubles = 5.6 MiB) is held
-// by every GPU that loads the library until the process exits.
+// Some callers cannot allocate device memory at the point where they need the
+// statistics: an application that reserves the GPU's memory up front in its own pool
+// and forbids any later cudaMalloc (a serving process that owns all of HBM, a host
+// framework whose plug-ins must not allocate), or latency-critical code that must not
+// take the implicit device-wide synchronisation a cudaMalloc/cudaFree can cause.  This
+// entry point computes, for every sub-cluster (k, h), the count, the sum of x and the
+// sum of x x^T of the points labelled (z = k, zbar = h), using only the caller's
+// buffers and a fixed scratch array that lives in this library's device image.  The
+// scratch (NA_G x 2 NA_KMAX x NA_EMAX doubles = 5.6 MiB) is held by every GPU that
+// loads the library until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "dpmm_internal.cuh"
@@ -124,8 +128,32 @@ __global__ void na_combine_kernel(StatLayout L, int G, int K, const double* scra
     if (threadIdx.x == 0) n_out[s] = M(d, d);
 }
 
+// The scratch address is looked up (cudaGetSymbolAddress) once per device and per
+// context: the array sits at a different address in every context the module is loaded
+// into, so the cache is keyed by the context current at the call (cuCtxGetCurrent,
+// resolved through the runtime's driver entry point), not by the device ordinal alone.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
 static std::mutex g_na_mu;
-static void* g_na_ptr[128];
+static struct {
+    CUcontext ctx;
+    void* ptr;
+} g_na_cache[128];
+
+static CUcontext na_current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+    }
+    CUcontext cx = nullptr;
+    if (fn && fn(&cx) != CUDA_SUCCESS) cx = nullptr;
+    return cx;
+}
 
 }  // namespace dpmm
 
@@ -138,20 +166,32 @@ extern "C" dpmm_status dpmm_suffstats_noalloc(const float* X, int64_t N, int d, 
     if (N < 1 || d < 1 || d > NA_DMAX || K < 1 || K > NA_KMAX) return DPMM_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return DPMM_ECUDA;
-    void* scratch = nullptr;
+    double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {  // set-up once per device, with that device current
+        const CUcontext cx = na_current_context();
+        if (!g_na_cache[dev].ptr || !cx || g_na_cache[dev].ctx != cx) {  // set-up, with that device current
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return DPMM_ECUDA;
-            g_na_ptr[dev] = p;
+            // the lookup has made the runtime's context current if none was
+            g_na_cache[dev].ctx = na_current_context();
+            g_na_cache[dev].ptr = p;
         }
-        scratch = g_na_ptr[dev];
+        scratch = (double*)g_na_cache[dev].ptr;
     }
     StatLayout L;
     L.init(d, STAT_FULL);
     cudaStream_t s = (cudaStream_t)stream;
-    na_partial_kernel<<<NA_G, 256, 0, s>>>(X, N, d, z, zbar, K, L, NA_G, (double*)scratch);
-    na_combine_kernel<<<2 * K, 128, 0, s>>>(L, NA_G, K, (const double*)scratch, n_out, sx_out, sxx_out);
-    return cudaGetLastError() == cudaSuccess ? DPMM_OK : DPMM_ECUDA;
+    int G = NA_G;
+    // launched with cudaLaunchKernel, whose return value is this launch's own error (an
+    // error left behind by an unrelated earlier launch is neither reported nor cleared)
+    void* a1[] = {(void*)&X, (void*)&N, (void*)&d, (void*)&z, (void*)&zbar, (void*)&K, (void*)&L, (void*)&G,
+                  (void*)&scratch};
+    if (cudaLaunchKernel((const void*)na_partial_kernel, dim3(NA_G), dim3(256), a1, 0, s) != cudaSuccess)
+        return DPMM_ECUDA;
+    const double* cs = scratch;
+    void* a2[] = {(void*)&L, (void*)&G, (void*)&K, (void*)&cs, (void*)&n_out, (void*)&sx_out, (void*)&sxx_out};
+    if (cudaLaunchKernel((const void*)na_combine_kernel, dim3(2 * K), dim3(128), a2, 0, s) != cudaSuccess)
+        return DPMM_ECUDA;
+    return DPMM_OK;
 }

@@ -34,7 +34,7 @@ def _prior(d):
 
 
 def _problems():
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     out = []
     for j, (N, d, K) in enumerate([(1500, 2, 4), (2049, 5, 3), (777, 3, 5), (3001, 4, 4)]):
@@ -110,7 +110,7 @@ def test_batch_equals_alone_reduced_precision(prec, d):
     state across contexts)."""
     import torch
 
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     pr = {"tf32": P.PREC_TF32, "bf16x3": P.PREC_BF16X3, "fp32": P.PREC_FP32}[prec]
     data = [synth.gaussian_mixture(N, d, 4, 6.0, seed=N)[0] for N in (20_001, 9_000, 33_333)]

@@ -25,7 +25,7 @@ def gpu():
 
 
 def _case(name):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     if name == "fp64":
         X, _ = synth.gaussian_mixture(4001, 3, 4, 6.0, seed=21, dtype=np.float64)

@@ -32,7 +32,7 @@ def _prior(d):
 
 
 def _data(d, N=5000, seed=3):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     return synth.gaussian_mixture(N, d, 3, 6.0, seed=seed)[0]
 

@@ -78,7 +78,7 @@ def _check_stats(o, g, rtol=1e-10):
 @pytest.mark.parametrize("N,d,K", [(1000, 2, 3), (2049, 5, 4), (777, 1, 2)])
 def test_label_step_fp64_matches_oracle(N, d, K):
     """Steps (e), (f) with the oracle's parameters injected: labels bit-exact."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, y = synth.gaussian_mixture(N, d, K, 4.0, seed=100 + N, dtype=np.float64)
     prior = _niw_prior(d)
@@ -109,7 +109,7 @@ def test_label_step_fp64_matches_oracle(N, d, K):
 
 def test_param_draws_fp64_match_oracle():
     """Steps (a)-(d): weights, sub-weights, NIW draws from identical statistics."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, d, K = 3000, 4, 3
     X, y = synth.gaussian_mixture(N, d, K, 5.0, seed=5, dtype=np.float64)
@@ -137,7 +137,7 @@ def test_param_draws_reduced_precision(prec, d):
     from the GPU's own statistics and the same Philox stream: the well-conditioned
     clusters to FP32 accuracy, the ill-conditioned one (two coordinates equal up to
     1e-3 noise) to FP64 accuracy, which only the FP64 retry reaches."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, K, it, seed = 4000, 4, 3, 99
     X, y = synth.gaussian_mixture(N, d, K, 5.0, seed=21)
@@ -172,7 +172,7 @@ def test_param_draws_reduced_precision(prec, d):
 @pytest.mark.parametrize("kind", [0, 1])
 def test_full_sweeps_fp64_match_oracle(kind):
     """Whole sweeps (params, labels, statistics, splits, merges) from K=1."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     if kind == 0:
         d = 3
@@ -199,7 +199,7 @@ def test_full_sweeps_fp64_match_oracle(kind):
 
 
 def test_k_max_saturation_counts_rejections():
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     d = 2
     X, _ = synth.gaussian_mixture(3000, d, 6, 10.0, seed=3, dtype=np.float64)
@@ -216,7 +216,7 @@ def test_k_max_saturation_counts_rejections():
 
 @pytest.mark.parametrize("N", [1, 2, 255, 256, 257])
 def test_tiny_and_ragged_sizes(N):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     d = 2
     X, _ = synth.gaussian_mixture(N, d, 2, 3.0, seed=N, dtype=np.float64)
@@ -233,7 +233,7 @@ def test_tiny_and_ragged_sizes(N):
 def test_invariants_large_fp32(init_K):
     """FP32 path at 200k points: invariants and statistics against a numpy recount
     of the GPU's own labels."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, d = 200_003, 8
     X, _ = synth.gaussian_mixture(N, d, 6, 6.0, seed=9)
@@ -262,7 +262,7 @@ def test_invariants_large_fp32(init_K):
 def test_fp32_labels_agree_with_fp64():
     """Reduced precision (FP32 CUDA cores) against the FP64 path on the same state,
     parameters and keys: label disagreement within budget."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, d, K = 50_000, 8, 5
     X, y = synth.gaussian_mixture(N, d, K, 5.0, seed=44)
@@ -291,7 +291,7 @@ def test_graph_replay_matches_eager(prec):
     """Sweeps on an explicit stream are replayed from a captured CUDA graph; the chain
     must be identical to the eager one (legacy default stream)."""
     import torch
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     d = 8 if prec == "fp64" else 32
     X, _ = synth.gaussian_mixture(20_001, d, 5, 6.0, seed=12)
@@ -316,7 +316,7 @@ def test_high_dimension_d128():
     pass, statistics blocks beyond the staged layouts): FP64 sweeps bit-exact against the
     oracle; the FP32 path (the TF32 setting is refused above d = 32) keeps the statistics
     consistent with its labels."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     d = 128
     X, _ = synth.gaussian_mixture(1501, d, 3, 4.0, seed=128, dtype=np.float64)

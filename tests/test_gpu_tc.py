@@ -36,7 +36,7 @@ def _prior(d):
 
 
 def _setup(N, d, K, seed, K_max=64, mean_scale=5.0):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, y = synth.gaussian_mixture(N, d, K, mean_scale, seed=seed)
     o = O.Oracle(O.NIW, d, K_max, 3.0, **_prior(d))
@@ -94,7 +94,7 @@ def test_tc_labels_agree_with_fp64(K):
 
 
 def test_tc_chain_finds_clusters():
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, d = 60_001, 32
     X, y = synth.gaussian_mixture(N, d, 6, 5.0, seed=99)
@@ -128,7 +128,7 @@ def test_tc_statistics_match_recount(N, d, K):
     splits and merges), counts are exact and first and second moments agree with an
     FP64 recount of the GPU's own labels to FP32 accuracy.  Small N spreads each
     cluster over many ranges and tiles with ragged ends."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, _ = synth.gaussian_mixture(N, d, K, 6.0, seed=N + 1)
     g = P.DPMM(0, d, 32, 10.0, prec=P.PREC_TF32, burn_out=2, **_prior(d))
@@ -156,7 +156,7 @@ def test_tc_statistics_match_recount(N, d, K):
 # ---------------------------------------------------------------- multinomial (BF16)
 
 def _mult_setup(N, d, K, seed, K_max=64, draws=100):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, y = synth.multinomial_mixture(N, d, K, draws, seed=seed)
     o = O.Oracle(O.DIRICHLET, d, K_max, 3.0, beta=np.ones(d))
@@ -203,7 +203,7 @@ def test_mult_labels_agree_with_fp64():
 def test_mult_chain_finds_topics():
     from collections import Counter
 
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, d, K = 40_000, 200, 8
     X, y = synth.multinomial_mixture(N, d, K, 100, seed=17)

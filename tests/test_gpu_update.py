@@ -33,7 +33,7 @@ def _prior(d):
 def test_update_data_sources_agree(prec, d):
     import torch
 
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     pr = {"fp32": P.PREC_FP32, "tf32": P.PREC_TF32, "fp64": P.PREC_FP64_PLAIN}[prec]
     dt = np.float64 if prec == "fp64" else np.float32

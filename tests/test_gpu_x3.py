@@ -40,7 +40,7 @@ def _prior(d):
 
 
 def _setup(N, d, K, seed, K_max=64):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, y = synth.gaussian_mixture(N, d, K, 5.0, seed=seed)
     o = O.Oracle(O.NIW, d, K_max, 3.0, **_prior(d))
@@ -87,7 +87,7 @@ def test_x3_scores_within_budget(N, d, K):
 
 def _setup_single(d):
     """One point, one cluster whose parameters come from the points of a larger draw."""
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, _ = synth.gaussian_mixture(4 * d, d, 1, 5.0, seed=d)
     o = O.Oracle(O.NIW, d, 4, 3.0, **_prior(d))
@@ -127,7 +127,7 @@ def test_x3_chain_finds_clusters_and_keeps_statistics(d, N, K):
     the statistics agree with an FP64 recount of the GPU's own labels (FP32 path)."""
     from collections import Counter
 
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     X, y = synth.gaussian_mixture(N, d, K, 8.0, seed=d + N)
     g = P.DPMM(0, d, 32, 10.0, prec=P.PREC_BF16X3, burn_out=3, **_prior(d))

@@ -6,6 +6,7 @@ probabilities computed with independent samplers, and invariants.
 A plausible slip in the oracle -- a dropped term in a marginal likelihood, a wrong
 Bartlett degree of freedom, a transposed precision factor, a wrong Gumbel sign, an
 off-by-one in the Hastings ratios -- fails at least one of these."""
+import itertools
 import math
 import os
 
@@ -365,11 +366,257 @@ def test_merge_acceptance_rate_matches_hastings_ratio(oracle_mod):
     assert abs(acc / R - H) < 5 * math.sqrt(H * (1 - H) / R), (acc / R, H)
 
 
+# ------------------------------------------------- multinomial / Dirichlet branch
+
+def _multinomial_logpmf(x, logtheta):
+    """log Multinomial(x; sum x, theta) by scipy (includes the multinomial coefficient,
+    which is the same for every cluster and cancels in every normalised probability)."""
+    th = np.exp(np.asarray(logtheta, float))
+    th = th / th.sum()
+    return stats.multinomial(int(np.sum(x)), th).logpmf(np.asarray(x, int))
+
+
+def test_label_step_is_exact_categorical_draw_dirichlet(oracle_mod):
+    """Steps (e), (f) with the Dirichlet prior: Gumbel-max frequencies against the
+    normalised pi_k Mult(x_i; theta_k) computed with scipy's multinomial pmf from the
+    drawn parameters, per point, and the sub-label frequencies given each cluster label
+    against pibar_kh Mult(x_i; theta_kh).  A slip in the multinomial score (theta in
+    place of log theta, a wrong slot, a dropped weight) fails one of the chi-squares."""
+    X = np.array([[2.0, 0.0, 1.0], [0.0, 2.0, 1.0], [1.0, 1.0, 1.0], [0.0, 0.0, 3.0]])
+    N, d, K = X.shape[0], 3, 3
+    o = O.Oracle(O.DIRICHLET, d, 8, 2.0, beta=np.array([1.0, 0.7, 1.3]))
+    o.set_data(X)
+    o.set_state(K, np.array([0, 1, 2, 0], np.int32), np.array([0, 1, 0, 1], np.uint8))
+    o.draw_params(23)
+    p = o.params()
+    R = 20000
+    Z = np.empty((R, N), np.int32)
+    ZB = np.empty((R, N), np.uint8)
+    for t in range(R):
+        Z[t], ZB[t] = o.label_probe(23, t)
+    informative = 0
+    for i in range(N):
+        lp = np.array([p["logw"][3 * k] + _multinomial_logpmf(X[i], p["logtheta"][3 * k]) for k in range(K)])
+        pr = np.exp(lp - lp.max())
+        pr /= pr.sum()
+        informative += (pr > 0.05).sum() >= 2
+        cnt = np.bincount(Z[:, i], minlength=K)
+        assert stats.chisquare(cnt, pr * R).pvalue > 1e-4, (i, cnt, pr * R)
+        for k in range(K):
+            sel = Z[:, i] == k
+            if sel.sum() < 200:
+                continue
+            lq = np.array([p["logw"][3 * k + 1 + h] + _multinomial_logpmf(X[i], p["logtheta"][3 * k + 1 + h])
+                           for h in range(2)])
+            q = np.exp(lq - lq.max())
+            q /= q.sum()
+            c = np.bincount(ZB[sel, i], minlength=2)
+            assert stats.chisquare(c, q * sel.sum()).pvalue > 1e-4, (i, k, c, q * sel.sum())
+    assert informative >= 2  # the draws are not all near-certain
+
+
+def _beta_binomial_log_marginal(C, b1, b2):
+    """f_x(C) of two-category count vectors without the multinomial coefficients: the
+    Beta integral of prod_i theta^{a_i} (1 - theta)^{b_i} against Beta(b1, b2)."""
+    from scipy.special import betaln
+
+    C = np.asarray(C, float).reshape(-1, 2)
+    return betaln(b1 + C[:, 0].sum(), b2 + C[:, 1].sum()) - betaln(b1, b2)
+
+
+# Twelve two-category count vectors in three clusters of four, with sub-labels; chosen
+# so that every split and merge of the three clusters is accepted with a probability
+# near one half (each Hastings ratio is asserted to lie in (0.2, 0.8)).
+_PLUMB_X = np.array([[2, 1], [0, 3], [1, 2], [0, 3], [0, 3], [0, 3], [1, 2], [2, 1], [0, 3], [1, 2], [2, 1], [0, 3]],
+                    float)
+_PLUMB_Z = np.repeat(np.arange(3), 4).astype(np.int32)
+_PLUMB_ZB = np.array([1, 0, 1, 0, 0, 0, 1, 1, 1, 0, 1, 1], np.uint8)
+_PLUMB_ALPHA, _PLUMB_B = 3.2, (2.16, 0.83)
+
+
+def _plumb_ratios(X, z, zb, alpha, b1, b2, K):
+    lg = math.lgamma
+    Lf = lambda sel: _beta_binomial_log_marginal(X[sel], b1, b2)
+    ps = []
+    for k in range(K):  # Eq. sample_splits
+        s = z == k
+        l, r = s & (zb == 0), s & (zb == 1)
+        nl, nr, n = l.sum(), r.sum(), s.sum()
+        lH = math.log(alpha) + lg(nl) + Lf(l) + lg(nr) + Lf(r) - lg(n) - Lf(s)
+        ps.append(min(1.0, math.exp(lH)))
+    pm = {}
+    for k1 in range(K):  # Eq. sample_merges
+        for k2 in range(k1 + 1, K):
+            s1, s2 = z == k1, z == k2
+            n1, n2 = s1.sum(), s2.sum()
+            lH = (lg(n1 + n2) - math.log(alpha) - lg(n1) - lg(n2) + Lf(s1 | s2) - Lf(s1) - Lf(s2) + lg(alpha)
+                  - lg(alpha + n1 + n2) + lg(alpha / 2 + n1) + lg(alpha / 2 + n2) - 2 * lg(alpha / 2))
+            pm[(k1, k2)] = min(1.0, math.exp(lH))
+    return ps, pm
+
+
+def test_split_acceptance_rate_matches_hastings_ratio_dirichlet(oracle_mod):
+    """Eq. sample_splits with the Dirichlet prior: P(accept) = min(1, H_split), H from
+    Beta-binomial marginals (scipy betaln, independent of the oracle's lgamma sums)."""
+    X, zb = _PLUMB_X[:4], _PLUMB_ZB[:4]
+    b1, b2 = _PLUMB_B
+    ps, _ = _plumb_ratios(X, np.zeros(4, np.int32), zb, _PLUMB_ALPHA, b1, b2, 1)
+    H = ps[0]
+    assert 0.2 < H < 0.8, H
+    o = O.Oracle(O.DIRICHLET, 2, 8, _PLUMB_ALPHA, beta=[b1, b2], burn_out=0)
+    o.set_data(X)
+    R = 6000
+    acc = 0
+    for r in range(R):
+        o.set_state(1, np.zeros(4, np.int32), zb)
+        o.sweep(1, 7000 + r, mask=O.MASK_SPLITMERGE)
+        acc += o.K == 2
+    assert abs(acc / R - H) < 5 * math.sqrt(H * (1 - H) / R), (acc / R, H)
+
+
+def test_merge_acceptance_rate_matches_hastings_ratio_dirichlet(oracle_mod):
+    """Eq. sample_merges with the Dirichlet prior (Beta-binomial marginals)."""
+    X, z = _PLUMB_X[:8], _PLUMB_Z[:8]
+    b1, b2 = _PLUMB_B
+    _, pm = _plumb_ratios(X, z, _PLUMB_ZB[:8], _PLUMB_ALPHA, b1, b2, 2)
+    H = pm[(0, 1)]
+    assert 0.2 < H < 0.8, H
+    o = O.Oracle(O.DIRICHLET, 2, 8, _PLUMB_ALPHA, beta=[b1, b2], burn_out=10 ** 6)
+    o.set_data(X)
+    R = 6000
+    acc = 0
+    for r in range(R):
+        o.set_state(2, z, np.zeros(8, np.uint8))
+        o.sweep(1, 11000 + r, mask=O.MASK_SPLITMERGE)
+        if o.K == 1:
+            acc += 1
+            _, zbo = o.labels()
+            assert list(zbo) == [0] * 4 + [1] * 4  # the old clusters become sub-clusters l, r
+    assert abs(acc / R - H) < 5 * math.sqrt(H * (1 - H) / R), (acc / R, H)
+
+
+def _plumb_outcomes(ps, pm, K, K_max, z, zb):
+    """Exact distribution of one split/merge step from a fixed state, enumerated from the
+    rules as the sampler states them: splits in increasing k, each accepted with
+    probability ps[k] on its own uniform, but one that would exceed K_max is rejected
+    and counted (that cluster stays untouched); the right half of an accepted split gets
+    the next id; merges over pairs k1 < k2 in lexicographic order among clusters no split
+    touched, each cluster in at most one merge, k1 keeps its id and its partner's points
+    join it as sub-cluster r (k1's own points become l); absorbed ids are removed and the
+    survivors renumbered in order.  Ages: 0 for clusters created or changed this sweep,
+    else the old age + 1.  Returns {(K', z', ages', zbar' outside split clusters,
+    (splits, merges, rejected)): probability}."""
+    out = {}
+    for sp in itertools.product([0, 1], repeat=K):
+        p_sp = np.prod([ps[k] if sp[k] else 1 - ps[k] for k in range(K)])
+        S, split_to, touched, rejected = K, [-1] * K, set(), 0
+        for k in range(K):
+            if sp[k]:
+                if S >= K_max:
+                    rejected += 1
+                    continue
+                split_to[k] = S
+                touched |= {k}
+                S += 1
+        # merges: enumerate the accept/reject results of the pairs actually proposed
+        def walk(k1, merged_into, head, prob):
+            if k1 >= K:
+                yield merged_into, head, prob
+                return
+            if k1 in touched or k1 in merged_into or k1 in head:
+                yield from walk(k1 + 1, merged_into, head, prob)
+                return
+            cands = [k2 for k2 in range(k1 + 1, K) if k2 not in touched and k2 not in merged_into and k2 not in head]
+            rej = 1.0
+            for k2 in cands:
+                yield from walk(k1 + 1, {**merged_into, k2: k1}, head | {k1}, prob * rej * pm[(k1, k2)])
+                rej *= 1 - pm[(k1, k2)]
+            yield from walk(k1 + 1, merged_into, head, prob * rej)
+
+        for merged_into, head, prob in walk(0, {}, frozenset(), p_sp):
+            zn, zbn = z.copy(), zb.astype(int).copy()
+            for i in range(len(z)):
+                k = z[i]
+                if split_to[k] >= 0:
+                    if zb[i] == 1:
+                        zn[i] = split_to[k]
+                    zbn[i] = -1  # redrawn: not part of the key
+                elif k in merged_into:
+                    zn[i], zbn[i] = merged_into[k], 1
+                elif k in head:
+                    zbn[i] = 0
+            age = [1] * S
+            for k in range(K):
+                if split_to[k] >= 0:
+                    age[k] = age[split_to[k]] = 0
+                if k in head:
+                    age[k] = 0
+            alive = [k for k in range(S) if k not in merged_into]
+            newid = {k: j for j, k in enumerate(alive)}
+            key = (len(alive), tuple(newid[k] for k in zn), tuple(age[k] for k in alive), tuple(zbn),
+                   (sum(v >= 0 for v in split_to), len(merged_into), rejected))
+            out[key] = out.get(key, 0.0) + prob
+    return out
+
+
+def test_split_merge_plumbing_exact_distribution(oracle_mod):
+    """One split/merge step (Eqs. sample_splits, sample_merges; one merge per cluster,
+    Sec. 4.3) from a fixed three-cluster state with K_max = 4, so that at most one split
+    fits and a second accepted split is rejected and counted: the joint distribution of
+    (K, relabelled z, ages, the deterministic sub-labels, counters) over 20,000 runs
+    against the exact distribution enumerated independently from the acceptance
+    probabilities.  This pins the id assignment, the compaction, the sub-labels of
+    merged clusters, the ages (split eligibility) and the K_max rule."""
+    X, z, zb = _PLUMB_X, _PLUMB_Z, _PLUMB_ZB
+    b1, b2 = _PLUMB_B
+    K, K_max = 3, 4
+    ps, pm = _plumb_ratios(X, z, zb, _PLUMB_ALPHA, b1, b2, K)
+    assert all(0.2 < v < 0.8 for v in ps + list(pm.values())), (ps, pm)
+    exact = _plumb_outcomes(ps, pm, K, K_max, z, zb)
+    assert abs(sum(exact.values()) - 1.0) < 1e-12
+    o = O.Oracle(O.DIRICHLET, 2, K_max, _PLUMB_ALPHA, beta=[b1, b2], burn_out=0)
+    o.set_data(X)
+    R = 20000
+    counts = {}
+    coin = []
+    for r in range(R):
+        o.set_state(K, z, zb)
+        o.sweep(1, 30000 + r, mask=O.MASK_SPLITMERGE)
+        zo, zbo = o.labels()
+        c = o.counters()
+        ages = tuple(int(v) for v in o.ages())
+        # sub-labels of the clusters a split created are redrawn; compare the rest
+        key_z = tuple(int(v) for v in zo)
+        counts_key = None
+        for key in exact:
+            if key[0] == o.K and key[1] == key_z and key[2] == ages and key[4] == (c["splits"], c["merges"],
+                                                                                 c["split_rejected_kmax"]):
+                if all(e < 0 or e == int(g) for e, g in zip(key[3], zbo)):
+                    counts_key = key
+                    coin.extend(int(g) for e, g in zip(key[3], zbo) if e < 0)
+                    break
+        assert counts_key is not None, (o.K, key_z, ages, list(zbo), c)
+        counts[counts_key] = counts.get(counts_key, 0) + 1
+    keys = sorted(exact, key=lambda k: -exact[k])
+    obs = np.array([counts.get(k, 0) for k in keys], float)
+    exp_ = np.array([exact[k] for k in keys]) * R
+    keep = exp_ > 5
+    chi = ((obs[keep] - exp_[keep]) ** 2 / exp_[keep]).sum()
+    rest_o, rest_e = obs[~keep].sum(), exp_[~keep].sum()
+    if rest_e > 0:
+        chi += (rest_o - rest_e) ** 2 / rest_e
+    df = int(keep.sum()) - 1 + (rest_e > 0)
+    assert stats.chi2.sf(chi, df) > 1e-4, (chi, df)
+    # the redrawn sub-labels of a split cluster are fair coins
+    coin = np.array(coin)
+    assert coin.size > 1000 and abs(coin.mean() - 0.5) < 5 * 0.5 / math.sqrt(coin.size)
+
+
 # -------------------------------------------------------------------- invariants
 
 @pytest.mark.parametrize("kind", [O.NIW, O.DIRICHLET])
 def test_chain_invariants(oracle_mod, kind):
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     if kind == O.NIW:
         X, _ = synth.gaussian_mixture(1500, 3, 4, 10.0, seed=7, dtype=np.float64)

@@ -31,7 +31,7 @@ def test_noalloc_statistics_match_ordinary_path():
 
     __graft_entry__.build()
     import paper_2204_08988_gb300 as P
-    from paper_2204_08988_gb300 import synth
+    import synth
 
     N, d = 100_003, 8
     X, y = synth.gaussian_mixture(N, d, 5, 4.0, seed=71)
