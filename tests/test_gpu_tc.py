@@ -66,9 +66,11 @@ def test_tc_scores_within_budget(N, d, K):
     X, y, zb, o, g, p = _setup(N, d, K, seed=N + d)
     s_tc = g.label_scores()
     s_64 = _fp64_scores(X, p, K)
+    # an empty cluster (log weight -inf) must score -inf, not a finite value that could win
+    assert np.array_equal(np.isneginf(s_tc), np.isneginf(s_64))
     fin = np.isfinite(s_64)
-    err = np.abs(s_tc - s_64)
-    cont = s_64 >= s_64.max(1, keepdims=True) - 20.0
+    err = np.where(fin, np.abs(s_tc - np.where(fin, s_64, 0.0)), 0.0)
+    cont = fin & (s_64 >= s_64.max(1, keepdims=True) - 20.0)
     assert err[cont].mean() < 0.02, err[cont].mean()
     assert np.quantile(err[cont], 0.99) < 0.1
     assert err[cont].max() < 0.5, err[cont].max()
@@ -179,8 +181,10 @@ def test_mult_scores_within_budget(N, d, K):
     X, y, zb, o, g, p = _mult_setup(N, d, K, seed=N + d)
     s_tc = g.label_scores()
     s_64 = np.stack([p["logw"][3 * k] + X.astype(np.float64) @ p["logtheta"][3 * k] for k in range(K)], 1)
-    err = np.abs(s_tc - s_64)
-    cont = s_64 >= s_64.max(1, keepdims=True) - 20.0
+    assert np.array_equal(np.isneginf(s_tc), np.isneginf(s_64))
+    fin = np.isfinite(s_64)
+    err = np.where(fin, np.abs(s_tc - np.where(fin, s_64, 0.0)), 0.0)
+    cont = fin & (s_64 >= s_64.max(1, keepdims=True) - 20.0)
     assert err[cont].mean() < 0.02, err[cont].mean()
     assert err[cont].max() < 0.2, err[cont].max()
     g.close()
