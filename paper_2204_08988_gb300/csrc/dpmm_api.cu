@@ -219,8 +219,9 @@ static dpmm_status check_derr(dpmm_ctx* c) {
 }
 
 static void free_data(dpmm_ctx* c) {
-    dfree(c->X); dfree(c->z); dfree(c->zbar); dfree(c->idx); dfree(c->hist); dfree(c->x3_ximg);
+    dfree(c->X); dfree(c->z); dfree(c->zbar); dfree(c->idx); dfree(c->hist); dfree(c->x3_ximg); dfree(c->tc_carry);
     c->X = nullptr; c->z = nullptr; c->zbar = nullptr; c->idx = nullptr; c->hist = nullptr; c->x3_ximg = nullptr;
+    c->tc_carry = nullptr;
 }
 
 static void drop_graph(dpmm_ctx* c) {
@@ -409,6 +410,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     A(&c->zbar, N);
     A(&c->idx, sizeof(int) * N);
     A(&c->hist, sizeof(int) * (size_t)c->K_max * c->T_tiles);
+    if (const size_t cb = tc_carry_bytes(c)) A(&c->tc_carry, cb);
     if (!ok) {
         free_data(c);
         return fail(c, DPMM_ENOMEM, "device allocation for the data failed");

@@ -238,6 +238,7 @@ struct dpmm_ctx {
 
     // tensor-core path
     int* tc_flag = nullptr;        // device: 1 when K did not fit the tensor-core kernel
+    void* tc_carry = nullptr;      // device: per-point state between cluster groups (TF32), N x 20 B
     double* dbg_scores = nullptr;  // device N x K scores when the score hook is active
 
     // one sweep captured as a CUDA graph (kernels read K and the sweep index from
@@ -269,6 +270,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
 cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed);
 cudaError_t launch_advance(dpmm_ctx* c);
 bool tc_supported(const dpmm_ctx* c);
+size_t tc_carry_bytes(const dpmm_ctx* c);
 cudaError_t tc_prepare(dpmm_ctx* c);
 bool substats_tc_supported(const dpmm_ctx* c);
 cudaError_t substats_tc_prepare(dpmm_ctx* c);

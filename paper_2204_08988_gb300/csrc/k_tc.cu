@@ -14,6 +14,16 @@
 // score plus the largest possible FP32 Gumbel is below the best perturbed score seen
 // so far is skipped, which leaves the argmax unchanged.
 //
+// Cluster groups: the factors of the clusters being scored are held in shared memory (up
+// to capc clusters: 27 at d = 32).  More clusters are scored in groups of capc: each CTA
+// passes over its tiles once per group, reloading the factor slice in between.  Between groups each point carries its best and
+// second-best scores so far (and the cluster of the best), and the best perturbed score
+// among the clusters drawn so far (and its cluster).  A group draws for its clusters within
+// the window of the running best whenever two or more clusters are in that window, and
+// also for the carried best cluster, whose draw was deferred while it stood alone; a
+// cluster skipped in an earlier group was outside an earlier (lower) best's window and so
+// is outside the final one.  The result is the same argmax as one pass over all clusters.
+//
 // CTA roles (576 threads, one CTA per SM, persistent over 128-point tiles):
 //   warp 0     : TMA producer (X tiles, 128 rows x 128 B, SWIZZLE_128B, 3 stages)
 //   warp 1     : TMEM allocation (512 columns) and the single-thread MMA issue
@@ -21,7 +31,8 @@
 //                clusters p, p + 4, ... of a chunk; the parts exchange their running
 //                maxima before drawing and then merge their argmax per point.
 // The factor image of all clusters is copied once into shared memory (pre-swizzled
-// by tc_prepare).  Accumulators are double-buffered in TMEM (2 x 256 columns).
+// by tc_prepare).  Accumulators are double-buffered in TMEM (NBUF = 2 buffers of 256
+// columns; four buffers of 128 columns were slower: the cost per chunk is mostly fixed).
 // Every mbarrier wait is bounded; on timeout the kernel records DPMM_ETIMEOUT,
 // drains its own copies and MMAs (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -46,17 +57,32 @@ constexpr int NTHREADS = 32 * (EPI0 + NEPI);
 // best score (FP32 uniforms: 16.64 + 2.82), plus one nat for rounding.
 constexpr float WINDOW = 20.5f;
 constexpr uint32_t TMEM_COLS = 512;
+constexpr int NBUF = 2;                        // TMEM accumulator buffers
+constexpr int BUFCOLS = (int)TMEM_COLS / NBUF; // columns per buffer (the chunk width)
+
+// per-point state carried from one cluster group to the next
+struct Carry {
+    float* g1;  // best score so far
+    float* g2;  // second-best score so far
+    float* v;   // best perturbed score among the clusters drawn so far (-inf: none)
+    int* k1;    // cluster of the best score
+    int* zv;    // cluster of the best perturbed score
+};
 
 struct Args {
     int64_t N;
     int d, dn;        // dimension and per-cluster column block (round_up(d, 8))
-    int NC;           // clusters per MMA chunk (NC * dn <= 256, multiple of 16)
+    int NC;           // clusters per MMA chunk (NC * dn <= BUFCOLS, multiple of 16)
     int cap_rows;     // factor rows that fit in shared memory
+    int capc;         // clusters per group (cap_rows / dn)
+    int gmax;         // most cluster groups (more clusters: the CUDA-core kernel)
+    int img_rows;     // rows of the factor image in global memory (all K_max clusters)
+    Carry carry;
     int Kmax;
     const int* dK;
     const uint32_t* diter;
     uint64_t seed;
-    const void* img;  // factor image: rows (k * dn + j) x 128 B, swizzled; at cap_rows * 128 B
+    const void* img;  // factor image: rows (k * dn + j) x 128 B, swizzled; at img_rows * 128 B
                       // the -b image: rows x 32 B, no swizzle (8-row groups of 256 B)
     const float* qc;  // c_k, slot 3k
     int32_t* z;
@@ -76,14 +102,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     unsigned char* bb = bs + (size_t)a.cap_rows * 128;          // cap_rows x 32
     float* ones = (float*)(bb + (size_t)a.cap_rows * 32);       // BM rows x 8, no swizzle
     float* sbuf = ones + BM * 8;                                // (cap_rows / dn) clusters x BM
-    float* ct = sbuf + (size_t)(a.cap_rows / a.dn) * BM;        // Kmax
-    uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + a.Kmax) + 7) & ~(uintptr_t)7);
+    float* sbend = sbuf + (size_t)(a.cap_rows / a.dn) * BM;
+    uint64_t* bars = (uint64_t*)(((uintptr_t)(sbend + a.Kmax) + 7) & ~(uintptr_t)7);
     uint64_t* full = bars;            // XST
     uint64_t* empty = full + XST;     // XST
-    uint64_t* tfull = empty + XST;    // 2
-    uint64_t* tempty = tfull + 2;     // 2
-    uint64_t* bload = tempty + 2;     // 1
-    uint64_t* sfull = bload + 1;      // 2 x 4 (slot, lane quarter): the parts published their two best
+    uint64_t* tfull = empty + XST;    // NBUF
+    uint64_t* tempty = tfull + NBUF;  // NBUF
+    uint64_t* bload = tempty + NBUF;  // 1: the group's factor image has landed (phase g & 1)
+    uint64_t* facfree = bload + 1;    // 1: the group's last MMAs are complete (phase g & 1)
+    uint64_t* sfull = facfree + 1;    // 2 x 4 (slot, lane quarter): the parts published their two best
     uint64_t* qbar = sfull + 8;       // 4: the parts of a lane quarter published their draws
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -94,14 +121,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = *a.dK;
-    const int rows = K * a.dn;
-    const int rows_pad = (rows + 15) / 16 * 16;
-    if (rows_pad > a.cap_rows) {  // does not fit: leave the step to the CUDA-core kernel
+    const int ngroups = (K + a.capc - 1) / a.capc;
+    if (ngroups > a.gmax) {  // too many groups: the CUDA-core kernel does the step
         if (blockIdx.x == 0 && threadIdx.x == 0) *a.overflow = 1;
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.overflow = 0;
-    const int nch = (K + a.NC - 1) / a.NC;
+    // the clusters of group g: [g capc, g capc + Kg(g))
+    auto group_size = [&](int g) { return min(a.capc, K - g * a.capc); };
     const int64_t ntiles = (a.N + BM - 1) / BM;
 
     if (threadIdx.x == 0) {
@@ -110,13 +137,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NBUF; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], NEPI * 32);
+            mbar_init(&tempty[b], NEPI);  // one arrival per epilogue warp
         }
         mbar_init(bload, 1);
-        for (int b = 0; b < 8; ++b) mbar_init(&sfull[b], NPART * 32);  // a quarter's rows only
-        for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART * 32);
+        mbar_init(facfree, 1);
+        for (int b = 0; b < 8; ++b) mbar_init(&sfull[b], NPART);  // a quarter's warps only
+        for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -132,7 +160,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         const int m = e >> 3, kk = e & 7;
         ones[(m >> 3) * 64 + (kk >> 2) * 32 + (m & 7) * 4 + (kk & 3)] = kk < 2 ? 1.f : 0.f;
     }
-    for (int k = threadIdx.x; k < K; k += blockDim.x) ct[k] = a.qc[3 * k];
     fence_before();
     __syncthreads();
     fence_after();
@@ -141,63 +168,79 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
 
     if (warp == 0) {
         if (lane == 0) {
-            // factor image, once
-            const uint32_t bbytes = (uint32_t)rows_pad * 128u, nbytes = (uint32_t)rows_pad * 32u;
-            mbar_expect_tx(bload, bbytes + nbytes);
-            for (uint32_t off = 0; off < bbytes; off += 32768u) {
-                uint32_t n = min(32768u, bbytes - off);
-                bulk_load(bs + off, (const unsigned char*)a.img + off, n, bload);
-            }
-            const unsigned char* nsrc = (const unsigned char*)a.img + (size_t)a.cap_rows * 128;
-            for (uint32_t off = 0; off < nbytes; off += 32768u) {
-                uint32_t n = min(32768u, nbytes - off);
-                bulk_load(bb + off, nsrc + off, n, bload);
-            }
-            int64_t it = 0;
+            int64_t it = 0;  // X tiles loaded, over all groups
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-                const int s = (int)(it % XST);
-                const uint32_t ph = (uint32_t)((it / XST) & 1);
-                if (!mbar_wait(&empty[s], ph ^ 1u, abort)) { ok = false; break; }
-                mbar_expect_tx(&full[s], XBYTES);
-                tma_load_2d(xs + (size_t)s * XBYTES, &xmap, 0, (int)(t * BM), &full[s]);
+            for (int g = 0; g < ngroups && ok; ++g) {
+                // the group's slice of the factor image (its first row g capc dn is a multiple
+                // of 8, so the swizzle phase and the 8-row groups of the -b image line up),
+                // once the previous group's MMAs no longer read the old one
+                if (g > 0 && !mbar_wait(facfree, (uint32_t)((g - 1) & 1), abort)) { ok = false; break; }
+                const int kb = g * a.capc, rows_pad = (group_size(g) * a.dn + 15) / 16 * 16;
+                const uint32_t bbytes = (uint32_t)rows_pad * 128u, nbytes = (uint32_t)rows_pad * 32u;
+                mbar_expect_tx(bload, bbytes + nbytes);
+                const unsigned char* fsrc = (const unsigned char*)a.img + (size_t)kb * a.dn * 128;
+                for (uint32_t off = 0; off < bbytes; off += 32768u) {
+                    uint32_t n = min(32768u, bbytes - off);
+                    bulk_load(bs + off, fsrc + off, n, bload);
+                }
+                const unsigned char* nsrc =
+                    (const unsigned char*)a.img + (size_t)a.img_rows * 128 + (size_t)kb * a.dn * 32;
+                for (uint32_t off = 0; off < nbytes; off += 32768u) {
+                    uint32_t n = min(32768u, nbytes - off);
+                    bulk_load(bb + off, nsrc + off, n, bload);
+                }
+                for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+                    const int s = (int)(it % XST);
+                    const uint32_t ph = (uint32_t)((it / XST) & 1);
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], XBYTES);
+                    tma_load_2d(xs + (size_t)s * XBYTES, &xmap, 0, (int)(t * BM), &full[s]);
+                }
+                // own copies must land before the next group's factors are loaded over them
+                if (ok && !mbar_wait(bload, (uint32_t)(g & 1), abort)) ok = false;
             }
             if (!ok) {
                 atomicExch(a.derr, (int)DPMM_ETIMEOUT);
                 *abort = 1;
             }
             // own copies must land before the CTA may exit
-            mbar_wait(bload, 0, abort);
             for (int64_t j = (it > XST ? it - XST : 0); j < it; ++j)
                 mbar_wait(&full[(int)(j % XST)], (uint32_t)((j / XST) & 1), abort);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            bool ok = mbar_wait(bload, 0, abort);
+            bool ok = true;
             int64_t it = 0, ch = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-                const int s = (int)(it % XST);
-                if (!mbar_wait(&full[s], (uint32_t)((it / XST) & 1), abort)) { ok = false; break; }
-                fence_after();
-                const uint32_t xa = saddr(xs + (size_t)s * XBYTES);
-                for (int c = 0; c < nch; ++c, ++ch) {
-                    const int b = (int)(ch & 1);
-                    if (!mbar_wait(&tempty[b], (uint32_t)(((ch >> 1) & 1) ^ 1), abort)) { ok = false; break; }
+            for (int g = 0; g < ngroups && ok; ++g) {
+                if (!mbar_wait(bload, (uint32_t)(g & 1), abort)) { ok = false; break; }
+                const int Kg = group_size(g), nch = (Kg + a.NC - 1) / a.NC;
+                for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+                    const int s = (int)(it % XST);
+                    if (!mbar_wait(&full[s], (uint32_t)((it / XST) & 1), abort)) { ok = false; break; }
                     fence_after();
-                    const int nclus = min(a.NC, K - c * a.NC);
-                    const int n = (nclus * a.dn + 15) / 16 * 16;
-                    const uint32_t ba = saddr(bs + (size_t)c * a.NC * a.dn * 128);
-                    const uint32_t nb = saddr(bb + (size_t)c * a.NC * a.dn * 32);
-                    const uint32_t id = idesc(n, FMT);
-                    const int ksteps = 4;  // 128-byte rows in 32-byte MMA steps
+                    const uint32_t xa = saddr(xs + (size_t)s * XBYTES);
+                    for (int c = 0; c < nch; ++c, ++ch) {
+                        const int b = (int)(ch % NBUF);
+                        if (!mbar_wait(&tempty[b], (uint32_t)(((ch / NBUF) & 1) ^ 1), abort)) { ok = false; break; }
+                        fence_after();
+                        const int nclus = min(a.NC, Kg - c * a.NC);
+                        const int n = (nclus * a.dn + 15) / 16 * 16;
+                        const uint32_t ba = saddr(bs + (size_t)c * a.NC * a.dn * 128);
+                        const uint32_t nb = saddr(bb + (size_t)c * a.NC * a.dn * 32);
+                        const uint32_t id = idesc(n, FMT);
+                        const int ksteps = 4;  // 128-byte rows in 32-byte MMA steps
 #pragma unroll
-                    for (int kk = 0; kk < ksteps; ++kk)
-                        mma<FMT>(tmem + (uint32_t)(b * 256), sdesc(xa + kk * 32), sdesc(ba + kk * 32), id, kk > 0);
-                    mma<FMT>(tmem + (uint32_t)(b * 256), sdesc_ns(saddr(ones)), sdesc_ns(nb), id, true);  // - b
-                    mma_commit(&tfull[b]);
+                        for (int kk = 0; kk < ksteps; ++kk)
+                            mma<FMT>(tmem + (uint32_t)(b * BUFCOLS), sdesc(xa + kk * 32), sdesc(ba + kk * 32), id,
+                                     kk > 0);
+                        mma<FMT>(tmem + (uint32_t)(b * BUFCOLS), sdesc_ns(saddr(ones)), sdesc_ns(nb), id, true);  // - b
+                        mma_commit(&tfull[b]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&empty[s]);
                 }
-                if (!ok) break;
-                mma_commit(&empty[s]);
+                // the factor image may be replaced once this group's MMAs are complete
+                if (ok) mma_commit(facfree);
             }
             if (!ok) {
                 atomicExch(a.derr, (int)DPMM_ETIMEOUT);
@@ -217,6 +260,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         int64_t ch = 0, it = 0;
         uint32_t nq = 0;  // uses of this quarter's draw barrier (the same in its four parts)
         bool ok = true;
+        for (int g = 0; g < ngroups && ok; ++g) {
+        const int kb = g * a.capc, Kg = group_size(g), nch = (Kg + a.NC - 1) / a.NC;
+        const bool first = g == 0, final = g == ngroups - 1;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
             const int64_t i = t * BM + r;
             // Exact Gumbel-max.  Every part scores its clusters (kept in shared memory)
@@ -226,24 +272,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             // part draws for its clusters within the window and part 0 merges.
             float m1 = -INFINITY, m2 = -INFINITY;
             int k1 = 0;
-            float* sr = sbuf + r;  // score of cluster k at sr[k * BM]
-            auto score = [&](int k, float q) {
-                const float sc = ct[k] - 0.5f * q;
+            float* sr = sbuf + r;  // score of the group's cluster kk at sr[kk * BM]
+            auto score = [&](int kk, float q) {
+                const float sc = __ldg(a.qc + 3 * (kb + kk)) - 0.5f * q;
                 if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
-                    if (i < a.N) a.scores[i * K + k] = (double)sc;
+                    if (i < a.N) a.scores[i * K + kb + kk] = (double)sc;
                 }
-                sr[k * BM] = sc;
+                sr[kk * BM] = sc;
                 const bool gt = sc > m1;
                 m2 = gt ? m1 : fmaxf(m2, sc);
-                k1 = gt ? k : k1;
+                k1 = gt ? kb + kk : k1;
                 m1 = gt ? sc : m1;
             };
             for (int c = 0; c < nch; ++c, ++ch) {
-                const int b = (int)(ch & 1);
-                if (!mbar_wait(&tfull[b], (uint32_t)((ch >> 1) & 1), abort)) { ok = false; break; }
+                const int b = (int)(ch % NBUF);
+                if (!mbar_wait(&tfull[b], (uint32_t)((ch / NBUF) & 1), abort)) { ok = false; break; }
                 fence_after();
-                const int nclus = min(a.NC, K - c * a.NC);
-                const uint32_t cbase = tmem + lane_off + (uint32_t)(b * 256);
+                const int nclus = min(a.NC, Kg - c * a.NC);
+                const uint32_t cbase = tmem + lane_off + (uint32_t)(b * BUFCOLS);
                 if (a.dn == 32) {  // 32-column loads never pass the block's own columns
                     for (int cc = part; cc < nclus; cc += NPART) {
                         float y[32];
@@ -265,8 +311,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                         score(c * a.NC + cc, q0 + q1);
                     }
                 }
+                // the warp's loads are complete (wait::ld); one lane arrives for the warp
                 fence_before();
-                mbar_arrive(&tempty[b]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
             // Slot sl is reused two tiles later; every reader of it has arrived on the
@@ -276,7 +324,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             xm1[sl][part][r] = m1;
             xm2[sl][part][r] = m2;
             xk1[sl][part][r] = k1;
-            mbar_arrive(&sfull[sl * 4 + quarter]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sfull[sl * 4 + quarter]);
             if (!mbar_wait(&sfull[sl * 4 + quarter], use, abort)) { ok = false; break; }
             // the row's best and second-best scores (every part computes the same)
             float g1 = xm1[sl][0][r], g2 = xm2[sl][0][r];
@@ -293,8 +342,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                     g2 = fmaxf(g2, o1);
                 }
             }
+            // the state carried from the earlier groups (their clusters have lower ids)
+            float cg1 = -INFINITY, cg2 = -INFINITY, cv = -INFINITY;
+            int ck1 = 0, cz = 0;
+            if (!first && i < a.N) {
+                cg1 = a.carry.g1[i];
+                cg2 = a.carry.g2[i];
+                cv = a.carry.v[i];
+                ck1 = a.carry.k1[i];
+                cz = a.carry.zv[i];
+            }
+            if (!first) {
+                if (cg1 >= g1) {
+                    g2 = fmaxf(g1, cg2);
+                    g1 = cg1;
+                    gk = ck1;
+                } else {
+                    g2 = fmaxf(g2, cg1);
+                }
+            }
             const float lim = g1 - WINDOW;
             const bool need = !(g2 <= lim);  // another cluster might win: draw
+            float vbest = cv;  // best perturbed score among all clusters drawn so far
+            int zbest = cz;
             if (__any_sync(0xffffffffu, need)) {  // the same answer in the four parts
                 float best = -INFINITY;
                 int zb = 0;
@@ -313,20 +383,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                     // lanes', any further one at once
                     int c0 = -1, c1 = -1;
                     float s0 = 0.f, s1 = 0.f;
-                    for (int k = part; k < K; k += NPART) {
-                        const float sc = sr[k * BM];
+                    for (int kk = part; kk < Kg; kk += NPART) {
+                        const float sc = sr[kk * BM];
                         if (sc > lim) {
-                            if (c0 < 0) { c0 = k; s0 = sc; }
-                            else if (c1 < 0) { c1 = k; s1 = sc; }
-                            else draw(k, sc);
+                            if (c0 < 0) { c0 = kb + kk; s0 = sc; }
+                            else if (c1 < 0) { c1 = kb + kk; s1 = sc; }
+                            else draw(kb + kk, sc);
                         }
                     }
                     if (c0 >= 0) draw(c0, s0);
                     if (c1 >= 0) draw(c1, s1);
+                    // the carried best cluster: its draw is deferred until a rival appears
+                    // (drawing it again later gives the same value)
+                    if (part == 0 && !first && cg1 > lim) draw(ck1, cg1);
                 }
                 mbest[sl][part][r] = best;
                 mz[sl][part][r] = zb;
-                mbar_arrive(&qbar[quarter]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&qbar[quarter]);
                 if (!mbar_wait(&qbar[quarter], (uint32_t)(nq & 1), abort)) { ok = false; break; }
                 ++nq;
                 if (part == 0 && need) {
@@ -339,10 +413,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                             zb = oz;
                         }
                     }
-                    gk = zb;
+                    if (cv > best || (cv == best && cz < zb)) {
+                        best = cv;
+                        zb = cz;
+                    }
+                    vbest = best;
+                    zbest = zb;
                 }
             }
-            if (part == 0 && i < a.N) a.z[i] = gk;
+            if (part == 0 && i < a.N) {
+                if (final) {
+                    a.z[i] = need ? zbest : gk;
+                } else {
+                    // read back by every part of this row in the next group, after barriers
+                    // this warp arrives on after these stores
+                    a.carry.g1[i] = g1;
+                    a.carry.g2[i] = g2;
+                    a.carry.v[i] = vbest;
+                    a.carry.k1[i] = gk;
+                    a.carry.zv[i] = zbest;
+                }
+            }
+        }
         }
         if (!ok) {
             atomicExch(a.derr, (int)DPMM_ETIMEOUT);
@@ -361,16 +453,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
 
 // factor image: row n = k * dn + j holds W_k[l][j], l = 0..31 (zero beyond d), in the
 // 128-byte swizzle pattern: 16-byte chunk c of row n sits at chunk c ^ (n & 7).  At
-// byte offset rows_cap * 128 follows the -b image (no swizzle, 32 B per row, element
+// byte offset img_rows * 128 (every cluster up to K_max) follows the -b image (no swizzle, 32 B per row, element
 // (n, l) at (n / 8) * 256 + (l / 4) * 128 + (n % 8) * 16 + (l % 4) * 4): row n holds
 // (-b_hi, -b_lo, 0, ..., 0), where b = sum_m mu_m W_k[m][j] is formed in FP64 with
 // the factor as the tensor cores see it, b_hi = tf32(b) and b_lo = tf32(b - b_hi).
 __global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const double* pW, const double* pmu,
-                                int rows_cap, float* img) {
+                                int img_rows, float* img) {
     const int K = *dK;
     const int rows = (K * dn + 15) / 16 * 16;
-    const int64_t total = (int64_t)min(rows, rows_cap) * 32;
-    float* nb = img + (size_t)rows_cap * 32;
+    const int64_t total = (int64_t)min(rows, img_rows) * 32;
+    float* nb = img + (size_t)img_rows * 32;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int n = (int)(e / 32), l = (int)(e % 32);
         const int k = n / dn, j = n % dn;
@@ -413,14 +505,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
 }
 
 struct TcCfg {
-    int dn, NC, cap_rows;
+    int dn, NC, cap_rows, capc, gmax, img_rows;
     size_t smem;
 };
+
+// cluster groups per label step at most; K beyond gmax * capc goes to the CUDA-core kernel
+constexpr int TC_GMAX = 4;
 
 static TcCfg tc_cfg(const dpmm_ctx* c) {
     TcCfg q;
     q.dn = (c->d + 7) / 8 * 8;
-    q.NC = 256 / q.dn;
+    q.NC = tc::BUFCOLS / q.dn;
     while ((q.NC * q.dn) % 16) --q.NC;
     const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 4 + 32 * 8 + 64;
     const size_t limit = 227 * 1024 - 24576;  // leave room for the kernel's static shared memory (22 KB)
@@ -429,6 +524,12 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * per_row;
     size_t cap = std::min(want, limit - fixed);
     q.cap_rows = (int)(cap / per_row / 16 * 16);
+    q.capc = q.cap_rows / q.dn;
+    q.gmax = std::max(1, std::min(TC_GMAX, (c->K_max + q.capc - 1) / q.capc));
+    // a group's slice starts at row kb * dn (a multiple of 8: the swizzle phase and the -b
+    // image's 8-row groups line up) and is read padded to 16 rows, which can pass the last
+    // cluster's rows by 8: 16 zero rows of slack
+    q.img_rows = (c->K_max * q.dn + 15) / 16 * 16 + 16;
     q.smem = fixed + (size_t)q.cap_rows * (128 + 32) + (size_t)(q.cap_rows / q.dn) * tc::BM * 4;
     if (q.smem < 120 * 1024) q.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     return q;
@@ -449,7 +550,7 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
     if (c->kind == DPMM_PRIOR_DIRICHLET) return mult_supported(c) ? mult_prepare(c) : cudaSuccess;
     if (c->prec != DPMM_PREC_TF32) return cudaSuccess;
     TcCfg q = tc_cfg(c);
-    const size_t bytes = (size_t)q.cap_rows * (128 + 32);
+    const size_t bytes = (size_t)q.img_rows * (128 + 32);
     if (!c->tc_img || c->tc_img_bytes < bytes) {
         if (c->tc_img) cudaFree(c->tc_img);
         c->tc_img = nullptr;
@@ -461,7 +562,7 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
         e = cudaMemsetAsync(c->tc_img, 0, bytes, c->stream);
         if (e != cudaSuccess) return e;
     }
-    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->p_W, c->p_mu, q.cap_rows,
+    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->p_W, c->p_mu, q.img_rows,
                                                     (float*)c->tc_img);
     c->nlaunch += 1;
     return cudaGetLastError();
@@ -488,12 +589,21 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
         if (e == cudaSuccess) e = cudaMemsetAsync(c->tc_flag, 0, sizeof(int), c->stream);
         if (e != cudaSuccess) return e;
     }
+    if (q.gmax > 1 && !c->tc_carry) return cudaErrorNotSupported;  // allocated with the data
     tc::Args a;
     a.N = c->N;
     a.d = c->d;
     a.dn = q.dn;
     a.NC = q.NC;
     a.cap_rows = q.cap_rows;
+    a.capc = q.capc;
+    a.gmax = q.gmax;
+    a.img_rows = q.img_rows;
+    {
+        float* f = (float*)c->tc_carry;
+        const size_t n = (size_t)c->N;
+        a.carry = tc::Carry{f, f + n, f + 2 * n, (int*)(f + 3 * n), (int*)(f + 4 * n)};
+    }
     a.Kmax = c->K_max;
     a.dK = c->dK;
     a.diter = c->diter;
@@ -511,12 +621,21 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
     const int grid = (int)std::min<int64_t>(c->num_sms, ntiles);
     prof_begin(c, "labels_tc");
     kern<<<grid, tc::NTHREADS, q.smem, c->stream>>>(map, a);
-    prof_end(c, "labels_tc");
     c->nlaunch += 1;
+    prof_end(c, "labels_tc");
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // K beyond the shared-memory capacity: the CUDA-core kernel does the step
     return launch_labels_simt_gated(c, seed, c->tc_flag);
 }
 
+}  // namespace dpmm
+
+namespace dpmm {
+// bytes of the per-point state carried between cluster groups of the TF32 label step
+// (0 when one group holds every cluster up to K_max)
+size_t tc_carry_bytes(const dpmm_ctx* c) {
+    if (c->kind != DPMM_PRIOR_NIW || c->prec != DPMM_PREC_TF32 || !tc_supported(c)) return 0;
+    return tc_cfg(c).gmax > 1 ? (size_t)c->N * 20 : 0;
+}
 }  // namespace dpmm

@@ -23,12 +23,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
 }
+// try_wait suspends the thread until the phase completes or a time limit passes; the
+// hint (in ns) asks for a long suspension, so that a waiting warp is woken by the phase
+// change instead of re-issuing the test in a loop and taking issue slots from the
+// warps that do the work
+constexpr uint32_t SUSPEND_NS = 200000;
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
+        : "r"(saddr(b)), "r"(parity), "r"(SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -144,16 +149,22 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* va,
     }
 }
 
-// squared norm of a 32-wide block (four independent chains)
+// squared norm of a 32-wide block: four independent chains (elements j = 0, 1, 2, 3 mod 4),
+// run two at a time by the packed FP32 FMA (fma.rn.f32x2: two FMAs, each rounded to
+// nearest, the same values as four scalar chains)
 __device__ __forceinline__ float sqsum32(const float* y) {
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+    uint64_t a01 = 0ull, a23 = 0ull;
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
-        q0 = fmaf(y[j], y[j], q0);
-        q1 = fmaf(y[j + 1], y[j + 1], q1);
-        q2 = fmaf(y[j + 2], y[j + 2], q2);
-        q3 = fmaf(y[j + 3], y[j + 3], q3);
+        uint64_t v01, v23;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(v01) : "f"(y[j]), "f"(y[j + 1]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(v23) : "f"(y[j + 2]), "f"(y[j + 3]));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a01) : "l"(v01));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a23) : "l"(v23));
     }
+    float q0, q1, q2, q3;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(q0), "=f"(q1) : "l"(a01));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(q2), "=f"(q3) : "l"(a23));
     return (q0 + q1) + (q2 + q3);
 }
 

@@ -61,8 +61,12 @@ def _fp64_scores(X, p, K):
     return out
 
 
-@pytest.mark.parametrize("N,d,K", [(5000, 32, 4), (3001, 32, 20), (2000, 8, 6), (1500, 20, 9)])
+@pytest.mark.parametrize("N,d,K", [(5000, 32, 4), (3001, 32, 20), (2000, 8, 6), (1500, 20, 9), (3001, 32, 28),
+                                   (9000, 32, 45), (12800, 32, 64), (8000, 8, 61)])
 def test_tc_scores_within_budget(N, d, K):
+    """Every score of every point against FP64.  Above 27 clusters at d = 32 the factors
+    no longer fit one launch's shared memory and the clusters are scored in groups, one
+    launch per group (K = 28: a group of one cluster; 45: two groups; 64 = K_max: three)."""
     X, y, zb, o, g, p = _setup(N, d, K, seed=N + d)
     s_tc = g.label_scores()
     s_64 = _fp64_scores(X, p, K)
@@ -78,10 +82,11 @@ def test_tc_scores_within_budget(N, d, K):
     g.close()
 
 
-@pytest.mark.parametrize("K", [20, 45])
+@pytest.mark.parametrize("K", [20, 28, 45, 64])
 def test_tc_labels_agree_with_fp64(K):
-    """K=45 at d=32 exceeds the shared-memory capacity of the tensor-core kernel, so
-    the CUDA-core kernel takes the step: labels must still agree."""
+    """Above 27 clusters at d = 32 the tensor-core kernel scores the clusters in groups
+    (one launch each) and carries each point's best scores and best perturbed score from
+    group to group; the labels must agree with FP64 as for one group."""
     N, d = 20000, 32
     X, y, zb, o, g, p = _setup(N, d, K, seed=7 + K)
     g.set_mask(2)
