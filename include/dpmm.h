@@ -92,7 +92,9 @@ typedef enum {
 } dpmm_prec;
 
 /* Create a chain.  alpha > 0 is the DP concentration (Eq. DPLatentVar); d >= 1
- * the dimension (at most 160 for the NIW prior, 4092 for the Dirichlet prior);
+ * the dimension (at most 160 for the NIW prior, 65536 for the Dirichlet prior;
+ * multinomial data of more than 256 categories are held as compressed rows, see
+ * dpmm_set_data_csr, run in FP32 or FP64_PLAIN and take K_max <= 256);
  * 1 <= K_max <= 1000 the capacity for clusters (a split that would exceed it is
  * rejected and counted, Sec. 4.1 "Propose and accept splits").
  * Errors: DPMM_EINVAL for invalid hyper-parameters or sizes (kappa0 <= 0,
@@ -114,6 +116,17 @@ dpmm_status dpmm_set_options(dpmm_ctx* ctx, dpmm_prec prec, int init_K, int burn
  * staged in device memory.  Resets the chain: the labels are drawn at the next sweep.
  * Errors: DPMM_EINVAL (N < 1, NULL X, type not allowed for the prior). */
 dpmm_status dpmm_set_data(dpmm_ctx* ctx, const void* X, int64_t N, dpmm_dtype dt, int on_device);
+
+/* Multinomial data of more than 256 categories as compressed rows (Sec. 5.3's
+ * document-word data; such data are also taken by dpmm_set_data as dense counts and
+ * compressed on the device): host arrays indptr[N + 1] (indptr[0] = 0, non-decreasing),
+ * indices[nnz] (categories in [0, d), increasing within each row) and counts[nnz]
+ * (in [0, 2^24)), nnz = indptr[N].  Copied; resets the chain like dpmm_set_data.  The
+ * score of point i under cluster k is log pi_k + sum over its nonzeros of count x
+ * log theta_kj, the same sum as over all d categories.  Errors: DPMM_EINVAL for a context
+ * that does not hold compressed rows (Gaussian, or d <= 256) or malformed arrays. */
+dpmm_status dpmm_set_data_csr(dpmm_ctx* ctx, const int64_t* indptr, const int32_t* indices, const int32_t* counts,
+                              int64_t N);
 
 /* Replace the values of the data (same N, d, dtype) and keep the chain's state.
  * Used for streaming data and for end-to-end timing with host-resident inputs.

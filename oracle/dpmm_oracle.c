@@ -234,7 +234,9 @@ orc_state* orc_create(int kind, int d, int K_max, double alpha, double kappa0, c
     o->init_K = init_K; o->burn_out = burn_out;
     o->kappa0 = kappa0; o->nu0 = nu0;
     o->m0 = (double*)calloc(d, sizeof(double));
-    o->psi0 = (double*)calloc((size_t)d * d, sizeof(double));
+    /* the d x d arrays exist for the Gaussian model only (a multinomial d can be 20,000) */
+    const size_t dd = kind == ORC_NIW ? (size_t)d * d : 1;
+    o->psi0 = (double*)calloc(dd, sizeof(double));
     o->beta = (double*)calloc(d, sizeof(double));
     if (kind == ORC_NIW) {
         memcpy(o->m0, m0, sizeof(double) * d);
@@ -246,10 +248,10 @@ orc_state* orc_create(int kind, int d, int K_max, double alpha, double kappa0, c
     o->age = (int*)calloc(K_max, sizeof(int));
     o->n = (double*)calloc(S, sizeof(double));
     o->sx = (double*)calloc((size_t)S * d, sizeof(double));
-    o->sxx = (double*)calloc((size_t)S * d * d, sizeof(double));
+    o->sxx = (double*)calloc((size_t)S * dd, sizeof(double));
     o->logw = (double*)calloc(S, sizeof(double));
     o->mu = (double*)calloc((size_t)S * d, sizeof(double));
-    o->W = (double*)calloc((size_t)S * d * d, sizeof(double));
+    o->W = (double*)calloc((size_t)S * dd, sizeof(double));
     o->logdetW = (double*)calloc(S, sizeof(double));
     o->logtheta = (double*)calloc((size_t)S * d, sizeof(double));
     return o;
@@ -287,7 +289,7 @@ static void orc_compute_stats(orc_state* o)
     int d = o->d, S = orc_stat_slots(o);
     memset(o->n, 0, sizeof(double) * S);
     memset(o->sx, 0, sizeof(double) * S * d);
-    memset(o->sxx, 0, sizeof(double) * S * d * d);
+    if (o->kind == ORC_NIW) memset(o->sxx, 0, sizeof(double) * S * d * d);
     for (int64_t i = 0; i < o->N; ++i) {
         const double* x = o->X + i * d;
         int s = 3 * o->z[i] + 1 + o->zbar[i];
@@ -301,9 +303,16 @@ static void orc_compute_stats(orc_state* o)
         int c = 3 * k, a = c + 1, b = c + 2;
         o->n[c] = o->n[a] + o->n[b];
         for (int j = 0; j < d; ++j) o->sx[(size_t)c * d + j] = o->sx[(size_t)a * d + j] + o->sx[(size_t)b * d + j];
-        for (int j = 0; j < d * d; ++j)
-            o->sxx[(size_t)c * d * d + j] = o->sxx[(size_t)a * d * d + j] + o->sxx[(size_t)b * d * d + j];
+        if (o->kind == ORC_NIW)
+            for (int j = 0; j < d * d; ++j)
+                o->sxx[(size_t)c * d * d + j] = o->sxx[(size_t)a * d * d + j] + o->sxx[(size_t)b * d * d + j];
     }
+}
+
+/* second moments of slot s (Gaussian), NULL for the multinomial model */
+static const double* orc_sxx(const orc_state* o, int s)
+{
+    return o->kind == ORC_NIW ? o->sxx + (size_t)s * o->d * o->d : NULL;
 }
 
 int orc_set_state(orc_state* o, int K, const int32_t* z, const uint8_t* zbar)
@@ -467,7 +476,7 @@ static void orc_draw_params(orc_state* o, uint64_t seed, uint32_t problem)
     }
     /* (c), (d) theta_k and thetabar_kh from their posteriors */
     double* mn = (double*)malloc(sizeof(double) * d);
-    double* psin = (double*)malloc(sizeof(double) * d * d);
+    double* psin = (double*)malloc(sizeof(double) * (o->kind == ORC_NIW ? (size_t)d * d : 1));
     for (int s3 = 0; s3 < 3 * K; ++s3) {
         const double* sx = o->sx + (size_t)s3 * d;
         if (o->kind == ORC_NIW) {
@@ -594,9 +603,9 @@ static void orc_split_merge(orc_state* o, uint64_t seed, uint32_t problem)
     for (int k = 0; k < K; ++k) {
         double nl = o->n[3 * k + 1], nr = o->n[3 * k + 2], nk = o->n[3 * k];
         if (o->age[k] < o->burn_out || nl < 1 || nr < 1) continue;
-        double lH = la + lgamma(nl) + orc_log_marginal_slot(o, nl, o->sx + (size_t)(3 * k + 1) * d, o->sxx + (size_t)(3 * k + 1) * d * d) +
-                    lgamma(nr) + orc_log_marginal_slot(o, nr, o->sx + (size_t)(3 * k + 2) * d, o->sxx + (size_t)(3 * k + 2) * d * d) -
-                    lgamma(nk) - orc_log_marginal_slot(o, nk, o->sx + (size_t)(3 * k) * d, o->sxx + (size_t)(3 * k) * d * d);
+        double lH = la + lgamma(nl) + orc_log_marginal_slot(o, nl, o->sx + (size_t)(3 * k + 1) * d, orc_sxx(o, 3 * k + 1)) +
+                    lgamma(nr) + orc_log_marginal_slot(o, nr, o->sx + (size_t)(3 * k + 2) * d, orc_sxx(o, 3 * k + 2)) -
+                    lgamma(nk) - orc_log_marginal_slot(o, nk, o->sx + (size_t)(3 * k) * d, orc_sxx(o, 3 * k));
         double u = orc_uniform(&key, (uint32_t)k, ORC_SPLIT, 0);
         if (log(u) < lH) {
             if (S >= o->K_max) { o->n_split_rejected_kmax++; continue; }
@@ -609,18 +618,19 @@ static void orc_split_merge(orc_state* o, uint64_t seed, uint32_t problem)
     }
 
     double* sxm = (double*)malloc(sizeof(double) * d);
-    double* sxxm = (double*)malloc(sizeof(double) * d * d);
+    double* sxxm = o->kind == ORC_NIW ? (double*)malloc(sizeof(double) * d * d) : NULL;
     for (int k1 = 0; k1 < K; ++k1) {
         if (touched[k1] || merged_into[k1] >= 0 || merge_head[k1]) continue;
         for (int k2 = k1 + 1; k2 < K; ++k2) {
             if (touched[k2] || merged_into[k2] >= 0 || merge_head[k2]) continue;
             double n1 = o->n[3 * k1], n2 = o->n[3 * k2], nm = n1 + n2;
             for (int j = 0; j < d; ++j) sxm[j] = o->sx[(size_t)3 * k1 * d + j] + o->sx[(size_t)3 * k2 * d + j];
-            for (int j = 0; j < d * d; ++j) sxxm[j] = o->sxx[(size_t)3 * k1 * d * d + j] + o->sxx[(size_t)3 * k2 * d * d + j];
+            if (sxxm)
+                for (int j = 0; j < d * d; ++j) sxxm[j] = o->sxx[(size_t)3 * k1 * d * d + j] + o->sxx[(size_t)3 * k2 * d * d + j];
             double lH = lgamma(nm) - la - lgamma(n1) - lgamma(n2) +
                         orc_log_marginal_slot(o, nm, sxm, sxxm) -
-                        orc_log_marginal_slot(o, n1, o->sx + (size_t)3 * k1 * d, o->sxx + (size_t)3 * k1 * d * d) -
-                        orc_log_marginal_slot(o, n2, o->sx + (size_t)3 * k2 * d, o->sxx + (size_t)3 * k2 * d * d) +
+                        orc_log_marginal_slot(o, n1, o->sx + (size_t)3 * k1 * d, orc_sxx(o, 3 * k1)) -
+                        orc_log_marginal_slot(o, n2, o->sx + (size_t)3 * k2 * d, orc_sxx(o, 3 * k2)) +
                         lgamma(o->alpha) - lgamma(o->alpha + nm) + lgamma(0.5 * o->alpha + n1) +
                         lgamma(0.5 * o->alpha + n2) - 2.0 * lgamma(0.5 * o->alpha);
             double u = orc_uniform(&key, (uint32_t)k1, ORC_MERGE, (uint32_t)k2);
@@ -723,7 +733,7 @@ void orc_get_stats(const orc_state* o, double* n, double* sx, double* sxx)
     int d = o->d, S = 3 * o->K;
     memcpy(n, o->n, sizeof(double) * S);
     memcpy(sx, o->sx, sizeof(double) * S * d);
-    if (sxx) memcpy(sxx, o->sxx, sizeof(double) * S * d * d);
+    if (sxx && o->kind == ORC_NIW) memcpy(sxx, o->sxx, sizeof(double) * S * d * d);
 }
 
 void orc_get_params(const orc_state* o, double* logw, double* mu, double* W, double* logdetW, double* logtheta)
@@ -731,7 +741,7 @@ void orc_get_params(const orc_state* o, double* logw, double* mu, double* W, dou
     int d = o->d, S = 3 * o->K;
     if (logw) memcpy(logw, o->logw, sizeof(double) * S);
     if (mu) memcpy(mu, o->mu, sizeof(double) * S * d);
-    if (W) memcpy(W, o->W, sizeof(double) * S * d * d);
+    if (W && o->kind == ORC_NIW) memcpy(W, o->W, sizeof(double) * S * d * d);
     if (logdetW) memcpy(logdetW, o->logdetW, sizeof(double) * S);
     if (logtheta) memcpy(logtheta, o->logtheta, sizeof(double) * S * d);
 }

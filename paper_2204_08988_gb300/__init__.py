@@ -33,7 +33,7 @@ EXPORTS = [
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
     "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
     "dpmm_sweep_batch", "dpmm_check_wait_timeout", "dpmm_checkpoint_size", "dpmm_save_checkpoint",
-    "dpmm_load_checkpoint",
+    "dpmm_load_checkpoint", "dpmm_set_data_csr",
 ]
 
 
@@ -89,6 +89,7 @@ def load():
             "dpmm_checkpoint_size": ([vp, C.POINTER(C.c_size_t)], i32),
             "dpmm_save_checkpoint": ([vp, vp, C.c_size_t], i32),
             "dpmm_load_checkpoint": ([vp, vp, C.c_size_t], i32),
+            "dpmm_set_data_csr": ([vp, vp, vp, vp, i64], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -142,6 +143,14 @@ def _array_arg(X):
 def dpmm_set_data(h, X):
     ptr, code, dev = _array_arg(X)
     _check(h, load().dpmm_set_data(h, ptr, int(X.shape[0]), code, dev))
+
+
+def dpmm_set_data_csr(h, indptr, indices, counts):
+    """Compressed rows (host arrays): indptr int64[N + 1], indices int32[nnz], counts int32[nnz]."""
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    ct = np.ascontiguousarray(counts, dtype=np.int32)
+    _check(h, load().dpmm_set_data_csr(h, _p(ip), _p(ix), _p(ct), int(ip.size - 1)))
 
 
 def dpmm_update_data(h, X):
@@ -332,6 +341,10 @@ class DPMM:
 
     def update_data(self, X):
         dpmm_update_data(self.h, X)
+
+    def set_data_csr(self, indptr, indices, counts):
+        dpmm_set_data_csr(self.h, indptr, indices, counts)
+        self.N = int(len(indptr) - 1)
 
     def sweep(self, iters, seed):
         dpmm_sweep(self.h, iters, seed)

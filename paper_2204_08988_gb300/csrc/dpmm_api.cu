@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -220,13 +221,93 @@ static dpmm_status check_derr(dpmm_ctx* c) {
 
 static void free_data(dpmm_ctx* c) {
     dfree(c->X); dfree(c->z); dfree(c->zbar); dfree(c->idx); dfree(c->hist); dfree(c->x3_ximg); dfree(c->tc_carry);
+    dfree(c->csr_ptr); dfree(c->csr_idx); dfree(c->csr_val);
     c->X = nullptr; c->z = nullptr; c->zbar = nullptr; c->idx = nullptr; c->hist = nullptr; c->x3_ximg = nullptr;
-    c->tc_carry = nullptr;
+    c->tc_carry = nullptr; c->csr_ptr = nullptr; c->csr_idx = nullptr; c->csr_val = nullptr; c->nnz = 0;
 }
 
 static void drop_graph(dpmm_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+}
+
+// ------------------------------------------------------------------ compressed rows
+// what every data set of the compressed-row path has in common: labels, the row
+// pointer, the prior in storage coordinates (beta), the sweep counter reset
+static dpmm_status sparse_alloc(dpmm_ctx* c, int64_t N) {
+    free_data(c);
+    c->N = N;
+    c->T_tiles = (int)((N + 255) / 256);
+    c->Gr = 1;
+    bool ok = true;
+    auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
+    A(&c->X, 16);  // no dense copy: a marker that data are set
+    A(&c->z, sizeof(int32_t) * N);
+    A(&c->zbar, N);
+    A(&c->csr_ptr, sizeof(int64_t) * (N + 1));
+    if (!ok) {
+        cudaGetLastError();
+        free_data(c);
+        return fail(c, DPMM_ENOMEM, "device allocation for the data failed");
+    }
+    CK(c, cudaDeviceSynchronize());  // the zeroing memsets ran on the legacy stream
+    return DPMM_OK;
+}
+
+static dpmm_status sparse_finish(dpmm_ctx* c) {
+    const int d = c->d;
+    std::vector<double> cen((size_t)2 * d + (size_t)d * d, 0.0);
+    for (int j = 0; j < d; ++j) cen[d + j] = c->beta[j];
+    c->h_center.assign(d, 0.0);
+    CK(c, cudaMemcpyAsync(c->center, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice, c->stream));
+    uint32_t zero = 0;
+    CK(c, cudaMemcpyAsync(c->diter, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->initialized = false;
+    c->h_iter = 0;
+    return DPMM_OK;
+}
+
+// dense counts (host or device) -> compressed rows on the device
+static dpmm_status sparse_upload(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_device) {
+    const size_t bytes = (size_t)c->N * c->d * dt_size(dt);
+    const void* src = X;
+    void* tmp = nullptr;
+    if (!on_device) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, X) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+            src = at.devicePointer;
+        } else {
+            cudaGetLastError();
+            CK(c, cudaMallocAsync(&tmp, bytes, c->stream));
+            CK(c, cudaMemcpyAsync(tmp, X, bytes, cudaMemcpyHostToDevice, c->stream));
+            src = tmp;
+        }
+    }
+    int* bad = nullptr;
+    CK(c, cudaMallocAsync((void**)&bad, sizeof(int), c->stream));
+    CK(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    cudaError_t e = sparse_build_dense(c, src, dt, bad);
+    int hb = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (tmp) cudaFreeAsync(tmp, c->stream);
+    cudaFreeAsync(bad, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    CK(c, e);
+    if (hb) return fail(c, DPMM_EINVAL, "multinomial data must be non-negative integer counts below 2^24");
+    return DPMM_OK;
+}
+
+static dpmm_status set_data_sparse(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, int on_device) {
+    dpmm_status s = sparse_alloc(c, N);
+    if (s != DPMM_OK) return s;
+    c->in_dt = dt;
+    s = sparse_upload(c, X, dt, on_device);
+    if (s != DPMM_OK) {
+        free_data(c);
+        return s;
+    }
+    return sparse_finish(c);
 }
 
 // ------------------------------------------------------------------ ABI
@@ -249,7 +330,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
                 if (prior->psi0[i * d + j] != prior->psi0[j * d + i]) return DPMM_EINVAL;
         if (!host_logdet_spd(prior->psi0, d, &ld0)) return DPMM_EINVAL;
     } else if (prior->kind == DPMM_PRIOR_DIRICHLET) {
-        if (!prior->beta) return DPMM_EINVAL;
+        if (!prior->beta || d > DIRICHLET_MAX_D) return DPMM_EINVAL;
         for (int j = 0; j < d; ++j)
             if (!(prior->beta[j] > 0.0)) return DPMM_EINVAL;
     } else {
@@ -279,7 +360,10 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         c->beta.assign(prior->beta, prior->beta + d);
     }
     c->st.init(d, c->kind == DPMM_PRIOR_NIW ? STAT_FULL : STAT_FIRST);
-    if (c->st.nblk > 1024) {
+    c->sparse = sparse_path(c);
+    // the dense statistics kernels' limit; the compressed-row label kernel scores up to
+    // 256 clusters (eight per lane)
+    if ((!c->sparse && c->st.nblk > 1024) || (c->sparse && K_max > 256)) {
         delete c;
         return DPMM_EINVAL;
     }
@@ -298,12 +382,12 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     A(&c->shift32, sizeof(float) * K_max * d);
     A(&c->p_logw, sizeof(double) * S);
     A(&c->p_mu, sizeof(double) * S * d);
-    A(&c->p_W, sizeof(double) * S * d * d);
+    if (c->kind == DPMM_PRIOR_NIW) A(&c->p_W, sizeof(double) * S * d * d);
     A(&c->p_logdetW, sizeof(double) * S);
     A(&c->p_c, sizeof(double) * S);
     A(&c->p_logtheta, sizeof(double) * S * d);
     A(&c->q_mu, sizeof(float) * S * d);
-    A(&c->q_W, sizeof(float) * S * d * d);
+    if (c->kind == DPMM_PRIOR_NIW) A(&c->q_W, sizeof(float) * S * d * d);
     A(&c->q_c, sizeof(float) * S);
     A(&c->q_b, sizeof(float) * S * d);
     A(&c->q_logtheta, sizeof(float) * S * d);
@@ -313,13 +397,37 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     A(&c->lgs, sizeof(double) * (S + 1));
     A(&c->retry, sizeof(int) * S);
     A(&c->tot, sizeof(int) * (K_max + 1));
-    c->records_bytes = sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
+    // range records of the dense statistics kernels (the compressed-row path adds its
+    // counts straight into the table)
+    c->records_bytes = c->sparse ? 0 : sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
     A(&c->records, c->records_bytes);
+    if (c->sparse) {
+        const size_t ks = (size_t)(K_max + 31) / 32 * 32;
+        A(&c->sp_cc, sizeof(float) * 2 * (size_t)K_max * d);
+        A(&c->sp_ltT, sizeof(double) * ks * d);
+        A(&c->sp_ct, sizeof(double) * K_max);
+        A(&c->sp_lgb, sizeof(double) * d);
+        bool uniform = true;
+        for (int j = 1; j < d; ++j) uniform = uniform && prior->beta[j] == prior->beta[0];
+        if (uniform) A(&c->sp_lgt, sizeof(double) * SP_LGT);
+        if (ok) {  // lgamma terms of the Dirichlet-multinomial marginal, from the host's libm
+            std::vector<double> lgb(d);
+            for (int j = 0; j < d; ++j) lgb[j] = std::lgamma(prior->beta[j]);
+            ok = cudaMemcpy(c->sp_lgb, lgb.data(), sizeof(double) * d, cudaMemcpyHostToDevice) == cudaSuccess;
+            if (ok && uniform) {
+                std::vector<double> t(SP_LGT);
+                const double b = prior->beta[0];
+                for (int q = 0; q < SP_LGT; ++q) t[q] = std::lgamma(b + q) - std::lgamma(b);
+                ok = cudaMemcpy(c->sp_lgt, t.data(), sizeof(double) * SP_LGT, cudaMemcpyHostToDevice) == cudaSuccess;
+            }
+        }
+    }
     A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1 + 6 * (size_t)K_max));
     A(&c->relabel, sizeof(int) * 4 * K_max);
     A(&c->acc, sizeof(int) * ((size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
     A(&c->center, sizeof(double) * (2 * (size_t)d + (size_t)d * d));
     if (!ok) {
+        cudaGetLastError();  // the failed allocation's error is not left for a later call to report
         dpmm_destroy(c);
         return DPMM_ENOMEM;
     }
@@ -346,7 +454,8 @@ void dpmm_destroy(dpmm_ctx* c) {
     void* ps[] = {c->dK, c->diter, c->age, c->counters, c->derr, c->stats, c->shift_new, c->shift_stats,
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
-                  c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg};
+                  c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg,
+                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
@@ -397,6 +506,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
         c->xs = (d + 3) / 4 * 4;
         if (c->prec == DPMM_PREC_TF32 && c->xs < 32) c->xs = 32;  // one 128-byte TMA box per row
     }
+    if (c->sparse) return set_data_sparse(c, X, N, dt, on_device);
     const size_t esz = c->xdt == 0 ? 8 : (c->xdt == 1 ? 4 : 2);
     c->T_tiles = (int)((N + 255) / 256);
     // ranges of the statistics step: about one per 512 points, at most 2 x SMs (the CUDA-core
@@ -412,6 +522,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     A(&c->hist, sizeof(int) * (size_t)c->K_max * c->T_tiles);
     if (const size_t cb = tc_carry_bytes(c)) A(&c->tc_carry, cb);
     if (!ok) {
+        cudaGetLastError();  // the failed allocation's error is not left for a later call to report
         free_data(c);
         return fail(c, DPMM_ENOMEM, "device allocation for the data failed");
     }
@@ -446,7 +557,47 @@ dpmm_status dpmm_update_data(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_d
     if (!c) return DPMM_EINVAL;
     if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
     if (!X || dt != c->in_dt) return fail(c, DPMM_EINVAL, "same dtype as dpmm_set_data required");
+    if (c->sparse) {  // new compressed rows (their length changes): the captured sweep refers to the old ones
+        drop_graph(c);
+        return sparse_upload(c, X, dt, on_device);
+    }
     return upload(c, X, dt, on_device, false);
+}
+
+dpmm_status dpmm_set_data_csr(dpmm_ctx* c, const int64_t* indptr, const int32_t* indices, const int32_t* counts,
+                              int64_t N) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->sparse) return fail(c, DPMM_EINVAL, "compressed rows are taken for multinomial data of more than 256 categories");
+    drop_graph(c);
+    if (!indptr || N < 1 || N > 0x7FFFFFFFLL || indptr[0] != 0) return fail(c, DPMM_EINVAL, "need 1 <= N < 2^31 and indptr[0] = 0");
+    const int64_t nnz = indptr[N];
+    if (nnz < 0 || (nnz > 0 && (!indices || !counts))) return fail(c, DPMM_EINVAL, "bad indptr or NULL arrays");
+    for (int64_t i = 0; i < N; ++i) {
+        if (indptr[i + 1] < indptr[i]) return fail(c, DPMM_EINVAL, "indptr must be non-decreasing");
+        for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+            if (indices[p] < 0 || indices[p] >= c->d || (p > indptr[i] && indices[p] <= indices[p - 1]))
+                return fail(c, DPMM_EINVAL, "indices must be in [0, d) and increasing within each row");
+            if (counts[p] < 0 || counts[p] >= (1 << 24)) return fail(c, DPMM_EINVAL, "counts must be in [0, 2^24)");
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    dpmm_status s = sparse_alloc(c, N);
+    if (s != DPMM_OK) return s;
+    c->in_dt = DPMM_I32;
+    c->nnz = nnz;
+    bool ok = dalloc(&c->csr_idx, sizeof(int) * std::max<int64_t>(nnz, 1)) == cudaSuccess &&
+              dalloc(&c->csr_val, sizeof(int) * std::max<int64_t>(nnz, 1)) == cudaSuccess;
+    if (!ok) {
+        free_data(c);
+        return fail(c, DPMM_ENOMEM, "device allocation for the data failed");
+    }
+    CK(c, cudaDeviceSynchronize());
+    CK(c, cudaMemcpyAsync(c->csr_ptr, indptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, c->stream));
+    if (nnz > 0) {
+        CK(c, cudaMemcpyAsync(c->csr_idx, indices, sizeof(int) * nnz, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->csr_val, counts, sizeof(int) * nnz, cudaMemcpyHostToDevice, c->stream));
+    }
+    return sparse_finish(c);
 }
 
 static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
@@ -456,9 +607,13 @@ static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
     CK(c, cudaMemsetAsync(c->shift_new, 0, sizeof(double) * c->K_max * c->d, c->stream));
     CK(c, cudaMemsetAsync(c->shift32, 0, sizeof(float) * c->K_max * c->d, c->stream));
     CK(c, launch_init_labels(c, seed));
-    CK(c, launch_sort(c));
-    CK(c, launch_substats(c, seed, 0));
-    CK(c, launch_combine(c));
+    if (c->sparse) {
+        CK(c, launch_sparse(c, seed, 2, nullptr));
+    } else {
+        CK(c, launch_sort(c));
+        CK(c, launch_substats(c, seed, 0));
+        CK(c, launch_combine(c));
+    }
     // clusters left empty by the initial draw are removed (no ages, no sweep index change)
     CK(c, launch_splitmerge(c, seed, 2, 0));
     CK(c, launch_relabel(c, seed));
@@ -476,7 +631,9 @@ static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
         if ((e = launch_params(c, seed)) != cudaSuccess) return e;
         if ((e = launch_derive(c)) != cudaSuccess) return e;
     }
-    if (c->step_mask & 2u) {
+    if ((c->step_mask & 2u) && c->sparse) {
+        if ((e = launch_sparse(c, seed, 0, nullptr)) != cudaSuccess) return e;
+    } else if (c->step_mask & 2u) {
         e = x3 ? launch_labels_x3(c, seed) : tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed);
         if (e != cudaSuccess) return e;
         if ((e = launch_sort(c)) != cudaSuccess) return e;
@@ -649,6 +806,9 @@ dpmm_status dpmm_load_checkpoint(dpmm_ctx* c, const void* buf, size_t bytes) {
             return st;
         }
     }
+    // the compressed-row path's compact counts are not in the checkpoint: recount them from
+    // the labels (integer sums: the same table)
+    if (c->sparse) CK(c, launch_sparse(c, 0, 2, nullptr));
     CK(c, cudaStreamSynchronize(c->stream));
     c->initialized = true;
     c->h_iter = h.iter;
@@ -767,9 +927,13 @@ dpmm_status dpmm_set_state(dpmm_ctx* c, int K, const int32_t* z, const uint8_t* 
     CK(c, cudaMemsetAsync(c->age, 0, sizeof(int) * c->K_max, c->stream));
     CK(c, cudaMemsetAsync(c->shift_new, 0, sizeof(double) * c->K_max * c->d, c->stream));
     CK(c, cudaMemsetAsync(c->shift32, 0, sizeof(float) * c->K_max * c->d, c->stream));
-    CK(c, launch_sort(c));
-    CK(c, launch_substats(c, 0, 0));
-    CK(c, launch_combine(c));
+    if (c->sparse) {
+        CK(c, launch_sparse(c, 0, 2, nullptr));
+    } else {
+        CK(c, launch_sort(c));
+        CK(c, launch_substats(c, 0, 0));
+        CK(c, launch_combine(c));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     c->initialized = true;
     return check_derr(c);
@@ -823,6 +987,7 @@ dpmm_status dpmm_set_params(dpmm_ctx* c, int K, const double* logw, const double
 
 dpmm_status dpmm_get_params(dpmm_ctx* c, double* logw, double* mu, double* W, double* logdetW, double* logtheta) {
     if (!c) return DPMM_EINVAL;
+    if (c->kind != DPMM_PRIOR_NIW && (mu || W || logdetW)) return fail(c, DPMM_EINVAL, "Gaussian parameters of a multinomial chain");
     int K = 0;
     CK(c, cudaMemcpyAsync(&K, c->dK, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -854,7 +1019,8 @@ dpmm_status dpmm_label_scores(dpmm_ctx* c, double* scores) {
     CK(c, cudaMalloc(&zkeep, sizeof(int32_t) * c->N));
     CK(c, cudaMemcpyAsync(zkeep, c->z, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->stream));
     const bool tc = c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16;
-    cudaError_t e = c->prec == DPMM_PREC_BF16X3 ? launch_labels_x3(c, c->seed)
+    cudaError_t e = c->sparse                   ? launch_sparse(c, c->seed, 3, nullptr)
+                    : c->prec == DPMM_PREC_BF16X3 ? launch_labels_x3(c, c->seed)
                     : tc                        ? launch_labels_tc(c, c->seed)
                                                 : launch_labels_simt(c, c->seed);
     CK(c, e);

@@ -34,6 +34,11 @@ enum : uint32_t {
 constexpr double GUMBEL_MAX_F64 = 37.5;
 constexpr float GUMBEL_MAX_F32 = 17.5f;
 
+// multinomial data with more categories than this are held as compressed rows
+constexpr int SPARSE_MIN_D = 256;
+constexpr int DIRICHLET_MAX_D = 65536;
+constexpr int SP_LGT = 1 << 16;  // entries of the lgamma-difference table (counts below it)
+
 __host__ __device__ inline void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                        uint32_t k1, uint32_t out[4]) {
 #pragma unroll
@@ -82,6 +87,41 @@ __device__ inline double d_normal(const Key& k, uint32_t c0, uint32_t tag, uint3
     double r = sqrt(-2.0 * log(u1));
     // sin / cos of 2 pi u2 as sinpi / cospi of 2 u2: no argument reduction by pi
     return (q & 1) ? r * sinpi(2.0 * u2) : r * cospi(2.0 * u2);
+}
+
+__device__ inline float f_normal(const Key& k, uint32_t c0, uint32_t tag, uint32_t base, uint32_t q) {
+    uint32_t w[4];
+    k.block(c0, tag, base + q / 2, w);
+    const float u1 = u01_f32(w[0]), u2 = u01_f32(w[2]);
+    const float r = sqrtf(-2.f * logf(u1));
+    return (q & 1) ? r * sinpif(2.f * u2) : r * cospif(2.f * u2);
+}
+
+// The FP32 form of d_log_gamma below (same Philox blocks, FP32 uniforms from the leading
+// bits of the same words), for the reduced-precision path of high-dimensional
+// multinomial data, whose FP64 draws would cost milliseconds per sweep on GB300's narrow
+// FP64 pipes.  An accept/reject decision within FP32 rounding of its bound can differ
+// from the FP64 one; the variate is then another draw from the same distribution.
+__device__ inline float f_log_gamma(const Key& k, uint32_t c0, uint32_t tag, uint32_t base, float a) {
+    float boost = 0.f;
+    if (a < 1.f) {
+        uint32_t w[4];
+        k.block(c0, tag, base + 63, w);
+        boost = logf(u01_f32(w[0])) / a;
+        a += 1.f;
+    }
+    const float dd = a - 1.f / 3.f, c = rsqrtf(9.f * dd);
+    for (uint32_t r = 0; r < 31; ++r) {
+        const float x = f_normal(k, c0, tag, base + 2 * r, 0);
+        float v = 1.f + c * x;
+        if (v <= 0.f) continue;
+        v = v * v * v;
+        uint32_t w[4];
+        k.block(c0, tag, base + 2 * r + 1, w);
+        const float u = u01_f32(w[0]);
+        if (logf(u) < 0.5f * x * x + dd - dd * v + dd * logf(v)) return logf(dd) + logf(v) + boost;
+    }
+    return logf(dd) + boost;
 }
 
 // log of a Gamma(a, 1) variate (Marsaglia & Tsang, ACM TOMS 2000), log space.
@@ -239,6 +279,18 @@ struct dpmm_ctx {
     // tensor-core path
     int* tc_flag = nullptr;        // device: 1 when K did not fit the tensor-core kernel
     void* tc_carry = nullptr;      // device: per-point state between cluster groups (TF32), N x 20 B
+
+    // multinomial data of more than SPARSE_MIN_D categories: compressed rows
+    bool sparse = false;
+    int64_t nnz = 0;
+    int64_t* csr_ptr = nullptr;    // N + 1
+    int* csr_idx = nullptr;        // nnz categories, increasing within a row
+    int* csr_val = nullptr;        // nnz counts
+    void* sp_ltT = nullptr;        // d x round_up(K_max, 32) cluster log theta (FP64 or FP32)
+    void* sp_ct = nullptr;         // K_max cluster log weights (FP64 or FP32)
+    float* sp_cc = nullptr;        // 2 K_max x d compact sub-cluster counts
+    double* sp_lgt = nullptr;      // lgamma(beta + c) - lgamma(beta), c < SP_LGT (uniform beta)
+    double* sp_lgb = nullptr;      // lgamma(beta_j)
     double* dbg_scores = nullptr;  // device N x K scores when the score hook is active
 
     // one sweep captured as a CUDA graph (kernels read K and the sweep index from
@@ -280,6 +332,10 @@ cudaError_t x3_prepare_data(dpmm_ctx* c);
 cudaError_t x3_prepare(dpmm_ctx* c);
 cudaError_t launch_labels_x3(dpmm_ctx* c, uint64_t seed);
 cudaError_t launch_wait_selftest(dpmm_ctx* c);
+bool sparse_path(const dpmm_ctx* c);
+cudaError_t sparse_build_dense(dpmm_ctx* c, const void* X, dpmm_dtype dt, int* bad);
+cudaError_t sparse_prepare(dpmm_ctx* c);
+cudaError_t launch_sparse(dpmm_ctx* c, uint64_t seed, int mode, const int* gate);
 
 // profiling helpers (no-ops unless enabled)
 void prof_begin(dpmm_ctx* c, const char* name);

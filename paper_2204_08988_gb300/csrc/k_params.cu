@@ -326,9 +326,11 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     }
 }
 
-// theta ~ Dir(beta + counts), as log theta (log-space Gamma draws).
+// theta ~ Dir(beta + counts), as log theta (log-space Gamma draws).  cc (compressed-row
+// path only): the compact sub-cluster counts, read instead of the statistics table.
 __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const int* dK, const uint32_t* diter,
-                                        uint64_t seed, const double* logw, double* p_logtheta, double* p_c) {
+                                        uint64_t seed, const double* logw, double* p_logtheta, double* p_c,
+                                        const float* cc) {
     __shared__ double sh[32];
     const int d = sv.L.d;
     const int K = *dK;
@@ -339,7 +341,10 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
     double* lt = p_logtheta + (size_t)s * d;
     double mx = -INFINITY;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double v = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, beta[j] + sv.m(k, h, j, d));
+        const double cnt = cc ? (h < 0 ? (double)cc[(size_t)(2 * k) * d + j] + (double)cc[(size_t)(2 * k + 1) * d + j]
+                                       : (double)cc[(size_t)(2 * k + h) * d + j])
+                              : sv.m(k, h, j, d);
+        double v = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, beta[j] + cnt);
         lt[j] = v;
         mx = fmax(mx, v);
     }
@@ -348,6 +353,39 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
     for (int j = threadIdx.x; j < d; j += blockDim.x) sum += exp(lt[j] - mx);
     double lse = mx + log(block_reduce_sum(sum, sh));
     for (int j = threadIdx.x; j < d; j += blockDim.x) lt[j] -= lse;
+    if (threadIdx.x == 0) p_c[s] = logw[s];
+}
+
+// The same draw in FP32 (reduced-precision path of compressed-row data): f_log_gamma,
+// FP32 normalisation; log theta stored in the FP64 table and its FP32 mirror.
+__global__ void dirichlet_params_f32_kernel(int d, const double* beta, const int* dK, const uint32_t* diter,
+                                            uint64_t seed, const double* logw, const float* cc, double* p_logtheta,
+                                            float* q_logtheta, double* p_c) {
+    __shared__ double sh[32];
+    const int K = *dK;
+    const int s = blockIdx.x;
+    if (s >= 3 * K) return;
+    const int k = s / 3, h = s % 3 - 1;
+    Key key{seed, diter[0], diter[1]};
+    float* qt = q_logtheta + (size_t)s * d;
+    float mx = -INFINITY;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float cnt = h < 0 ? cc[(size_t)(2 * k) * d + j] + cc[(size_t)(2 * k + 1) * d + j]
+                                : cc[(size_t)(2 * k + h) * d + j];
+        const float v = f_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, (float)beta[j] + cnt);
+        qt[j] = v;
+        mx = fmaxf(mx, v);
+    }
+    mx = (float)block_reduce_max((double)mx, sh);
+    float sum = 0.f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sum += __expf(qt[j] - mx);
+    const float lse = mx + logf((float)block_reduce_sum((double)sum, sh));
+    double* lt = p_logtheta + (size_t)s * d;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float v = qt[j] - lse;
+        qt[j] = v;
+        lt[j] = (double)v;
+    }
     if (threadIdx.x == 0) p_c[s] = logw[s];
 }
 
@@ -441,8 +479,14 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         c->nlaunch += 1;
     } else {
         prof_begin(c, "dirichlet_params");
-        dirichlet_params_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(make_sv(c), c->center + c->d, c->dK, c->diter,
-                                                                     seed, c->p_logw, c->p_logtheta, c->p_c);
+        if (c->sparse && c->prec != DPMM_PREC_FP64_PLAIN)
+            dirichlet_params_f32_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(
+                c->d, c->center + c->d, c->dK, c->diter, seed, c->p_logw, c->sp_cc, c->p_logtheta, c->q_logtheta,
+                c->p_c);
+        else
+            dirichlet_params_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(make_sv(c), c->center + c->d, c->dK,
+                                                                         c->diter, seed, c->p_logw, c->p_logtheta,
+                                                                         c->p_c, c->sparse ? c->sp_cc : nullptr);
         prof_end(c, "dirichlet_params");
         c->nlaunch += 1;
     }
@@ -457,6 +501,7 @@ cudaError_t launch_derive(dpmm_ctx* c) {
     prof_end(c, "derive");
     c->nlaunch += 1;
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c->sparse) e = sparse_prepare(c);
     if (e == cudaSuccess && tc_supported(c)) e = tc_prepare(c);
     if (e == cudaSuccess && substats_tc_supported(c)) e = substats_tc_prepare(c);
     if (e == cudaSuccess && x3_supported(c)) e = x3_prepare(c);

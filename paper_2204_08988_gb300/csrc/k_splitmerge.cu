@@ -188,6 +188,67 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     }
 }
 
+// The Dirichlet-multinomial log marginals of compressed-row data (many categories):
+// the counts come from the compact sub-cluster count table, and only categories with a
+// nonzero count contribute (for c = 0, lgamma(beta_j + c) - lgamma(beta_j) = 0).  The term
+// for count c is read from a table of lgamma(beta + c) - lgamma(beta) made on the host when
+// every beta_j is equal and c is below its length, and computed otherwise.  Same outputs
+// as marginal_kernel (Ltab), one CTA per cluster, sub-cluster and pair.
+__global__ void marginal_sparse_kernel(SMArgs a, const float* cc, const double* lgt, int nlgt, const double* lgb,
+                                       double* Ltab) {
+    __shared__ double shc[32], sha[32];
+    const int K = *a.dK;
+    const int e = blockIdx.x;
+    const int npairs = K * (K - 1) / 2;
+    if (e >= 3 * K + npairs) return;
+    const int d = a.L.d, tid = threadIdx.x, nt = blockDim.x;
+    int k1, k2, h;
+    if (e < 3 * K) {
+        k1 = e / 3;
+        k2 = -1;
+        h = e % 3 - 1;
+    } else {
+        pair_of(e - 3 * K, K, k1, k2);
+        h = -1;
+    }
+    double* out = Ltab + (e < 3 * K ? e : 3 * a.K_max + (e - 3 * K));
+    if (e < 3 * K && (tid == 32 || tid == 33)) {  // the slot's lgamma terms for the Hastings ratios
+        const double ns = smv(a, k1, h, d, d);
+        Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
+    }
+    const float* a0 = cc + (size_t)(2 * k1 + (h < 0 ? 0 : h)) * d;
+    const float* a1 = h < 0 ? cc + (size_t)(2 * k1 + 1) * d : nullptr;
+    const float* b0 = k2 >= 0 ? cc + (size_t)(2 * k2) * d : nullptr;
+    const float* b1 = k2 >= 0 ? cc + (size_t)(2 * k2 + 1) * d : nullptr;
+    double sc = 0.0, acc = 0.0;
+    for (int j = tid; j < d; j += nt) {
+        float c = a0[j];
+        if (a1) c += a1[j];
+        if (b0) c += b0[j] + b1[j];  // integers below 2^24: exact
+        if (c > 0.f) {
+            sc += (double)c;
+            acc += (lgt && c < (float)nlgt) ? lgt[(int)c] : lgamma(a.beta[j] + (double)c) - lgb[j];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    }
+    if ((tid & 31) == 0) {
+        shc[tid >> 5] = sc;
+        sha[tid >> 5] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double c = 0.0, l = 0.0;
+        for (int w = 0; w < (nt + 31) / 32; ++w) {  // fixed order
+            c += shc[w];
+            l += sha[w];
+        }
+        *out = l + a.lg_sum_beta - lgamma(a.sum_beta + c);
+    }
+}
+
 // Every split and merge ratio with its Philox uniform, in parallel: acc[k] for the
 // split of cluster k, acc[K_max + p] for merge pair p; 1 = accepted if proposed.
 // Indices in the Philox counters are those after removing emptied clusters.
@@ -492,7 +553,11 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
             if (e != cudaSuccess) return e;
         }
         prof_begin(c, "marginal");
-        marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);
+        if (c->sparse)
+            marginal_sparse_kernel<<<items, 256, 0, c->stream>>>(s, c->sp_cc, c->sp_lgt, c->sp_lgt ? SP_LGT : 0,
+                                                                c->sp_lgb, c->Ltab);
+        else
+            marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);
         prof_end(c, "marginal");
         c->nlaunch += 1;
     }

@@ -1321,6 +1321,7 @@ cudaError_t launch_combine(dpmm_ctx* c) {
 
 // statistics recomputed from the labels, only when the split/merge step changed them
 cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate) {
+    if (c->sparse) return launch_sparse(c, 0, 2, gate);
     cudaError_t e = sort_impl(c, gate);
     if (e == cudaSuccess) e = substats_dispatch(c, 0, 0, gate);
     if (e == cudaSuccess) {

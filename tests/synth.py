@@ -16,6 +16,8 @@ Workloads (sizes as the benchmark uses them):
   batched    : 512 independent mixtures, N log-uniform on [1e3, 1e6] (about 7.4e7
                points in all), d drawn from {2, 8, 32, 64}, true K uniform on {2..30},
                generated as gauss_d32; FP32 (batch_problems).
+  newsgroups : d=20,000 word counts of N=11,314 documents from 20 topics, lengths
+               log-uniform on [30, 600] words (newsgroups_like), compressed rows.
 """
 from __future__ import annotations
 
@@ -75,6 +77,41 @@ def multinomial_mixture(N, d, K, draws, seed, topic_conc=0.1):
         if idx.size:
             X[idx] = rng.multinomial(draws, theta[k], size=idx.size)
     return X, labels.astype(np.int32)
+
+
+def newsgroups_like(N=11_314, d=20_000, K=20, seed=1006, topic_conc=0.05, len_lo=30, len_hi=600):
+    """Count vectors shaped like the 20newsgroups bag-of-words data of Sec. 5.3 (N = 11,314
+    documents, a 20,000-word vocabulary, 20 groups), synthetic: topics ~ Dir(topic_conc 1_d),
+    mixture weights Dir(1), document lengths log-uniform on [len_lo, len_hi] words, each
+    word drawn from the document's topic.  Returns compressed rows (indptr int64[N + 1],
+    indices int32[nnz] increasing within a row, counts int32[nnz]) and the labels."""
+    rng = np.random.default_rng(seed)
+    theta = rng.dirichlet(np.full(d, topic_conc), size=K)
+    w = rng.dirichlet(np.ones(K))
+    labels = rng.choice(K, size=N, p=w).astype(np.int32)
+    lengths = np.exp(rng.uniform(np.log(len_lo), np.log(len_hi), N)).astype(np.int64)
+    rows = [None] * N
+    for k in range(K):
+        docs = np.nonzero(labels == k)[0]
+        if docs.size == 0:
+            continue
+        words = rng.choice(d, size=int(lengths[docs].sum()), p=theta[k])
+        cut = np.cumsum(lengths[docs])[:-1]
+        for i, ws in zip(docs, np.split(words, cut)):
+            rows[i] = np.unique(ws, return_counts=True)
+    indptr = np.zeros(N + 1, np.int64)
+    indptr[1:] = np.cumsum([r[0].size for r in rows])
+    indices = np.concatenate([r[0] for r in rows]).astype(np.int32)
+    counts = np.concatenate([r[1] for r in rows]).astype(np.int32)
+    return indptr, indices, counts, labels
+
+
+def csr_to_dense(indptr, indices, counts, d, dtype=np.int32):
+    N = indptr.size - 1
+    X = np.zeros((N, d), dtype=dtype)
+    rows = np.repeat(np.arange(N), np.diff(indptr))
+    X[rows, indices] = counts
+    return X
 
 
 def workload(name, N=None, seed=None):

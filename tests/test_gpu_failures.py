@@ -75,9 +75,18 @@ def test_nan_data_reported_as_numeric_error(prec):
 
 
 def test_impossible_allocation_is_enomem():
-    # 4092 categories (the largest multinomial dimension) and 1000 clusters: the parameter
-    # tables would need more than 400 GB
-    d = 4092
-    with pytest.raises(P.DPMMError) as e:
-        P.dpmm_create(P.PRIOR_DIRICHLET, d, 1000, 1.0, beta=np.ones(d))
-    assert e.value.status == P.DPMM_ENOMEM, (e.value.status, str(e.value))
+    # N = 2^31 - 1 points of dimension 32 in FP64 need 550 GB of device memory: the
+    # allocation fails before the input is read (the host buffer passed is one row)
+    import ctypes as C
+
+    d = 32
+    g = P.DPMM(0, d, 4, 1.0, prec=P.PREC_FP64_PLAIN, **_prior(d))
+    row = np.zeros(d)
+    st = P.load().dpmm_set_data(g.h, C.c_void_p(row.ctypes.data), (1 << 31) - 1, P.F64, 0)
+    assert st == P.DPMM_ENOMEM, (st, P.dpmm_last_error(g.h))
+    # the context is still usable
+    X = np.random.default_rng(0).standard_normal((500, d))
+    g.set_data(X)
+    g.sweep(1, 1)
+    assert g.labels()[0].shape == (500,)
+    g.close()
