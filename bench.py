@@ -49,7 +49,11 @@ WORKLOADS = {
     "multinomial": dict(K_max=128),
     "gauss_d128": dict(K_max=128),
     "batched": dict(K_max=64),
+    "newsgroups": dict(K_max=64),
 }
+# arithmetic of each workload when --prec is not given
+DEFAULT_PREC = {"gauss_d32": "tf32", "gauss_d2": "fp64", "multinomial": "bf16", "gauss_d128": "bf16x3",
+                "batched": "mixed", "newsgroups": "fp32"}
 
 
 def parse():
@@ -59,7 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gauss_d32", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="tf32", choices=sorted(PREC))
+    ap.add_argument("--prec", default=None, choices=sorted(PREC), help="default: the workload's own (see DEFAULT_PREC)")
     ap.add_argument("--burnin", type=int, default=150)
     ap.add_argument("--n", type=int, default=None, help="override N (smaller cases for profiling)")
     ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
@@ -116,11 +120,34 @@ class Clocks:
 
 
 def load_workload(name, n, seed_offset):
+    """(X, y, prior, options); for the compressed-row workload X is (indptr, indices, counts, d)."""
     import synth
 
+    if name == "newsgroups":
+        ip, ix, ct, y = synth.newsgroups_like(seed=1006 + seed_offset, **({} if n is None else {"N": n}))
+        d = 20_000
+        return (ip, ix, ct, d), y, dict(kind=1, beta=np.ones(d)), dict(alpha=10.0)
     base = {"gauss_d2": 1001, "gauss_d32": 1002, "multinomial": 1003, "gauss_d128": 1004}[name]
     X, y, prior, opt = synth.workload(name, N=n, seed=base + seed_offset)
     return X, y, prior, opt
+
+
+def dense_rows(X, n):
+    """The first n points as a dense FP64 array (the oracle's input)."""
+    if isinstance(X, tuple):
+        import synth
+
+        ip, ix, ct, d = X
+        return synth.csr_to_dense(ip[: n + 1], ix[: ip[n]], ct[: ip[n]], d, dtype=np.float64)
+    return X[:n].astype(np.float64)
+
+
+def n_points(X):
+    return X[0].size - 1 if isinstance(X, tuple) else X.shape[0]
+
+
+def n_dims(X):
+    return X[3] if isinstance(X, tuple) else X.shape[1]
 
 
 def oracle_rate(name, X, y, prior, opt, budget_s=12.0, max_sweeps=4):
@@ -130,16 +157,17 @@ def oracle_rate(name, X, y, prior, opt, budget_s=12.0, max_sweeps=4):
     kind = O.NIW if prior["kind"] == 0 else O.DIRICHLET
     kw = {k: v for k, v in prior.items() if k != "kind"}
     K = int(y.max()) + 1
-    o = O.Oracle(kind, X.shape[1], max(64, K), opt["alpha"], burn_out=15, **kw)
+    N = n_points(X)
+    o = O.Oracle(kind, n_dims(X), max(64, K), opt["alpha"], burn_out=15, **kw)
     # size the sample from a probe so the whole measurement stays ~budget_s
-    n0 = min(len(X), 2000)
-    o.set_data(X[:n0].astype(np.float64))
+    n0 = min(N, 2000)
+    o.set_data(dense_rows(X, n0))
     o.set_state(K, y[:n0] % K, (np.arange(n0) % 2).astype(np.uint8))
     t0 = time.perf_counter()
     o.sweep(1, 1)
     per_pt = (time.perf_counter() - t0) / n0
-    n = int(min(len(X), max(n0, budget_s / max_sweeps / max(per_pt, 1e-9))))
-    o.set_data(X[:n].astype(np.float64))
+    n = int(min(N, max(n0, budget_s / max_sweeps / max(per_pt, 1e-9))))
+    o.set_data(dense_rows(X, n))
     o.set_state(K, y[:n] % K, (np.arange(n) % 2).astype(np.uint8))
     sweeps = 0
     t0 = time.perf_counter()
@@ -162,7 +190,7 @@ def run_reference(a):
         opt = dict(alpha=10.0)
     else:
         X, y, prior, opt = load_workload(a.workload, a.n, 0)
-    N = X.shape[0]
+    N = n_points(X)
     vals = []
     info = None
     steps = max(1, min(a.steps, 3))
@@ -175,7 +203,7 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-sweeps/s", "n_gpus": a.gpus,
            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * N / v, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": a.workload, "N": N, "d": int(X.shape[1]), "sample": sample,
+           "config": {"workload": a.workload, "N": N, "d": int(n_dims(X)), "sample": sample,
                       "ms_per_step": "extrapolated: N / value, the sample's rate applied to all N points"},
            "cpu_baseline": {"value": v, "unit": "point-sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "point-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -342,6 +370,8 @@ def main_batched(a):
 
 def main():
     a = parse()
+    if a.prec is None:
+        a.prec = DEFAULT_PREC[a.workload]
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
@@ -367,17 +397,22 @@ def main():
     _build.build()
 
     X, y, prior, opt = load_workload(a.workload, a.n, rank)
-    N, d = X.shape
+    N, d = n_points(X), n_dims(X)
     kind = prior["kind"]
+    csr = isinstance(X, tuple)
     kw = {k: v for k, v in prior.items() if k != "kind"}
     K_max = WORKLOADS[a.workload]["K_max"]
     stream = torch.cuda.Stream()
     g = P.DPMM(kind, d, K_max, opt["alpha"], prec=PREC[a.prec], init_K=1, burn_out=15,
                stream=stream.cuda_stream, **kw)
-    Xd = torch.from_numpy(X).cuda()
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        g.set_data(Xd)
+    Xd = None
+    if csr:
+        g.set_data_csr(*X[:3])
+    else:
+        Xd = torch.from_numpy(X).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            g.set_data(Xd)
     seed = 0
     if a.init_truth:
         K_true = int(y.max()) + 1
@@ -453,6 +488,11 @@ def main():
                 roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "peak_source": "fp32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz" if a.prec == "fp32"
                         else "fp64: nominal 1.25 TFLOP/s"}
+        elif csr:
+            # compressed rows: 8 B per nonzero (category, count), the row pointer and the labels
+            bytes_ = 8 * int(X[0][-1]) + 8 * (N + 1) + 5 * N
+            roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "peak_source": "measured copy bandwidth"}
         else:
             bytes_ = N * d * (2 if a.prec == "bf16" else 4) + 4 * N
             roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -477,7 +517,7 @@ def main():
             roof["sweep"] = {"flop": sw_flops, "bytes": sw_bytes, "bound_ms": t_bound * 1e3,
                              "achieved": sw_flops / step_s / 1e12, "unit": "TFLOP/s"}
         else:
-            sw_bytes = N * (2.0 * d + 5.0)
+            sw_bytes = (8.0 * int(X[0][-1]) + 13.0 * N) if csr else N * (2.0 * d + 5.0)
             t_bound = sw_bytes / (hbm_peak * 1e9)
             roof["sweep"] = {"bytes": sw_bytes, "bound_ms": t_bound * 1e3, "achieved": sw_bytes / step_s / 1e9,
                              "unit": "GB/s"}
@@ -498,13 +538,16 @@ def main():
     # arms time sweeps at the same number of clusters
     fp64 = None
     est_s = 2.0 * N * d * d * Kavg / 1e12 if kind == 0 else 2.0 * N * d * Kavg / 1e12
-    if a.prec != "fp64" and not a.no_fp64 and world == 1 and est_s < 2.0:
+    if a.prec != "fp64" and not a.no_fp64 and world == 1 and (est_s < 2.0 or csr):
         z_now, zb_now = g.labels()
         K_now = g.K
         g64 = P.DPMM(kind, d, K_max, opt["alpha"], prec=PREC["fp64"], init_K=1, burn_out=15,
                      stream=stream.cuda_stream, **kw)
-        with torch.cuda.stream(stream):
-            g64.set_data(Xd)
+        if csr:
+            g64.set_data_csr(*X[:3])
+        else:
+            with torch.cuda.stream(stream):
+                g64.set_data(Xd)
         g64.set_state(K_now, z_now, zb_now)
         g64.sweep(2, seed)  # warm-up (the second sweep captures the graph)
         ms64, K64 = timed_steps(g64, a.fp64_steps)
@@ -517,7 +560,7 @@ def main():
 
     # end to end through the C ABI: pinned host X in, labels out, every step
     e2e = None
-    if not a.no_e2e:
+    if not a.no_e2e and not csr:
         Xh = torch.from_numpy(X).pin_memory()
         zh = torch.empty(N, dtype=torch.int32).pin_memory()
         zbh = torch.empty(N, dtype=torch.uint8).pin_memory()

@@ -407,6 +407,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         A(&c->sp_ltT, sizeof(double) * ks * d);
         A(&c->sp_ct, sizeof(double) * K_max);
         A(&c->sp_lgb, sizeof(double) * d);
+        A(&c->sp_part, sizeof(float) * 2 * S * ((d + 2047) / 2048));
         bool uniform = true;
         for (int j = 1; j < d; ++j) uniform = uniform && prior->beta[j] == prior->beta[0];
         if (uniform) A(&c->sp_lgt, sizeof(double) * SP_LGT);
@@ -455,7 +456,7 @@ void dpmm_destroy(dpmm_ctx* c) {
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
                   c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg,
-                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb};
+                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);

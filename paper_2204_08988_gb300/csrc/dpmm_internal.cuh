@@ -291,6 +291,7 @@ struct dpmm_ctx {
     float* sp_cc = nullptr;        // 2 K_max x d compact sub-cluster counts
     double* sp_lgt = nullptr;      // lgamma(beta + c) - lgamma(beta), c < SP_LGT (uniform beta)
     double* sp_lgb = nullptr;      // lgamma(beta_j)
+    void* sp_part = nullptr;       // 3 K_max x ceil(d / 2048) (max, sum exp) of the FP32 theta draws
     double* dbg_scores = nullptr;  // device N x K scores when the score hook is active
 
     // one sweep captured as a CUDA graph (kernels read K and the sweep index from

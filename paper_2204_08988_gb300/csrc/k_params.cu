@@ -357,19 +357,24 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
 }
 
 // The same draw in FP32 (reduced-precision path of compressed-row data): f_log_gamma,
-// FP32 normalisation; log theta stored in the FP64 table and its FP32 mirror.
-__global__ void dirichlet_params_f32_kernel(int d, const double* beta, const int* dK, const uint32_t* diter,
-                                            uint64_t seed, const double* logw, const float* cc, double* p_logtheta,
-                                            float* q_logtheta, double* p_c) {
+// FP32 normalisation; log theta stored in the FP64 table and its FP32 mirror.  A slot's
+// d categories (20,000 for document data) are spread over blockIdx.y chunks of
+// DP_CHUNK; the first kernel draws and leaves each chunk's maximum and sum of
+// exp(v - maximum), the second combines a slot's chunks in a fixed order and normalises.
+constexpr int DP_CHUNK = 2048;
+
+__global__ void dirichlet_draw_f32_kernel(int d, const double* beta, const int* dK, const uint32_t* diter,
+                                          uint64_t seed, const float* cc, float* q_logtheta, float2* part) {
     __shared__ double sh[32];
     const int K = *dK;
     const int s = blockIdx.x;
     if (s >= 3 * K) return;
     const int k = s / 3, h = s % 3 - 1;
+    const int j0 = blockIdx.y * DP_CHUNK, j1 = min(d, j0 + DP_CHUNK);
     Key key{seed, diter[0], diter[1]};
     float* qt = q_logtheta + (size_t)s * d;
     float mx = -INFINITY;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const float cnt = h < 0 ? cc[(size_t)(2 * k) * d + j] + cc[(size_t)(2 * k + 1) * d + j]
                                 : cc[(size_t)(2 * k + h) * d + j];
         const float v = f_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, (float)beta[j] + cnt);
@@ -378,15 +383,34 @@ __global__ void dirichlet_params_f32_kernel(int d, const double* beta, const int
     }
     mx = (float)block_reduce_max((double)mx, sh);
     float sum = 0.f;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) sum += __expf(qt[j] - mx);
-    const float lse = mx + logf((float)block_reduce_sum((double)sum, sh));
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) sum += __expf(qt[j] - mx);
+    sum = (float)block_reduce_sum((double)sum, sh);
+    if (threadIdx.x == 0) part[(size_t)s * gridDim.y + blockIdx.y] = make_float2(mx, sum);
+}
+
+__global__ void dirichlet_norm_f32_kernel(int d, const int* dK, const double* logw, const float2* part,
+                                          float* q_logtheta, double* p_logtheta, double* p_c) {
+    const int K = *dK;
+    const int s = blockIdx.x;
+    if (s >= 3 * K) return;
+    const int nc = gridDim.y;
+    float mx = -INFINITY;
+    for (int q = 0; q < nc; ++q) mx = fmaxf(mx, part[(size_t)s * nc + q].x);
+    float sum = 0.f;
+    for (int q = 0; q < nc; ++q) {
+        const float2 p = part[(size_t)s * nc + q];
+        sum += p.y * __expf(p.x - mx);
+    }
+    const float lse = mx + logf(sum);
+    const int j0 = blockIdx.y * DP_CHUNK, j1 = min(d, j0 + DP_CHUNK);
+    float* qt = q_logtheta + (size_t)s * d;
     double* lt = p_logtheta + (size_t)s * d;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const float v = qt[j] - lse;
         qt[j] = v;
         lt[j] = (double)v;
     }
-    if (threadIdx.x == 0) p_c[s] = logw[s];
+    if (blockIdx.y == 0 && threadIdx.x == 0) p_c[s] = logw[s];
 }
 
 // FP32 mirrors of the drawn parameters for the reduced-precision paths, and the
@@ -413,10 +437,11 @@ __global__ void derive_kernel(int kind, int d, int tf32, const int* dK, const do
                 shift32[(size_t)(s / 3) * d + j] = (float)mu[j];
             }
         }
-    } else {
-        for (int j = tid; j < d; j += nt) q_logtheta[(size_t)s * d + j] = (float)p_logtheta[(size_t)s * d + j];
+    } else {  // blockIdx.y: chunks of 4096 categories
+        const int j0 = blockIdx.y * 4096, j1 = min(d, j0 + 4096);
+        for (int j = j0 + tid; j < j1; j += nt) q_logtheta[(size_t)s * d + j] = (float)p_logtheta[(size_t)s * d + j];
     }
-    if (tid == 0) q_c[s] = (float)p_c[s];
+    if (tid == 0 && blockIdx.y == 0) q_c[s] = (float)p_c[s];
 }
 
 static StatView make_sv(dpmm_ctx* c) { return StatView{c->stats, c->st}; }
@@ -479,11 +504,14 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         c->nlaunch += 1;
     } else {
         prof_begin(c, "dirichlet_params");
-        if (c->sparse && c->prec != DPMM_PREC_FP64_PLAIN)
-            dirichlet_params_f32_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(
-                c->d, c->center + c->d, c->dK, c->diter, seed, c->p_logw, c->sp_cc, c->p_logtheta, c->q_logtheta,
-                c->p_c);
-        else
+        if (c->sparse && c->prec != DPMM_PREC_FP64_PLAIN) {
+            const dim3 grid(3 * c->K_max, (c->d + DP_CHUNK - 1) / DP_CHUNK);
+            dirichlet_draw_f32_kernel<<<grid, 256, 0, c->stream>>>(c->d, c->center + c->d, c->dK, c->diter, seed,
+                                                                  c->sp_cc, c->q_logtheta, (float2*)c->sp_part);
+            dirichlet_norm_f32_kernel<<<grid, 256, 0, c->stream>>>(c->d, c->dK, c->p_logw, (const float2*)c->sp_part,
+                                                                  c->q_logtheta, c->p_logtheta, c->p_c);
+            c->nlaunch += 1;
+        } else
             dirichlet_params_kernel<<<3 * c->K_max, 256, 0, c->stream>>>(make_sv(c), c->center + c->d, c->dK,
                                                                          c->diter, seed, c->p_logw, c->p_logtheta,
                                                                          c->p_c, c->sparse ? c->sp_cc : nullptr);
@@ -495,7 +523,8 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
 
 cudaError_t launch_derive(dpmm_ctx* c) {
     prof_begin(c, "derive");
-    derive_kernel<<<3 * c->K_max, 128, 0, c->stream>>>(c->kind, c->d, c->prec == DPMM_PREC_TF32, c->dK, c->p_logw, c->p_mu, c->p_W, c->p_c,
+    const dim3 dgrid(3 * c->K_max, c->kind == DPMM_PRIOR_NIW ? 1 : (c->d + 4095) / 4096);
+    derive_kernel<<<dgrid, 128, 0, c->stream>>>(c->kind, c->d, c->prec == DPMM_PREC_TF32, c->dK, c->p_logw, c->p_mu, c->p_W, c->p_c,
                                                        c->p_logtheta, c->q_mu, c->q_W, c->q_c, c->q_b,
                                                        c->q_logtheta, c->shift_new, c->shift32);
     prof_end(c, "derive");

@@ -200,15 +200,27 @@ __global__ void __launch_bounds__(256) sparse_sweep_kernel(SpArgs<T> a) {
                 const int n = (int)min((int64_t)32, r1 - p0);
                 const int jj = lane < n ? a.idx[p0 + lane] : 0;
                 const T cv = lane < n ? (T)a.val[p0 + lane] : T(0);
-                for (int q = 0; q < n; ++q) {  // increasing category order
-                    const int j = __shfl_sync(0xffffffffu, jj, q);
-                    const T c = __shfl_sync(0xffffffffu, cv, q);
-                    const T* row = a.lt_t + (size_t)j * a.ks;
+                // increasing category order; four nonzeros' table rows are loaded before
+                // they are added, so that their loads overlap
+                for (int q0 = 0; q0 < n; q0 += 4) {
+                    T lv[4][KQ], cq[4];
 #pragma unroll
-                    for (int u = 0; u < KQ; ++u) {
-                        const int k = lane + 32 * u;
-                        if (k < K) acc[u] = madd(acc[u], c, row[k]);
+                    for (int v = 0; v < 4; ++v) {
+                        const int q = q0 + v < n ? q0 + v : n - 1;
+                        const int j = __shfl_sync(0xffffffffu, jj, q);
+                        cq[v] = __shfl_sync(0xffffffffu, cv, q);
+                        const T* row = a.lt_t + (size_t)j * a.ks;
+#pragma unroll
+                        for (int u = 0; u < KQ; ++u) {
+                            const int k = lane + 32 * u;
+                            lv[v][u] = k < K ? row[k] : T(0);
+                        }
                     }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (q0 + v < n)
+#pragma unroll
+                            for (int u = 0; u < KQ; ++u) acc[u] = madd(acc[u], cq[v], lv[v][u]);
                 }
             }
             // scores log pi_k + log f(x_i; theta_k) and the exact Gumbel-max

@@ -459,6 +459,9 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
     }
     __syncthreads();
     const int Kn = s_Knew;
+    // the statistics shifts follow their clusters (Gaussian only: the multinomial
+    // statistics are not shifted, and d x K can be 20,000 x 100 there)
+    if (a.s.kind == DPMM_PRIOR_NIW)
     for (int q = tid; q < Kn * d; q += blockDim.x) {
         int k = q / d, j = q % d;
         double v = a.s.shift_stats[(size_t)src[k] * d + j];
