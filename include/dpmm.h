@@ -108,7 +108,9 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
  * may be split (the examples pass 15); cuda_stream: a cudaStream_t or NULL. */
 dpmm_status dpmm_set_options(dpmm_ctx* ctx, dpmm_prec prec, int init_K, int burn_out, void* cuda_stream);
 
-/* Data: N x d row-major of type dt.  The library copies and converts it into its
+/* Data (Sec. 2.2: the observations x_1..x_N the mixture is fitted to; Sec. 4.5: the
+ * library holds them once on the device, O(d N) memory): N x d row-major of type dt.
+ * The library copies and converts it into its
  * own device buffer (FP64 for FP64_PLAIN, FP32 for FP32/TF32/BF16X3, BF16 for BF16;
  * Gaussian data is centred by its mean, an exact reparameterisation undone in
  * every output).  X is device memory (on_device = 1) or host memory: page-locked
@@ -157,6 +159,26 @@ dpmm_status dpmm_set_problem(dpmm_ctx* ctx, uint32_t problem);
  * DPMM_EINVAL for a NULL array or entry, n < 0 or iters < 0. */
 dpmm_status dpmm_sweep_batch(dpmm_ctx* const* ctxs, int n, int iters, uint64_t seed);
 
+/* Point-sharded chains: the data of one chain split over several contexts (e.g. one per
+ * GPU).  Every step of Sec. 4.1 that depends on all points reads only
+ * the sufficient statistics (Sec. 4.4), so a shard needs its own points and the sum of all
+ * shards' statistics.  dpmm_set_shard: this context's data are points [point_offset,
+ * point_offset + N) of the whole data set; the random streams of its points are those of
+ * their index in the whole set.  Call after dpmm_set_data.  dpmm_sweep_sharded: `iters`
+ * sweeps of the chain whose points are held by the G contexts shards[0..G) (1 <= G <= 16,
+ * shard s starting where shard s - 1 ends, all with the same prior, options and state).
+ * After each shard's label step, and again after a relabelling, the shards' statistics are
+ * summed in shard order and every shard receives the sum; every shard then draws the same
+ * parameters and takes the same split/merge decisions.  Counts are exact in any order; FP64
+ * sums differ from an unsharded chain's by rounding only.  The Gaussian reduced-precision
+ * paths centre each context's data by its own mean and are refused (DPMM_EINVAL); the
+ * FP64-plain and multinomial paths are supported.  Synchronises between its phases; a
+ * sharded context must not be swept by dpmm_sweep alone.  Errors: DPMM_EINVAL (NULL or
+ * mismatched shards, offsets that do not tile the points), DPMM_ESTATE (a shard without
+ * data), DPMM_ECUDA. */
+dpmm_status dpmm_set_shard(dpmm_ctx* ctx, int64_t point_offset);
+dpmm_status dpmm_sweep_sharded(dpmm_ctx* const* shards, int G, int iters, uint64_t seed);
+
 /* Checkpoint and resume.  A checkpoint holds everything the next sweep reads, taken
  * at a sweep boundary: K, the sweep counter, the problem id, the labels z and zbar,
  * the cluster ages (split eligibility, Sec. 3.4 burn_out), the sufficient-statistics
@@ -181,8 +203,10 @@ dpmm_status dpmm_load_checkpoint(dpmm_ctx* ctx, const void* buf, size_t bytes);
  * DPMM_ETIMEOUT when the mechanism works; the context stays usable.  Synchronises. */
 dpmm_status dpmm_check_wait_timeout(dpmm_ctx* ctx);
 
-/* Labels into caller-owned host arrays of length N (z in [0, K), zbar in {0,1}).
- * Either pointer may be NULL.  Synchronises. */
+/* The chain's current assignments (Sec. 2.3: the cluster labels z_i of Eq. DPLatentVar's
+ * latent variables and the auxiliary sub-cluster labels zbar_i of the augmented space)
+ * into caller-owned host arrays of length N (z in [0, K), zbar in {0,1}).  Either
+ * pointer may be NULL.  Synchronises. */
 dpmm_status dpmm_get_labels(dpmm_ctx* ctx, int32_t* z, uint8_t* zbar);
 
 /* Sufficient statistics (Sec. 4.4) in the data's original coordinates, for the

@@ -33,7 +33,7 @@ EXPORTS = [
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
     "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
     "dpmm_sweep_batch", "dpmm_check_wait_timeout", "dpmm_checkpoint_size", "dpmm_save_checkpoint",
-    "dpmm_load_checkpoint", "dpmm_set_data_csr",
+    "dpmm_load_checkpoint", "dpmm_set_data_csr", "dpmm_set_shard", "dpmm_sweep_sharded",
 ]
 
 
@@ -90,6 +90,8 @@ def load():
             "dpmm_save_checkpoint": ([vp, vp, C.c_size_t], i32),
             "dpmm_load_checkpoint": ([vp, vp, C.c_size_t], i32),
             "dpmm_set_data_csr": ([vp, vp, vp, vp, i64], i32),
+            "dpmm_set_shard": ([vp, i64], i32),
+            "dpmm_sweep_sharded": ([vp, i32, i32, u64], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -238,6 +240,36 @@ def dpmm_sweep_batch(handles, iters, seed):
         raise DPMMError(st, "dpmm_sweep_batch failed (see the failing chain's dpmm_last_error)")
 
 
+def dpmm_set_shard(h, point_offset):
+    _check(h, load().dpmm_set_shard(h, int(point_offset)))
+
+
+def dpmm_sweep_sharded(handles, iters, seed):
+    """Sweeps of one chain whose points are split over the given contexts (in order)."""
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    st = load().dpmm_sweep_sharded(arr, len(handles), int(iters), int(seed))
+    if st != DPMM_OK:
+        msgs = [dpmm_last_error(h) for h in handles]
+        raise DPMMError(st, "; ".join(m for m in msgs if m) or "dpmm_sweep_sharded failed")
+
+
+def shard_allreduce(table, group=None):
+    """The sum of a statistics table over the ranks of a torch.distributed process group,
+    added in rank order (rank 0 + rank 1 + ...), the same bits on every rank: the exchange
+    of a point-sharded chain across processes (one GPU each).  `table` is a numpy array;
+    every rank passes the same shape."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.from_numpy(np.ascontiguousarray(table))
+    parts = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, t, group=group)
+    out = parts[0].clone()
+    for p in parts[1:]:
+        out += p
+    return out.numpy()
+
+
 def dpmm_set_params(h, K, logw, mu=None, W=None, logdetW=None, logtheta=None):
     a = [None if v is None else np.ascontiguousarray(v, dtype=np.float64) for v in (logw, mu, W, logdetW, logtheta)]
     _check(h, load().dpmm_set_params(h, int(K), *[_p(v) for v in a]))
@@ -380,6 +412,9 @@ class DPMM:
 
     def set_problem(self, problem):
         dpmm_set_problem(self.h, problem)
+
+    def set_shard(self, point_offset):
+        dpmm_set_shard(self.h, point_offset)
 
     def checkpoint(self):
         return dpmm_save_checkpoint(self.h)

@@ -372,7 +372,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     bool ok = true;
     auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
     A(&c->dK, sizeof(int));
-    A(&c->diter, 2 * sizeof(uint32_t));  // [sweep index, problem id]
+    A(&c->diter, 3 * sizeof(uint32_t));  // [sweep index, problem id, point offset]
     A(&c->age, sizeof(int) * K_max);
     A(&c->counters, sizeof(int) * 8);
     A(&c->derr, sizeof(int));
@@ -433,7 +433,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         return DPMM_ENOMEM;
     }
     cudaMemset(c->derr, 0, sizeof(int));
-    cudaMemset(c->diter, 0, 2 * sizeof(uint32_t));
+    cudaMemset(c->diter, 0, 3 * sizeof(uint32_t));
     cudaMemset(c->retry, 0, sizeof(int) * S);
     cudaMemset(c->counters, 0, sizeof(int) * 8);
     cudaMemset(c->p_logw, 0, sizeof(double) * S);
@@ -456,7 +456,7 @@ void dpmm_destroy(dpmm_ctx* c) {
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
                   c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg,
-                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part};
+                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
@@ -601,7 +601,9 @@ dpmm_status dpmm_set_data_csr(dpmm_ctx* c, const int64_t* indptr, const int32_t*
     return sparse_finish(c);
 }
 
-static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
+// Initial labels (K = init_K, fair sub-label coins) and the statistics of this context's
+// points.
+static dpmm_status init_phase_a(dpmm_ctx* c, uint64_t seed) {
     const int K = c->init_K;
     CK(c, cudaMemcpyAsync(c->dK, &K, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaMemsetAsync(c->age, 0, sizeof(int) * c->K_max, c->stream));
@@ -615,15 +617,28 @@ static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
         CK(c, launch_substats(c, seed, 0));
         CK(c, launch_combine(c));
     }
-    // clusters left empty by the initial draw are removed (no ages, no sweep index change)
+    return DPMM_OK;
+}
+
+// clusters left empty by the initial draw are removed (no ages, no sweep index change)
+static dpmm_status init_phase_b(dpmm_ctx* c, uint64_t seed) {
     CK(c, launch_splitmerge(c, seed, 2, 0));
     CK(c, launch_relabel(c, seed));
     c->initialized = true;
     return DPMM_OK;
 }
 
-// the kernels of one sweep, in order, on the context's stream
-static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
+static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
+    dpmm_status s = init_phase_a(c, seed);
+    return s != DPMM_OK ? s : init_phase_b(c, seed);
+}
+
+// The kernels of one sweep, in order, on the context's stream, in three phases: (a) the
+// parameters from the statistics, the labels, sub-labels and the statistics of this
+// context's points; (b) splits, merges, relabelling and the recount of the statistics
+// when anything changed; (c) the sweep index.  A point-sharded sweep exchanges the
+// statistics after (a) and after (b).
+static cudaError_t sweep_phase_a(dpmm_ctx* c, uint64_t seed) {
     const bool tc = (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16);
     const bool x3 = c->prec == DPMM_PREC_BF16X3;
     cudaError_t e = cudaSuccess;
@@ -641,10 +656,20 @@ static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
         if ((e = launch_substats(c, seed, 1)) != cudaSuccess) return e;
         if ((e = launch_combine(c)) != cudaSuccess) return e;
     }
-    if ((e = launch_splitmerge(c, seed, (c->step_mask & 2u) ? 1 : 0, (c->step_mask & 4u) ? 1 : 0)) != cudaSuccess)
-        return e;
-    if ((e = launch_relabel(c, seed)) != cudaSuccess) return e;
-    return launch_advance(c);
+    return e;
+}
+
+static cudaError_t sweep_phase_b(dpmm_ctx* c, uint64_t seed) {
+    cudaError_t e = launch_splitmerge(c, seed, (c->step_mask & 2u) ? 1 : 0, (c->step_mask & 4u) ? 1 : 0);
+    if (e != cudaSuccess) return e;
+    return launch_relabel(c, seed);
+}
+
+static cudaError_t enqueue_sweep(dpmm_ctx* c, uint64_t seed) {
+    cudaError_t e = sweep_phase_a(c, seed);
+    if (e == cudaSuccess) e = sweep_phase_b(c, seed);
+    if (e == cudaSuccess) e = launch_advance(c);
+    return e;
 }
 
 dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
@@ -838,6 +863,94 @@ dpmm_status dpmm_sweep_batch(dpmm_ctx* const* ctxs, int n, int iters, uint64_t s
             const dpmm_status s = dpmm_sweep(ctxs[i], 1, seed);
             if (s != DPMM_OK) return s;
         }
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_set_shard(dpmm_ctx* c, int64_t point_offset) {
+    if (!c) return DPMM_EINVAL;
+    if (point_offset < 0 || point_offset + c->N > 0x7FFFFFFFLL)
+        return fail(c, DPMM_EINVAL, "the shard must lie within points [0, 2^31)");
+    const uint32_t off = (uint32_t)point_offset;
+    CK(c, cudaMemcpyAsync(c->diter + 2, &off, sizeof(off), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->poff = point_offset;
+    return DPMM_OK;
+}
+
+// every shard must describe the same chain: same model, options and state
+static dpmm_status shard_check(dpmm_ctx* const* sh, int G) {
+    dpmm_ctx* a = sh[0];
+    int64_t next = 0;
+    for (int s = 0; s < G; ++s) {
+        dpmm_ctx* b = sh[s];
+        if (!b->X) return fail(b, DPMM_ESTATE, "every shard needs its data");
+        if (b->kind != a->kind || b->d != a->d || b->K_max != a->K_max || b->prec != a->prec || b->alpha != a->alpha ||
+            b->kappa0 != a->kappa0 || b->nu0 != a->nu0 || b->m0 != a->m0 || b->psi0 != a->psi0 || b->beta != a->beta ||
+            b->init_K != a->init_K || b->burn_out != a->burn_out || b->step_mask != a->step_mask ||
+            b->device != a->device || b->initialized != a->initialized)
+            return fail(b, DPMM_EINVAL, "shards of one chain need the same prior, options, device and state");
+        if (b->poff != next) return fail(b, DPMM_EINVAL, "shard s must start where shard s - 1 ends (dpmm_set_shard)");
+        next += b->N;
+        CK(b, cudaStreamSynchronize(b->stream));
+    }
+    // the shards' data were centred separately (reduced-precision Gaussian paths centre by
+    // the data's mean); one chain needs one coordinate system
+    for (int s = 1; s < G; ++s)
+        if (sh[s]->h_center != a->h_center)
+            return fail(sh[s], DPMM_EINVAL, "sharded Gaussian chains need the FP64-plain path (uncentred data)");
+    return DPMM_OK;
+}
+
+static dpmm_status sync_all(dpmm_ctx* const* sh, int G) {
+    for (int s = 0; s < G; ++s) CK(sh[s], cudaStreamSynchronize(sh[s]->stream));
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_sweep_sharded(dpmm_ctx* const* sh, int G, int iters, uint64_t seed) {
+    if (!sh || G < 1 || G > 16 || iters < 0) return DPMM_EINVAL;
+    for (int s = 0; s < G; ++s)
+        if (!sh[s]) return DPMM_EINVAL;
+    dpmm_status st = shard_check(sh, G);
+    if (st != DPMM_OK) return st;
+    dpmm_ctx* c0 = sh[0];
+    auto phase = [&](auto&& f) -> dpmm_status {
+        for (int s = 0; s < G; ++s) {
+            dpmm_status r = f(sh[s]);
+            if (r != DPMM_OK) return r;
+        }
+        return sync_all(sh, G);
+    };
+    auto exchange = [&](const int* gate) -> dpmm_status {
+        CK(c0, shard_exchange(sh, G, gate));
+        CK(c0, cudaStreamSynchronize(c0->stream));
+        return DPMM_OK;
+    };
+    if (!c0->initialized) {
+        if ((st = phase([&](dpmm_ctx* c) { return init_phase_a(c, seed); })) != DPMM_OK) return st;
+        if ((st = exchange(nullptr)) != DPMM_OK) return st;
+        if ((st = phase([&](dpmm_ctx* c) { return init_phase_b(c, seed); })) != DPMM_OK) return st;
+        if ((st = exchange(c0->counters + 4)) != DPMM_OK) return st;
+    }
+    for (int it = 0; it < iters; ++it) {
+        st = phase([&](dpmm_ctx* c) {
+            CK(c, sweep_phase_a(c, seed));
+            return DPMM_OK;
+        });
+        if (st != DPMM_OK) return st;
+        if ((st = exchange(nullptr)) != DPMM_OK) return st;
+        st = phase([&](dpmm_ctx* c) {
+            CK(c, sweep_phase_b(c, seed));
+            return DPMM_OK;
+        });
+        if (st != DPMM_OK) return st;
+        if ((st = exchange(c0->counters + 4)) != DPMM_OK) return st;  // only when the shards recounted
+        st = phase([&](dpmm_ctx* c) {
+            CK(c, launch_advance(c));
+            return DPMM_OK;
+        });
+        if (st != DPMM_OK) return st;
+    }
+    for (int s = 0; s < G; ++s) sh[s]->seed = seed;
     return DPMM_OK;
 }
 

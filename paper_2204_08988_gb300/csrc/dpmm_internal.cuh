@@ -15,6 +15,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -57,11 +58,20 @@ __host__ __device__ inline void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+// The entity word c0 of the point-keyed streams (tags INIT, Z, ZBAR, RESUB) is the point's
+// index in the whole data set: poff + its index in this context's data (poff = 0 unless the
+// data are one shard of a larger set, dpmm_set_shard).
+__host__ __device__ inline bool point_tag(uint32_t tag) {
+    return tag == TAG_INIT || tag == TAG_Z || tag == TAG_ZBAR || tag == TAG_RESUB;
+}
+
 struct Key {
     uint64_t seed;
     uint32_t iter;
     uint32_t problem;
+    uint32_t poff;  // point offset of this context's data in the whole data set
     __host__ __device__ void block(uint32_t c0, uint32_t tag, uint32_t blk, uint32_t w[4]) const {
+        if (point_tag(tag)) c0 += poff;
         philox(c0, iter, (tag << 24) | (blk & 0xFFFFFFu), problem, (uint32_t)seed, (uint32_t)(seed >> 32), w);
     }
 };
@@ -229,7 +239,7 @@ struct dpmm_ctx {
     int32_t* z = nullptr;
     uint8_t* zbar = nullptr;
     int* dK = nullptr;        // device: current K
-    uint32_t* diter = nullptr;// device: [sweep counter, problem id] (Philox counter words c1, c3)
+    uint32_t* diter = nullptr;// device: [sweep counter, problem id, point offset] (Philox words c1, c3; c0 offset)
     int* age = nullptr;       // device, K_max
     int* counters = nullptr;  // device, 8
     int* derr = nullptr;      // device error word
@@ -292,6 +302,10 @@ struct dpmm_ctx {
     double* sp_lgt = nullptr;      // lgamma(beta + c) - lgamma(beta), c < SP_LGT (uniform beta)
     double* sp_lgb = nullptr;      // lgamma(beta_j)
     void* sp_part = nullptr;       // 3 K_max x ceil(d / 2048) (max, sum exp) of the FP32 theta draws
+
+    // point-sharded chains: this context's first point in the whole data set
+    int64_t poff = 0;
+    void* shard_scratch = nullptr; // the summed statistics of a sharded sweep (shard 0)
     double* dbg_scores = nullptr;  // device N x K scores when the score hook is active
 
     // one sweep captured as a CUDA graph (kernels read K and the sweep index from
@@ -337,6 +351,7 @@ bool sparse_path(const dpmm_ctx* c);
 cudaError_t sparse_build_dense(dpmm_ctx* c, const void* X, dpmm_dtype dt, int* bad);
 cudaError_t sparse_prepare(dpmm_ctx* c);
 cudaError_t launch_sparse(dpmm_ctx* c, uint64_t seed, int mode, const int* gate);
+cudaError_t shard_exchange(dpmm_ctx* const* sh, int G, const int* gate);
 
 // profiling helpers (no-ops unless enabled)
 void prof_begin(dpmm_ctx* c, const char* name);

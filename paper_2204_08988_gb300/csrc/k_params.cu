@@ -72,7 +72,7 @@ struct VarArgs {
 __global__ void variates_kernel(VarArgs a) {
     const int K = *a.dK;
     const int d = a.sv.L.d;
-    Key key{a.seed, a.diter[0], a.diter[1]};
+    Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if ((int)blockIdx.y == 3 * a.Kmax) {
         const int T = 3 * K + 1;
@@ -337,7 +337,7 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
     const int s = blockIdx.x;
     if (s >= 3 * K) return;
     const int k = s / 3, h = s % 3 - 1;
-    Key key{seed, diter[0], diter[1]};
+    Key key{seed, diter[0], diter[1], diter[2]};
     double* lt = p_logtheta + (size_t)s * d;
     double mx = -INFINITY;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
@@ -371,7 +371,7 @@ __global__ void dirichlet_draw_f32_kernel(int d, const double* beta, const int* 
     if (s >= 3 * K) return;
     const int k = s / 3, h = s % 3 - 1;
     const int j0 = blockIdx.y * DP_CHUNK, j1 = min(d, j0 + DP_CHUNK);
-    Key key{seed, diter[0], diter[1]};
+    Key key{seed, diter[0], diter[1], diter[2]};
     float* qt = q_logtheta + (size_t)s * d;
     float mx = -INFINITY;
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {

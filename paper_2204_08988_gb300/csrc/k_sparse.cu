@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) sparse_sweep_kernel(SpArgs<T> a) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const Key key{a.seed, a.diter[0], a.diter[1]};
+    const Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
     for (int64_t i = w0; i < a.N; i += nw) {
         const int64_t r0 = a.ptr[i], r1 = a.ptr[i + 1];
         int zi, hi = 0;

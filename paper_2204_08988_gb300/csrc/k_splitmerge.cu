@@ -259,7 +259,7 @@ __global__ void hastings_kernel(SMArgs a, const double* Ltab, const uint32_t* di
     const int npairs = K * (K - 1) / 2;
     if (e >= K + npairs) return;
     const int d = a.L.d;
-    Key key{seed, diter[0], diter[1]};
+    Key key{seed, diter[0], diter[1], diter[2]};
     auto live = [&](int k) { return labels_ran ? smv(a, k, -1, d, d) > 0 : true; };
     auto cid = [&](int k) {
         int c = 0;
@@ -494,7 +494,7 @@ __global__ void relabel_kernel(int64_t N, const int* relabel, int Kmax, const in
     if (mode == 1) zbar[i] = 0;
     else if (mode == 2) zbar[i] = 1;
     else if (mode == 3) {
-        Key key{seed, diter[0], diter[1]};
+        Key key{seed, diter[0], diter[1], diter[2]};
         zbar[i] = d_uniform(key, (uint32_t)i, TAG_RESUB, 0) < 0.5 ? 0 : 1;
     }
 }

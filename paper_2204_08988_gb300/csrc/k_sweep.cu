@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
     T* xr = sx + (size_t)tid * (d + 1);
     if (live)
         for (int j = 0; j < d; ++j) xr[j] = ldx<T, XT>(X + i * xs + j);
-    Key key{seed, diter[0], diter[1]};
+    Key key{seed, diter[0], diter[1], diter[2]};
     T best = -INFINITY;
     int zb = 0;
     uint32_t w[4];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(MAXT) substats_kernel(SubArgs<T> a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, a.diter[0], a.diter[1]};
+    Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
     const XT* X = (const XT*)a.X;
 
     // register block of this thread
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(256) substats_f32_kernel(SubArgs<float> a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, a.diter[0], a.diter[1]};
+    Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
     const XT* X = (const XT*)a.X;
     const bool worker = tid < nblk * G;
     const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float>
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, a.diter[0], a.diter[1]};
+    Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
     const XT* X = (const XT*)a.X;
     const bool worker = tid < nblk;
     int jb = 0, lb = 0;
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int g = blockIdx.x;
     const int64_t p0 = (int64_t)g * a.R, p1 = min(a.N, p0 + a.R);
-    Key key{a.seed, a.diter[0], a.diter[1]};
+    Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
     const XT* X = (const XT*)a.X;
     const bool worker = tid < nblk * G;
     const int myblk = worker ? tid % nblk : 0, grp = worker ? tid / nblk : 0;
@@ -1025,7 +1025,7 @@ __global__ void init_labels_kernel(int64_t N, int initK, uint64_t seed, const ui
                                    uint8_t* zbar) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    Key key{seed, 0, diter[1]};
+    Key key{seed, 0, diter[1], diter[2]};
     uint32_t w[4];
     key.block((uint32_t)i, TAG_INIT, 0, w);
     int k = (int)(u01_f64(w[0], w[1]) * initK);

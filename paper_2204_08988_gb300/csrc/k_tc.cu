@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     unsigned char* bb = bs + (size_t)a.cap_rows * 128;          // cap_rows x 32
     float* ones = (float*)(bb + (size_t)a.cap_rows * 32);       // BM rows x 8, no swizzle
     float* sbuf = ones + BM * 8;                                // (cap_rows / dn) clusters x BM
-    float* sbend = sbuf + (size_t)(a.cap_rows / a.dn) * BM;
-    uint64_t* bars = (uint64_t*)(((uintptr_t)(sbend + a.Kmax) + 7) & ~(uintptr_t)7);
+    float* ct = sbuf + (size_t)(a.cap_rows / a.dn) * BM;         // 2 x Kmax: c_k of a group, by group parity
+    uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + 2 * a.Kmax) + 7) & ~(uintptr_t)7);
     uint64_t* full = bars;            // XST
     uint64_t* empty = full + XST;     // XST
     uint64_t* tfull = empty + XST;    // NBUF
@@ -139,12 +139,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         }
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], NEPI);  // one arrival per epilogue warp
+            mbar_init(&tempty[b], NEPI * 32);
         }
         mbar_init(bload, 1);
         mbar_init(facfree, 1);
-        for (int b = 0; b < 8; ++b) mbar_init(&sfull[b], NPART);  // a quarter's warps only
-        for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART);
+        for (int b = 0; b < 8; ++b) mbar_init(&sfull[b], NPART * 32);
+        for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART * 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -177,6 +177,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 if (g > 0 && !mbar_wait(facfree, (uint32_t)((g - 1) & 1), abort)) { ok = false; break; }
                 const int kb = g * a.capc, rows_pad = (group_size(g) * a.dn + 15) / 16 * 16;
                 const uint32_t bbytes = (uint32_t)rows_pad * 128u, nbytes = (uint32_t)rows_pad * 32u;
+                // the group's c_k, published by this thread's arrival below (the epilogue of
+                // group g - 2, the last reader of this half, has finished: the factors of
+                // group g - 1 are no longer read)
+                float* ctg = ct + (g & 1) * a.capc;
+                for (int kk = 0; kk < group_size(g); ++kk) ctg[kk] = a.qc[3 * (kb + kk)];
                 mbar_expect_tx(bload, bbytes + nbytes);
                 const unsigned char* fsrc = (const unsigned char*)a.img + (size_t)kb * a.dn * 128;
                 for (uint32_t off = 0; off < bbytes; off += 32768u) {
@@ -256,13 +261,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const uint32_t iter = *a.diter;
-        Key key{a.seed, iter, a.diter[1]};
+        Key key{a.seed, iter, a.diter[1], a.diter[2]};
         int64_t ch = 0, it = 0;
         uint32_t nq = 0;  // uses of this quarter's draw barrier (the same in its four parts)
         bool ok = true;
         for (int g = 0; g < ngroups && ok; ++g) {
         const int kb = g * a.capc, Kg = group_size(g), nch = (Kg + a.NC - 1) / a.NC;
         const bool first = g == 0, final = g == ngroups - 1;
+        // the group's c_k table (written before the factor copies' arrival)
+        if (!mbar_wait(bload, (uint32_t)(g & 1), abort)) { ok = false; break; }
+        const float* ctg = ct + (g & 1) * a.capc;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
             const int64_t i = t * BM + r;
             // Exact Gumbel-max.  Every part scores its clusters (kept in shared memory)
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             int k1 = 0;
             float* sr = sbuf + r;  // score of the group's cluster kk at sr[kk * BM]
             auto score = [&](int kk, float q) {
-                const float sc = __ldg(a.qc + 3 * (kb + kk)) - 0.5f * q;
+                const float sc = ctg[kk] - 0.5f * q;
                 if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
                     if (i < a.N) a.scores[i * K + kb + kk] = (double)sc;
                 }
@@ -313,8 +321,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 }
                 // the warp's loads are complete (wait::ld); one lane arrives for the warp
                 fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[b]);
+                mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
             // Slot sl is reused two tiles later; every reader of it has arrived on the
@@ -324,8 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             xm1[sl][part][r] = m1;
             xm2[sl][part][r] = m2;
             xk1[sl][part][r] = k1;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sfull[sl * 4 + quarter]);
+            mbar_arrive(&sfull[sl * 4 + quarter]);
             if (!mbar_wait(&sfull[sl * 4 + quarter], use, abort)) { ok = false; break; }
             // the row's best and second-best scores (every part computes the same)
             float g1 = xm1[sl][0][r], g2 = xm2[sl][0][r];
@@ -399,8 +405,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 }
                 mbest[sl][part][r] = best;
                 mz[sl][part][r] = zb;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&qbar[quarter]);
+                mbar_arrive(&qbar[quarter]);
                 if (!mbar_wait(&qbar[quarter], (uint32_t)(nq & 1), abort)) { ok = false; break; }
                 ++nq;
                 if (part == 0 && need) {
@@ -517,7 +522,7 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     q.dn = (c->d + 7) / 8 * 8;
     q.NC = tc::BUFCOLS / q.dn;
     while ((q.NC * q.dn) % 16) --q.NC;
-    const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 4 + 32 * 8 + 64;
+    const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 8 + 32 * 8 + 64;
     const size_t limit = 227 * 1024 - 24576;  // leave room for the kernel's static shared memory (22 KB)
     // factor row, -b row, and each cluster's 128 scores spread over its dn rows
     const size_t per_row = 128 + 32 + (tc::BM * 4 + q.dn - 1) / q.dn;

@@ -56,7 +56,7 @@ struct Args {
 __device__ __noinline__ void gumbel_update(uint64_t seed, uint32_t iter, uint32_t prob, uint32_t i, int k, float sc,
                                            float* best,
                                            int* zb) {
-    Key key{seed, iter, prob};
+    Key key{seed, iter, prob, 0};  // i is the point's index in the whole data set
     uint32_t w[4];
     key.block(i, TAG_Z, (uint32_t)(k >> 1), w);
     const float u = u01_f32((k & 1) ? w[2] : w[0]);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
                 t1[c] = t2[c] = -INFINITY;
                 tk[c] = c;
             }
-            const uint32_t iter = a.diter[0], prob = a.diter[1];
+            const uint32_t iter = a.diter[0], prob = a.diter[1], poff = a.diter[2];  // poff: point offset (shards)
             const uint32_t tb = tmem + lane_off + (uint32_t)(b * 128);
             for (int k0 = 0; k0 < NB; k0 += 32) {
                 float y[32];
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_mult_kernel(const __grid_c
                         for (int j = 0; j < 32; ++j) {
                             const int k = k0 + j;
                             const float sc = k < K ? ct[k] + y[j] : -INFINITY;
-                            if (sc > lim) gumbel_update(a.seed, iter, prob, (uint32_t)i, k, sc, &best, &zd);
+                            if (sc > lim) gumbel_update(a.seed, iter, prob, (uint32_t)i + poff, k, sc, &best, &zd);
                         }
                     }
                 }

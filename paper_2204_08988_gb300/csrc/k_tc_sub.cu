@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
         // ------------------------------------------------------------ score warps
         const int q = warp & 3, r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        Key key{a.seed, a.diter[0], a.diter[1]};
+        Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
         float c0 = 0.f, c1 = 0.f;
         bool ok = true;
         int it = 0;

@@ -79,7 +79,7 @@ struct Args {
 __device__ __noinline__ void gumbel_draw(uint64_t seed, uint32_t iter, uint32_t prob, uint32_t i, int k, float sc,
                                          float* best,
                                          int* zb) {
-    Key key{seed, iter, prob};
+    Key key{seed, iter, prob, 0};  // i is the point's index in the whole data set
     uint32_t w[4];
     key.block(i, TAG_Z, (uint32_t)(k >> 1), w);
     const float u = u01_f32((k & 1) ? w[2] : w[0]);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_x3_kernel(Args a) {
         const int quarter = warp & 3, mt = ew >> 2;
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t iter = a.diter[0], prob = a.diter[1];
+        const uint32_t iter = a.diter[0], prob = a.diter[1], poff = a.diter[2];  // poff: point offset (shards)
         uint32_t cc = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < npass && ok; t += gridDim.x) {
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_x3_kernel(Args a) {
                 if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
                     if (i < a.N) a.scores[i * K + k] = (double)sc;
                 }
-                if (sc + GSKIP > best) gumbel_draw(a.seed, iter, prob, (uint32_t)i, k, sc, &best, &zb);
+                if (sc + GSKIP > best) gumbel_draw(a.seed, iter, prob, (uint32_t)i + poff, k, sc, &best, &zb);
             }
             if (ok && i < a.N) a.z[i] = zb;
         }

@@ -46,3 +46,41 @@ def test_job_rate_single_process():
 
     value, ms = bench.job_rate(20.0, 100, 4, 1)
     assert ms == 20.0 and value == pytest.approx(100 * 4 / 0.020)
+
+
+def _shard_rank(rank, world, port, out):
+    import numpy as np
+    import torch.distributed as dist
+
+    import paper_2204_08988_gb300 as P
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # a statistics table of this rank's shard: counts and FP64 sums of very different sizes
+        rng = np.random.default_rng(100 + rank)
+        table = rng.standard_normal((6, 45)) * 10.0 ** rng.integers(-8, 8, (6, 45))
+        out[rank] = P.shard_allreduce(table).tobytes()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_shard_statistics_sum_in_rank_order():
+    """The cross-process exchange of a point-sharded chain: every rank receives the same
+    bits, the sum rank 0 + rank 1 + rank 2 in that order (FP64 addition is not associative,
+    so a fixed order is what makes the shards agree)."""
+    import numpy as np
+
+    world, port = 3, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    tables = []
+    for r in range(world):
+        rng = np.random.default_rng(100 + r)
+        tables.append(rng.standard_normal((6, 45)) * 10.0 ** rng.integers(-8, 8, (6, 45)))
+    want = (tables[0] + tables[1]) + tables[2]
+    for r in range(world):
+        got = np.frombuffer(res[r], dtype=np.float64).reshape(6, 45)
+        assert np.array_equal(got, want)
