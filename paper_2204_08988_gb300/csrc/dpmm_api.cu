@@ -390,6 +390,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     if (c->kind == DPMM_PRIOR_NIW) A(&c->q_W, sizeof(float) * S * d * d);
     A(&c->q_c, sizeof(float) * S);
     A(&c->q_b, sizeof(float) * S * d);
+    if (c->kind == DPMM_PRIOR_NIW) A(&c->p_b, sizeof(double) * S * d);
     A(&c->q_logtheta, sizeof(float) * S * d);
     A(&c->cweights, sizeof(double) * K_max);
     A(&c->eps, sizeof(double) * S * d);
@@ -456,7 +457,7 @@ void dpmm_destroy(dpmm_ctx* c) {
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
                   c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg,
-                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch};
+                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch, c->p_b};
     for (void* p : ps) dfree(p);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);

@@ -258,6 +258,7 @@ struct dpmm_ctx {
     double *p_logw = nullptr, *p_mu = nullptr, *p_W = nullptr, *p_logdetW = nullptr, *p_c = nullptr,
            *p_logtheta = nullptr;
     float *q_mu = nullptr, *q_W = nullptr, *q_c = nullptr, *q_b = nullptr, *q_logtheta = nullptr;
+    double* p_b = nullptr;   // b = mu^T W per slot (FP64, TF32-rounded W on the TF32 path)
     void* tc_img = nullptr;  // tensor-core operand image of the cluster parameters
     size_t tc_img_bytes = 0;
     void* tcs_img = nullptr;  // tensor-core sub-cluster factor images (K_max x 10 KB)

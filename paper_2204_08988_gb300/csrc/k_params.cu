@@ -166,7 +166,7 @@ struct NiwPrior {
 // factorisation loses more than 10 bits of a pivot to cancellation (or meets a
 // non-positive one) is flagged in retry[] and redone by the FP64 instantiation
 // (launched with retry set, it takes only the flagged slots).
-// Dynamic shared memory: (E doubles when staged) + (d*ld + 7*d (+ d*d when W fits)) T.
+// Dynamic shared memory: (E doubles when staged) + (d*ld + 11*d (+ d*d when W fits)) T.
 __device__ inline float log_t(float x) { return logf(x); }
 __device__ inline double log_t(double x) { return log(x); }
 
@@ -193,8 +193,9 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     T* rd = acc + d;              // d: 1 / U_jj
     T* rw = rd + d;               // d: 1 / W_jj
     T* piv = rw + d;              // d: pivots
+    T* cols = piv + d;            // 4 d: the factorisation's scaled panel columns
     double* Wg = p_W + (size_t)s * d * d;
-    T* W = w_in_smem ? piv + d : (T*)Wg;  // d x d working copy (global only when T = double)
+    T* W = w_in_smem ? cols + 4 * d : (T*)Wg;  // d x d working copy (global only when T = double)
     __shared__ double sh[32];
     __shared__ double s_n, s_rn, s_kn, s_rkn;
     __shared__ int s_fail;
@@ -240,8 +241,7 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         if (l == j) dg[j] = a;
     }
     __syncthreads();
-    // rw is free until the solve: scratch
-    chol_ldl_t<T>(A, d, ld, piv, rd, rw, dg, sizeof(T) == 4 ? T(1.0 / 1024) : T(0), &s_fail);
+    chol_ldl_t<T>(A, d, ld, piv, rd, cols, dg, sizeof(T) == 4 ? T(1.0 / 1024) : T(0), &s_fail);
     if (s_fail) {
         if (sizeof(T) == 4) {  // redo this slot in FP64
             if (tid == 0) retry[s] = 1;
@@ -417,7 +417,7 @@ __global__ void dirichlet_norm_f32_kernel(int d, const int* dK, const double* lo
 // shift the next statistics are accumulated with (the cluster's drawn mean).
 __global__ void derive_kernel(int kind, int d, int tf32, const int* dK, const double* p_logw, const double* p_mu,
                               const double* p_W, const double* p_c, const double* p_logtheta, float* q_mu,
-                              float* q_W, float* q_c, float* q_b, float* q_logtheta, double* shift_new,
+                              float* q_W, float* q_c, float* q_b, double* p_b, float* q_logtheta, double* shift_new,
                               float* shift32) {
     const int K = *dK;
     const int s = blockIdx.x;
@@ -432,6 +432,7 @@ __global__ void derive_kernel(int kind, int d, int tf32, const int* dK, const do
             double b = 0.0;  // b_j = sum_l mu_l W_lj, with W as the tensor cores see it
             for (int l = 0; l <= j; ++l) b += mu[l] * (tf32 ? (double)round_tf32((float)W[l * d + j]) : W[l * d + j]);
             q_b[(size_t)s * d + j] = (float)b;
+            p_b[(size_t)s * d + j] = b;  // read by the tensor-core image builds
             if (s % 3 == 0) {
                 shift_new[(size_t)(s / 3) * d + j] = (double)(float)mu[j];
                 shift32[(size_t)(s / 3) * d + j] = (float)mu[j];
@@ -469,7 +470,7 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         NiwPrior pr{c->kappa0, c->nu0, c->center + c->d, c->center + 2 * c->d};
         // shared memory of the T instantiation: E doubles (staged), then d*ld + 7 d (+ d*d) T
         auto plan = [&](size_t tsz, int& staged, int& w_in_smem) {
-            size_t sm = tsz * (dl + 7 * (size_t)c->d);
+            size_t sm = tsz * (dl + 11 * (size_t)c->d);
             staged = w_in_smem = 0;
             if (sm + 8 * E <= 200 * 1024) {
                 sm += 8 * E;
@@ -525,7 +526,7 @@ cudaError_t launch_derive(dpmm_ctx* c) {
     prof_begin(c, "derive");
     const dim3 dgrid(3 * c->K_max, c->kind == DPMM_PRIOR_NIW ? 1 : (c->d + 4095) / 4096);
     derive_kernel<<<dgrid, 128, 0, c->stream>>>(c->kind, c->d, c->prec == DPMM_PREC_TF32, c->dK, c->p_logw, c->p_mu, c->p_W, c->p_c,
-                                                       c->p_logtheta, c->q_mu, c->q_W, c->q_c, c->q_b,
+                                                       c->p_logtheta, c->q_mu, c->q_W, c->q_c, c->q_b, c->p_b,
                                                        c->q_logtheta, c->shift_new, c->shift32);
     prof_end(c, "derive");
     c->nlaunch += 1;

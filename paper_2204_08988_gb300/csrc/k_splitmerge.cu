@@ -62,7 +62,7 @@ __device__ inline void pair_of(int p, int K, int& k1, int& k2) {
     k2 = r + 1 + (p - off);
 }
 
-// Dynamic shared memory: d*d + 4*d doubles.
+// Dynamic shared memory: d (d | 1) + 10 d doubles (+ 2 E when the statistics are staged).
 __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     extern __shared__ double smem[];
     __shared__ double sh[32];
@@ -124,7 +124,8 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     double* x2 = x1 + d;
     double* piv = x2 + d;      // pivots of the factorisation
     double* rs = piv + d;
-    double* S1 = rs + d;       // staged statistics of (k1, h) and of cluster k2 (E each)
+    double* cols = rs + d;     // 4 d: the factorisation's scaled panel columns
+    double* S1 = cols + 4 * d; // staged statistics of (k1, h) and of cluster k2 (E each)
     double* S2 = S1 + a.L.E;
     const bool staged = a.stage != 0;
     if (staged) {
@@ -171,7 +172,7 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
         A[q] = a.psi0[j * d + l] + C + f * (xb[j] - a.m0s[j]) * (xb[l] - a.m0s[l]);
     }
     __syncthreads();
-    chol_ldl(A, d, ld, piv, rs, x1, derr);  // x1 is free by now: scratch
+    chol_ldl(A, d, ld, piv, rs, cols, derr);
     // -(nun/2) log|Psi_n| and the multivariate-lgamma ratio (the prior's part from the
     // host), summed over j by all threads; lane 0 of warp 0 adds log kappa_n
     double part = 0.0;
@@ -544,7 +545,7 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
         // statistics blocks it reads when they fit
         size_t sm = 0;
         if (c->kind == DPMM_PRIOR_NIW) {
-            sm = sizeof(double) * ((size_t)c->d * (c->d | 1) + 6 * c->d);
+            sm = sizeof(double) * ((size_t)c->d * (c->d | 1) + 10 * c->d);
             const size_t st = sm + sizeof(double) * 2 * (size_t)c->st.E;
             if (st <= 160 * 1024) {
                 sm = st;

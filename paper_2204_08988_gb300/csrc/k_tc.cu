@@ -461,8 +461,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
 // byte offset img_rows * 128 (every cluster up to K_max) follows the -b image (no swizzle, 32 B per row, element
 // (n, l) at (n / 8) * 256 + (l / 4) * 128 + (n % 8) * 16 + (l % 4) * 4): row n holds
 // (-b_hi, -b_lo, 0, ..., 0), where b = sum_m mu_m W_k[m][j] is formed in FP64 with
-// the factor as the tensor cores see it, b_hi = tf32(b) and b_lo = tf32(b - b_hi).
-__global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const double* pW, const double* pmu,
+// the factor as the tensor cores see it (by derive_kernel, once per sweep for every
+// slot), b_hi = tf32(b) and b_lo = tf32(b - b_hi).
+__global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const double* pW, const double* pb,
                                 int img_rows, float* img) {
     const int K = *dK;
     const int rows = (K * dn + 15) / 16 * 16;
@@ -480,9 +481,7 @@ __global__ void tc_image_kernel(const int* dK, int Kmax, int d, int dn, const do
         if (l < 8) {
             float bv = 0.f;
             if (live && l < 2) {
-                const double* mu = pmu + (size_t)3 * k * d;
-                double bj = 0.0;
-                for (int m = 0; m <= j; ++m) bj += mu[m] * (double)round_tf32((float)W[(size_t)m * d + j]);
+                const double bj = pb[(size_t)3 * k * d + j];  // formed once per sweep by derive_kernel
                 const float hi = round_tf32((float)bj);
                 bv = l == 0 ? -hi : -round_tf32((float)(bj - (double)hi));
             }
@@ -567,7 +566,7 @@ cudaError_t tc_prepare(dpmm_ctx* c) {
         e = cudaMemsetAsync(c->tc_img, 0, bytes, c->stream);
         if (e != cudaSuccess) return e;
     }
-    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->p_W, c->p_mu, q.img_rows,
+    tc::tc_image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->K_max, c->d, q.dn, c->p_W, c->p_b, q.img_rows,
                                                     (float*)c->tc_img);
     c->nlaunch += 1;
     return cudaGetLastError();

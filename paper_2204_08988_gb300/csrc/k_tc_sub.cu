@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
 // swizzle, 32 B per row, element (n, l) at (n / 8) * 256 + (l / 4) * 128 + (n % 8) *
 // 16 + (l % 4) * 4) with row n = (-b_hi, -b_lo, 0, ...), b = sum_m mu_s[m] W_s[m][j]
 // in FP64 with the factor as the tensor cores see it.
-__global__ void image_kernel(const int* dK, int d, const double* pW, const double* pmu, unsigned char* img) {
+__global__ void image_kernel(const int* dK, int d, const double* pW, const double* pb, unsigned char* img) {
     const int K = *dK;
     const int64_t total = (int64_t)K * 64 * 32;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -583,9 +583,7 @@ __global__ void image_kernel(const int* dK, int d, const double* pW, const doubl
         if (l < 8) {
             float bv = 0.f;
             if (j < d && l < 2) {
-                const double* mu = pmu + (size_t)s * d;
-                double bj = 0.0;
-                for (int m = 0; m <= j; ++m) bj += mu[m] * (double)round_tf32((float)W[(size_t)m * d + j]);
+                const double bj = pb[(size_t)s * d + j];  // formed once per sweep by derive_kernel
                 const float hi = round_tf32((float)bj);
                 bv = l == 0 ? -hi : -round_tf32((float)(bj - (double)hi));
             }
@@ -610,7 +608,7 @@ cudaError_t substats_tc_prepare(dpmm_ctx* c) {
         e = cudaMemsetAsync(c->tcs_img, 0, bytes, c->stream);
         if (e != cudaSuccess) return e;
     }
-    tcs::image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->d, c->p_W, c->p_mu, (unsigned char*)c->tcs_img);
+    tcs::image_kernel<<<256, 256, 0, c->stream>>>(c->dK, c->d, c->p_W, c->p_b, (unsigned char*)c->tcs_img);
     c->nlaunch += 1;
     return cudaGetLastError();
 }
