@@ -11,7 +11,8 @@ and K timed sweeps follow.  L2 is flushed (256 MiB write) between timed steps,
 outside the timed events.
 
 --impl reference times the FP64 CPU oracle (the paper's method written as plain
-loops) on a bounded sample of the same workload, on this host's cores.
+loops) on a bounded sample of the same workload, on all of this host's cores (one
+independent oracle chain per core on its own slice of the sample).
 Multi-GPU (torchrun): independent replicas, one chain per GPU (weak scaling).
 """
 import argparse
@@ -36,7 +37,8 @@ METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one
 # per cluster): the point part scales with N, the factor part with K.  Must be re-taken (or
 # removed) whenever that kernel changes.
 TRAFFIC_BYTES = {
-    ("labels_tc", "gauss_d32"): ((256.261120e6 + 9.003008e6) / 2e6, 0.0),
+    # 2 M points, K = 20: 256.170240 MB read + 8.826368 MB written
+    ("labels_tc", "gauss_d32"): ((256.170240e6 + 8.826368e6) / 2e6, 0.0),
     # 262,144 points, K = 56: 138.378752 MB read + 4.014592 MB written, of which the 56 factor
     # images (69,632 B each, read once from DRAM, then from L2) are the cluster part
     ("labels_x3", "gauss_d128"): ((138.378752e6 + 4.014592e6 - 56 * 69632) / 262144, 69632.0),
@@ -178,6 +180,84 @@ def oracle_rate(name, X, y, prior, opt, budget_s=12.0, max_sweeps=4):
     return n * sweeps / el, dict(n=n, sweeps=sweeps, K=K, seconds=el)
 
 
+def rows_slice(X, a, b):
+    """Points [a, b) in the workload's own form (dense rows, or compressed rows rebased)."""
+    if isinstance(X, tuple):
+        ip, ix, ct, d = X
+        return (ip[a: b + 1] - ip[a], ix[ip[a]: ip[b]], ct[ip[a]: ip[b]], d)
+    return X[a:b]
+
+
+def _oracle_chain_worker(job, barrier, out):
+    """One oracle chain on its own slice of points (a spawned process): set-up, then the
+    timed sweeps once every worker is ready."""
+    import oracle as O
+
+    kind, d, kmax, alpha, kw, Xs, ys, sweeps = job
+    n = ys.size
+    K = int(ys.max()) + 1
+    o = O.Oracle(kind, d, kmax, alpha, burn_out=15, **kw)
+    o.set_data(dense_rows(Xs, n))
+    o.set_state(K, ys % K, (np.arange(n) % 2).astype(np.uint8))
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        o.sweep(1, 1)
+    out.put((n, sweeps, time.perf_counter() - t0))
+
+
+def oracle_rate_cores(name, X, y, prior, opt, budget_s=12.0, sweeps=3, cores=None):
+    """The FP64 oracle as it stands on every host core: one independent chain per core
+    (spawned processes, no threads inside the oracle), each on a contiguous slice of a
+    bounded sample and started from the generating labels; the rate is the points swept by
+    all chains over the slowest chain's time, the chains starting together."""
+    import multiprocessing as mp
+
+    import oracle as O
+
+    cores = cores or len(os.sched_getaffinity(0))
+    kind = O.NIW if prior["kind"] == 0 else O.DIRICHLET
+    kw = {k: v for k, v in prior.items() if k != "kind"}
+    N = n_points(X)
+    K = int(y.max()) + 1
+    # per-point cost from a one-core probe, then a sample of about budget_s per chain
+    n0 = min(N, 1000)
+    o = O.Oracle(kind, n_dims(X), max(64, K), opt["alpha"], burn_out=15, **kw)
+    o.set_data(dense_rows(X, n0))
+    o.set_state(K, y[:n0] % K, (np.arange(n0) % 2).astype(np.uint8))
+    t0 = time.perf_counter()
+    o.sweep(1, 1)
+    per_pt = (time.perf_counter() - t0) / n0
+    del o
+    n = int(min(N, cores * max(64, budget_s / sweeps / max(per_pt, 1e-9))))
+    cuts = np.linspace(0, n, cores + 1).astype(np.int64)
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(cores), ctx.Queue()
+    procs = []
+    for c in range(cores):
+        a, b = int(cuts[c]), int(cuts[c + 1])
+        job = (kind, n_dims(X), max(64, K), opt["alpha"], kw, rows_slice(X, a, b), y[a:b].copy(), sweeps)
+        p = ctx.Process(target=_oracle_chain_worker, args=(job, barrier, out))
+        p.start()
+        procs.append(p)
+    import queue
+
+    res, deadline = [], time.time() + 900
+    while len(res) < cores:
+        try:
+            res.append(out.get(timeout=2))
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in procs) or time.time() > deadline:
+                for p in procs:
+                    p.terminate()
+                raise RuntimeError("an oracle chain process failed")
+    for p in procs:
+        p.join(timeout=60)
+    pts = sum(r[0] * r[1] for r in res)
+    el = max(r[2] for r in res)
+    return pts / el, dict(n=n, sweeps=sweeps, K=K, seconds=el, cores=cores)
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -195,17 +275,19 @@ def run_reference(a):
     info = None
     steps = max(1, min(a.steps, 3))
     for _ in range(steps):
-        v, info = oracle_rate(a.workload, X, y, prior, opt, budget_s=8.0, max_sweeps=2)
+        v, info = oracle_rate_cores(a.workload, X, y, prior, opt, budget_s=8.0, sweeps=2)
         vals.append(v)
     v = float(np.median(vals))
-    sample = "first %d of the N=%d points, %d sweeps per step from the generating labels (K=%d)" % (
-        info["n"], N, info["sweeps"], info["K"])
+    sample = ("first %d of the N=%d points split into %d contiguous slices, one independent oracle chain "
+              "per host core, %d sweeps per step from the generating labels (K=%d)" % (
+                  info["n"], N, info["cores"], info["sweeps"], info["K"]))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "point-sweeps/s", "n_gpus": a.gpus,
            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * N / v, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": a.workload, "N": N, "d": int(n_dims(X)), "sample": sample,
                       "ms_per_step": "extrapolated: N / value, the sample's rate applied to all N points"},
-           "cpu_baseline": {"value": v, "unit": "point-sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": "point-sweeps/s", "cores": info["cores"], "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": v, "unit": "point-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -464,6 +546,10 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # "measured": the pool's own figure from MEASURED_PEAKS.json; "fallback": one earlier
+    # GB300 measurement (1.9 PFLOP/s BF16 burst, 6.8 TB/s copy), used when that file is absent
+    bf16_src = "measured" if "bf16_tflops" in peaks else "fallback"
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     # roofline of the dominant kernel: the label step
     lk = [k for k in prof if k.startswith("labels")]
@@ -476,8 +562,8 @@ def main():
             if a.prec in ("tf32", "bf16", "bf16x3"):
                 peak = bf16_peak * (1.1 / 2.25) if a.prec == "tf32" else bf16_peak
                 roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "peak_source": ("measured bf16 x nominal tf32/bf16 ratio 1.1/2.25" if a.prec == "tf32"
-                                        else "measured bf16 burst")}
+                        "peak_source": (bf16_src + " bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
+                                        if a.prec == "tf32" else bf16_src + " bf16 burst")}
                 if a.prec == "bf16x3":
                     # issued: three BF16 products on the padded dimension plus the one-step -b product
                     dp = 64 if d <= 64 else 128
@@ -492,11 +578,11 @@ def main():
             # compressed rows: 8 B per nonzero (category, count), the row pointer and the labels
             bytes_ = 8 * int(X[0][-1]) + 8 * (N + 1) + 5 * N
             roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "peak_source": "measured copy bandwidth"}
+                    "peak_source": hbm_src + " copy bandwidth"}
         else:
             bytes_ = N * d * (2 if a.prec == "bf16" else 4) + 4 * N
             roof = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "peak_source": "measured copy bandwidth"}
+                    "peak_source": hbm_src + " copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         # DRAM bytes per launch from the ncu capture summarised in profiles/ (taken on a smaller
         # case, scaled by the points and clusters processed); null without a current capture
@@ -585,10 +671,15 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        v, info = oracle_rate(a.workload, X, y, prior, opt)
-        cpu = {"value": v, "unit": "point-sweeps/s", "cores": 1, "kind": "oracle",
-               "sample": "first %d of the N=%d points, %d sweep(s) from the generating labels (K=%d), "
-                         "single-threaded FP64 oracle" % (info["n"], N, info["sweeps"], info["K"])}
+        v1, i1 = oracle_rate(a.workload, X, y, prior, opt)
+        v, info = oracle_rate_cores(a.workload, X, y, prior, opt)
+        cpu = {"value": v, "unit": "point-sweeps/s", "cores": info["cores"], "kind": "oracle",
+               "sample": "first %d of the N=%d points split into %d contiguous slices, one independent FP64 "
+                         "oracle chain per host core, %d sweeps from the generating labels (K=%d)" % (
+                             info["n"], N, info["cores"], info["sweeps"], info["K"]),
+               "single_core": {"value": v1, "cores": 1,
+                               "sample": "first %d of the N=%d points, %d sweep(s) from the generating labels, "
+                                         "one oracle chain" % (i1["n"], N, i1["sweeps"])}}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "point-sweeps/s", "n_gpus": world, "steps": a.steps,

@@ -133,3 +133,33 @@ def test_sharded_chain_refuses_mismatched_shards():
     assert e.value.status == P.DPMM_EINVAL
     for g in (a, b, c, f):
         g.close()
+
+
+def test_compressed_rows_fp32_three_shards_equal_unsharded_chain():
+    """The FP32 compressed-row path (20newsgroups shape, smaller N): statistics are integer
+    counts, which add exactly in any order, so three shards give the very chain of one
+    context: labels, sub-labels, K and counts identical sweep after sweep."""
+    import synth
+
+    N, d = 3_001, 2_000
+    ip, ix, ct, y = synth.newsgroups_like(N=N, d=d, K=6, seed=64, len_lo=20, len_hi=150)
+    cuts = [0, 700, 1_901, N]
+    parts = [(ip[a: b + 1] - ip[a], ix[ip[a]: ip[b]], ct[ip[a]: ip[b]]) for a, b in zip(cuts, cuts[1:])]
+    beta = np.ones(d)
+    gs = _shards(1, d, 16, 5.0, parts, P.PREC_FP32, beta=beta)
+    one = P.DPMM(1, d, 16, 5.0, prec=P.PREC_FP32, burn_out=2, beta=beta)
+    one.set_data_csr(ip, ix, ct)
+    for t in range(15):
+        one.sweep(1, 75)
+        P.dpmm_sweep_sharded([g.h for g in gs], 1, 75)
+        assert all(g.K == one.K for g in gs), t
+        z1, zb1 = one.labels()
+        assert np.array_equal(z1, np.concatenate([g.labels()[0] for g in gs])), t
+        assert np.array_equal(zb1, np.concatenate([g.labels()[1] for g in gs])), t
+        n1, sx1, _ = one.stats()
+        for g in gs:
+            ng, sxg, _ = g.stats()
+            assert np.array_equal(n1, ng) and np.array_equal(sx1, sxg), t
+    assert one.K >= 3
+    for g in gs + [one]:
+        g.close()

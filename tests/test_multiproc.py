@@ -84,3 +84,22 @@ def test_shard_statistics_sum_in_rank_order():
     for r in range(world):
         got = np.frombuffer(res[r], dtype=np.float64).reshape(6, 45)
         assert np.array_equal(got, want)
+
+
+def test_reference_arm_runs_one_oracle_chain_per_core():
+    """`bench.py --impl reference` on a small sample: the oracle as it stands, one chain per
+    host core in spawned processes started together; the JSON line carries its rate and the
+    cores it used."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                        "--workload", "gauss_d2", "--n", "3000"], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
