@@ -39,11 +39,11 @@ METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one
 TRAFFIC_BYTES = {
     # 2 M points, K = 20: 256.170240 MB read + 8.826368 MB written
     ("labels_tc", "gauss_d32"): ((256.170240e6 + 8.826368e6) / 2e6, 0.0),
-    # 262,144 points, K = 56: 138.378752 MB read + 4.014592 MB written, of which the 56 factor
-    # images (69,632 B each, read once from DRAM, then from L2) are the cluster part
-    ("labels_x3", "gauss_d128"): ((138.378752e6 + 4.014592e6 - 56 * 69632) / 262144, 69632.0),
-    # 1 M points: 400.153856 MB read + 6.711808 MB written (the log theta image is a few KB)
-    ("labels_tc_mult", "multinomial"): ((400.153856e6 + 6.711808e6) / 1e6, 0.0),
+    # 262,144 points, K = 56: 143.424256 MB read + written, of which the 56 factor images
+    # (69,632 B each, read once from DRAM, then from L2) are the cluster part
+    ("labels_x3", "gauss_d128"): ((143.424256e6 - 56 * 69632) / 262144, 69632.0),
+    # 1 M points: 406.888161 MB read + written (the log theta image is a few KB)
+    ("labels_tc_mult", "multinomial"): (406.888161e6 / 1e6, 0.0),
 }
 WORKLOADS = {
     "gauss_d32": dict(K_max=64),

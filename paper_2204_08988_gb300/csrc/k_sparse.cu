@@ -16,10 +16,11 @@
 //       (exact: the others' score plus the largest Gumbel is below the best score plus
 //       the smallest), then the two sub-cluster scores of the chosen cluster and z-bar;
 //       mode 1: z-bar only; mode 2: neither.  Every mode adds the point's counts into
-//       the statistics of its sub-cluster with atomic adds of integers (exact, so the
-//       order of the additions does not matter): the FP64 table in its usual layout
-//       and a compact FP32 copy (2 K_max x d) that the split/merge step reads.
+//       the compact count table of its sub-cluster (FP32, 2 K_max x d, read by the
+//       parameter draws and the split/merge step) with atomic adds of integers (exact,
+//       so the order of the additions does not matter).
 //   sparse_zero_kernel  : clears the entries of the 2K sub-clusters those adds touch.
+//   sparse_fill_kernel  : copies the compact counts into the FP64 statistics table.
 //   csr_*               : the compressed rows of a dense input (count, scan, fill).
 #include <math.h>
 
@@ -181,11 +182,17 @@ __device__ inline const double* slot_lt<double>(const SpArgs<double>& a, int s) 
 template <>
 __device__ inline const float* slot_lt<float>(const SpArgs<float>& a, int s) { return a.q_logtheta + (size_t)s * a.d; }
 
+constexpr int SP_WARPS = 8;  // warps per CTA (256 threads)
+constexpr int SP_DEPTH = 16; // table rows in flight per lane in the cluster-score loop
+
 template <typename T, int KQ>
 __global__ void __launch_bounds__(256) sparse_sweep_kernel(SpArgs<T> a) {
     if (a.gate && *a.gate == 0) return;
+    // per warp: the (category, count) pairs of 32 nonzeros, read back as broadcasts
+    __shared__ int2 pairs[SP_WARPS][32];
     const int K = *a.dK;
     const int lane = threadIdx.x & 31;
+    int2* pr = pairs[threadIdx.x >> 5];
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
@@ -198,32 +205,38 @@ __global__ void __launch_bounds__(256) sparse_sweep_kernel(SpArgs<T> a) {
             for (int q = 0; q < KQ; ++q) acc[q] = T(0);
             for (int64_t p0 = r0; p0 < r1; p0 += 32) {
                 const int n = (int)min((int64_t)32, r1 - p0);
-                const int jj = lane < n ? a.idx[p0 + lane] : 0;
-                const T cv = lane < n ? (T)a.val[p0 + lane] : T(0);
-                // increasing category order; four nonzeros' table rows are loaded before
-                // they are added, so that their loads overlap
-                for (int q0 = 0; q0 < n; q0 += 4) {
-                    T lv[4][KQ], cq[4];
+                __syncwarp();
+                if (lane < n) pr[lane] = make_int2(a.idx[p0 + lane], a.val[p0 + lane]);
+                __syncwarp();
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int q = q0 + v < n ? q0 + v : n - 1;
-                        const int j = __shfl_sync(0xffffffffu, jj, q);
-                        cq[v] = __shfl_sync(0xffffffffu, cv, q);
-                        const T* row = a.lt_t + (size_t)j * a.ks;
+                for (int u = 0; u < KQ; ++u) {
+                    if (32 * u >= K) break;
+                    // lane k reads log theta_{k, j_q} (the table is category-major: one
+                    // category's K values are contiguous, so the warp reads one row segment
+                    // per nonzero); SP_DEPTH nonzeros' reads are issued before they are added,
+                    // and the additions run in increasing q: those of a loop over the
+                    // nonzeros one at a time
+                    const int k = lane + 32 * u;
+                    const bool on = k < K;
+                    const T* col = a.lt_t + k;
+                    T sk = acc[u];
+                    for (int q0 = 0; q0 < n; q0 += SP_DEPTH) {
+                        T lv[SP_DEPTH];
+                        int cq[SP_DEPTH];
 #pragma unroll
-                        for (int u = 0; u < KQ; ++u) {
-                            const int k = lane + 32 * u;
-                            lv[v][u] = k < K ? row[k] : T(0);
+                        for (int v = 0; v < SP_DEPTH; ++v) {
+                            const int2 jc = pr[min(q0 + v, n - 1)];
+                            cq[v] = jc.y;
+                            lv[v] = on ? col[(size_t)jc.x * a.ks] : T(0);
                         }
+#pragma unroll
+                        for (int v = 0; v < SP_DEPTH; ++v)
+                            if (q0 + v < n) sk = madd(sk, (T)cq[v], lv[v]);
                     }
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (q0 + v < n)
-#pragma unroll
-                            for (int u = 0; u < KQ; ++u) acc[u] = madd(acc[u], cq[v], lv[v][u]);
+                    acc[u] = sk;
                 }
             }
-            // scores log pi_k + log f(x_i; theta_k) and the exact Gumbel-max
+        // scores log pi_k + log f(x_i; theta_k) and the exact Gumbel-max
             T sc[KQ], best = -INFINITY;
 #pragma unroll
             for (int u = 0; u < KQ; ++u) {
@@ -274,19 +287,45 @@ __global__ void __launch_bounds__(256) sparse_sweep_kernel(SpArgs<T> a) {
             const T* lr = slot_lt<T>(a, 3 * zi + 2);
             T sl = T(0), sr = T(0);
             if (sizeof(T) == 8) {
-                if (lane == 0)
-                    for (int64_t p = r0; p < r1; ++p) {
-                        const T c = (T)a.val[p];
-                        const int j = a.idx[p];
-                        sl = madd(sl, c, ll[j]);
-                        sr = madd(sr, c, lr[j]);
+                // lane q loads its nonzero's two values; every lane then adds them in
+                // increasing q (the order of the loop over all j), so lane 0 holds the sums
+                for (int64_t p0 = r0; p0 < r1; p0 += 32) {
+                    const int n = (int)min((int64_t)32, r1 - p0);
+                    T c = T(0), vl = T(0), vr = T(0);
+                    if (lane < n) {
+                        const int j = a.idx[p0 + lane];
+                        c = (T)a.val[p0 + lane];
+                        vl = ll[j];
+                        vr = lr[j];
                     }
+                    for (int q = 0; q < n; ++q) {
+                        const T cq = __shfl_sync(0xffffffffu, c, q);
+                        sl = madd(sl, cq, __shfl_sync(0xffffffffu, vl, q));
+                        sr = madd(sr, cq, __shfl_sync(0xffffffffu, vr, q));
+                    }
+                }
             } else {
-                for (int64_t p = r0 + lane; p < r1; p += 32) {
-                    const T c = (T)a.val[p];
-                    const int j = a.idx[p];
-                    sl = madd(sl, c, ll[j]);
-                    sr = madd(sr, c, lr[j]);
+                // lane-parallel partial sums, eight nonzeros' loads in flight per lane
+                for (int64_t p0 = r0 + lane; p0 < r1; p0 += 256) {
+                    T c[8], tl[8], tr[8];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const int64_t p = p0 + 32 * v;
+                        c[v] = T(0);
+                        tl[v] = tr[v] = T(0);
+                        if (p < r1) {
+                            const int j = a.idx[p];
+                            c[v] = (T)a.val[p];
+                            tl[v] = ll[j];
+                            tr[v] = lr[j];
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < 8; ++v)
+                        if (p0 + 32 * v < r1) {
+                            sl = madd(sl, c[v], tl[v]);
+                            sr = madd(sr, c[v], tr[v]);
+                        }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     sl += __shfl_xor_sync(0xffffffffu, sl, o);
@@ -305,30 +344,50 @@ __global__ void __launch_bounds__(256) sparse_sweep_kernel(SpArgs<T> a) {
         } else {
             hi = a.zbar[i] ? 1 : 0;
         }
-        // statistics: integer counts, exact in any order
+        // statistics: integer counts, exact in any order, added to the compact table (FP32,
+        // exact up to 2^24 per entry); sparse_fill_kernel copies it into the FP64 table
         const int s = 2 * zi + hi;
-        double* Ss = a.S + (size_t)s * a.L.E;
         float* cs = a.cc + (size_t)s * a.d;
-        for (int64_t p = r0 + lane; p < r1; p += 32) {
-            const int j = a.idx[p];
-            const int v = a.val[p];
-            atomicAdd(Ss + a.L.ent(j, a.d), (double)v);
-            atomicAdd(cs + j, (float)v);
+        for (int64_t p0 = r0 + lane; p0 < r1; p0 += 256) {
+            int j[8], v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t p = p0 + 32 * u;
+                j[u] = p < r1 ? a.idx[p] : -1;
+                v[u] = p < r1 ? a.val[p] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (j[u] >= 0) atomicAdd(cs + j[u], (float)v[u]);
         }
-        if (lane == 0) atomicAdd(Ss + a.L.ent(a.d, a.d), 1.0);
+        if (lane == 0) atomicAdd(a.S + (size_t)s * a.L.E + a.L.ent(a.d, a.d), 1.0);
     }
 }
 
-// the entries the adds above touch, for the 2K sub-clusters
+// the entries the adds above touch, for the 2K sub-clusters (grid: y = sub-cluster slot,
+// 2 K_max rows; x strides over the d + 1 entries of a slot)
 __global__ void sparse_zero_kernel(const int* dK, const int* gate, StatLayout L, double* S, float* cc) {
     if (gate && *gate == 0) return;
-    const int K = *dK, d = L.d;
-    const int64_t total = (int64_t)2 * K * (d + 1);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e / (d + 1)), j = (int)(e % (d + 1));
+    const int s = blockIdx.y, d = L.d;
+    if (s >= 2 * *dK) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= d; j += gridDim.x * blockDim.x) {
         S[(size_t)s * L.E + L.ent(j, d)] = 0.0;
         if (j < d) cc[(size_t)s * d + j] = 0.f;
     }
+}
+
+// the FP64 statistics of the 2K sub-clusters from the compact counts (exact: integers)
+__global__ void sparse_fill_kernel(const int* dK, const int* gate, StatLayout L, double* S, const float* cc) {
+    if (gate && *gate == 0) return;
+    const int s = blockIdx.y, d = L.d;
+    if (s >= 2 * *dK) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+        S[(size_t)s * L.E + L.ent(j, d)] = (double)cc[(size_t)s * d + j];
+}
+
+// x blocks of the zero and fill grids: enough 256-thread blocks to cover a slot's entries
+static dim3 slot_grid(const dpmm_ctx* c) {
+    return dim3((unsigned)std::min(16, (c->d + 1 + 255) / 256), (unsigned)(2 * c->K_max));
 }
 
 // ------------------------------------------------------------------ host
@@ -386,8 +445,9 @@ cudaError_t sparse_prepare(dpmm_ctx* c) {
 }
 
 template <typename T, int KQ>
-static void launch_sp(dpmm_ctx* c, const SpArgs<T>& a, int grid) {
-    sparse_sweep_kernel<T, KQ><<<grid, 256, 0, c->stream>>>(a);
+static cudaError_t launch_sp(dpmm_ctx* c, const SpArgs<T>& a, int grid) {
+    sparse_sweep_kernel<T, KQ><<<grid, 32 * SP_WARPS, 0, c->stream>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -417,11 +477,10 @@ static cudaError_t sparse_sweep_t(dpmm_ctx* c, uint64_t seed, int mode, const in
     a.scores = (mode == 0 || mode == 3) ? c->dbg_scores : nullptr;
     const int grid = (int)std::min<int64_t>((c->N + 7) / 8, 16 * (int64_t)c->num_sms);
     const int kq = (c->K_max + 31) / 32;
-    if (kq <= 1) launch_sp<T, 1>(c, a, grid);
-    else if (kq <= 2) launch_sp<T, 2>(c, a, grid);
-    else if (kq <= 4) launch_sp<T, 4>(c, a, grid);
-    else launch_sp<T, 8>(c, a, grid);
-    return cudaGetLastError();
+    if (kq <= 1) return launch_sp<T, 1>(c, a, grid);
+    if (kq <= 2) return launch_sp<T, 2>(c, a, grid);
+    if (kq <= 4) return launch_sp<T, 4>(c, a, grid);
+    return launch_sp<T, 8>(c, a, grid);
 }
 
 // mode 0: labels, sub-labels and statistics; 1: sub-labels and statistics; 2: statistics;
@@ -431,7 +490,7 @@ cudaError_t launch_sparse(dpmm_ctx* c, uint64_t seed, int mode, const int* gate)
     cudaError_t e = cudaSuccess;
     if (mode != 3) {
         prof_begin(c, "zero_sparse");
-        sparse_zero_kernel<<<4 * c->num_sms, 256, 0, c->stream>>>(c->dK, gate, c->st, c->stats, c->sp_cc);
+        sparse_zero_kernel<<<slot_grid(c), 256, 0, c->stream>>>(c->dK, gate, c->st, c->stats, c->sp_cc);
         prof_end(c, "zero_sparse");
         c->nlaunch += 1;
         e = cudaGetLastError();
@@ -442,7 +501,12 @@ cudaError_t launch_sparse(dpmm_ctx* c, uint64_t seed, int mode, const int* gate)
                                         : sparse_sweep_t<float>(c, seed, mode, gate);
     prof_end(c, name);
     c->nlaunch += 1;
-    return e;
+    if (e != cudaSuccess || mode == 3) return e;
+    prof_begin(c, "fill_sparse");
+    sparse_fill_kernel<<<slot_grid(c), 256, 0, c->stream>>>(c->dK, gate, c->st, c->stats, c->sp_cc);
+    prof_end(c, "fill_sparse");
+    c->nlaunch += 1;
+    return cudaGetLastError();
 }
 
 }  // namespace dpmm

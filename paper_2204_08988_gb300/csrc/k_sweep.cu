@@ -837,12 +837,13 @@ __global__ void __launch_bounds__(WIDE_T, 1) substats_wide_kernel(SubArgs<float>
 }
 
 // Multinomial variant (first-moment statistics only): the point's counts become a
-// float row in shared memory (x, then 1, then zeros); the current run's two
-// sub-cluster log theta vectors are staged in shared memory; each sub-cluster score is
-// a d-long dot product fed by float4 loads; each worker thread owns the counts of one
-// 4-category block for both sub-clusters.  Dynamic shared memory: P x dp rows, P ints
-// (k), P + 2 ints (runs), P bytes (h), then 2 dp + 2 floats (staged parameters), then
-// the flush buffer G x nblk x 8 floats.
+// float row in shared memory (x, then 1, then zeros), each row loaded by one warp in
+// 16-byte pieces, four rows in flight per lane; the current run's two sub-cluster log
+// theta vectors are staged in shared memory; each sub-cluster score is a d-long dot
+// product fed by float4 loads; each worker thread owns the counts of one 4-category
+// block for both sub-clusters.  Dynamic shared memory: P x dp rows, P ints (k), P + 2
+// ints (runs), P ints (point indices), P bytes (h), then 2 dp + 2 floats (staged
+// parameters), then the flush buffer G x nblk x 8 floats.
 template <typename XT>
 __global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
     if (a.gate && *a.gate == 0) return;
@@ -852,8 +853,9 @@ __global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
     int* kq = (int*)(xs + (size_t)P * dp);
     int* runs = kq + P;
     int* nruns = runs + P + 1;
-    unsigned char* hq = (unsigned char*)(nruns + 1);
-    float* lt0 = (float*)(smraw + (((size_t)P * dp * 4 + (2 * P + 2) * sizeof(int) + P + 15) / 16) * 16);
+    int* iq = nruns + 1;
+    unsigned char* hq = (unsigned char*)(iq + P);
+    float* lt0 = (float*)(smraw + (((size_t)P * dp * 4 + (3 * P + 2) * sizeof(int) + P + 15) / 16) * 16);
     float* lt1 = lt0 + dp;
     float* cc = lt1 + dp;
     float* red = (float*)(((uintptr_t)(cc + 2) + 15) & ~(uintptr_t)15);
@@ -906,27 +908,50 @@ __global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
         if (tid < np) {
             i = a.idx[base + tid];
             kq[tid] = a.z[i];
-            float* xr = xs + (size_t)tid * dp;
+            iq[tid] = i;
+        }
+        __syncthreads();
+        {
+            const int lane = tid & 31, nwarp = nt >> 5;
             if constexpr (sizeof(XT) == 2) {  // 16-byte loads: 8 BF16 counts (rows are 16-byte aligned)
-                const uint4* src = (const uint4*)(X + (int64_t)i * a.xs);
-                const int nfull = d / 8;  // whole 8-count chunks inside the row's d columns
-                for (int j8 = 0; j8 < nfull; ++j8) {
-                    const uint4 q = src[j8];
-                    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
-                    float f[8];
+                const int nfull = d / 8;      // whole 8-count chunks inside the row's d columns
+                for (int q0 = tid >> 5; q0 < np; q0 += 4 * nwarp) {
+                    for (int c0 = 0; c0 < nfull; c0 += 32) {
+                        const int c8 = c0 + lane;
+                        uint4 v[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        f[2 * u] = __uint_as_float(wv[u] << 16);
-                        f[2 * u + 1] = __uint_as_float(wv[u] & 0xFFFF0000u);
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q0 + u * nwarp;
+                            if (q < np && c8 < nfull) v[u] = ((const uint4*)(X + (int64_t)iq[q] * a.xs))[c8];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q0 + u * nwarp;
+                            if (q < np && c8 < nfull) {
+                                const uint32_t wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                                float f[8];
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) {
+                                    f[2 * w] = __uint_as_float(wv[w] << 16);
+                                    f[2 * w + 1] = __uint_as_float(wv[w] & 0xFFFF0000u);
+                                }
+                                float* xr = xs + (size_t)q * dp + 8 * c8;
+                                *(float4*)xr = make_float4(f[0], f[1], f[2], f[3]);
+                                *(float4*)(xr + 4) = make_float4(f[4], f[5], f[6], f[7]);
+                            }
+                        }
                     }
-                    *(float4*)(xr + 8 * j8) = make_float4(f[0], f[1], f[2], f[3]);
-                    *(float4*)(xr + 8 * j8 + 4) = make_float4(f[4], f[5], f[6], f[7]);
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u * nwarp;
+                        if (q >= np) break;
+                        for (int j = 8 * nfull + lane; j < dp; j += 32)
+                            xs[(size_t)q * dp + j] = j < d ? ldx<float, XT>(X + (int64_t)iq[q] * a.xs + j) : (j == d ? 1.f : 0.f);
+                    }
                 }
-                for (int j = 8 * nfull; j < dp; ++j)
-                    xr[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : (j == d ? 1.f : 0.f);
             } else {
-                for (int j = 0; j < dp; ++j)
-                    xr[j] = j < d ? ldx<float, XT>(X + (int64_t)i * a.xs + j) : (j == d ? 1.f : 0.f);
+                for (int q = tid >> 5; q < np; q += nwarp)
+                    for (int j = lane; j < dp; j += 32)
+                        xs[(size_t)q * dp + j] = j < d ? ldx<float, XT>(X + (int64_t)iq[q] * a.xs + j) : (j == d ? 1.f : 0.f);
             }
         }
         __syncthreads();
@@ -1215,7 +1240,7 @@ static cudaError_t substats_mult_t(dpmm_ctx* c, uint64_t seed, int draw, const i
     int P = (int)((96 * 1024) / ((size_t)L.dp * 4));
     P = std::max(32, std::min(256, P / 32 * 32));
     const int G = std::max(1, 256 / L.nblk);
-    size_t head = (size_t)P * L.dp * 4 + (2 * (size_t)P + 2) * sizeof(int) + P;
+    size_t head = (size_t)P * L.dp * 4 + (3 * (size_t)P + 2) * sizeof(int) + P;
     head = (head + 15) / 16 * 16;
     const size_t smem = head + ((size_t)2 * L.dp + 2) * 4 + 16 + (size_t)G * L.nblk * 8 * 4;
     SubArgs<float> a;
