@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 sys.path.insert(0, os.path.join(ROOT, "tests"))  # synth.py: the seeded input generators
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3, "bf16x3": 4}
+KERNEL = {"tensor": 0, "cuda_core": 1, "auto": 2}
 DTYPE = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16", "fp32": "f32", "bf16x3": "bf16x3"}
 METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one GB300"
 # ncu DRAM bytes (read + write) per launch of the label kernel, from one capture of it on a
@@ -74,6 +75,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain arm on the same state")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--breakdown", action="store_true", help="add a per-kernel time table from a separate profiled pass")
+    ap.add_argument("--kernel", default=None, choices=["tensor", "cuda_core", "auto"],
+                    help="label-step kernel (dpmm_set_kernel); default: auto for the batched workload, else tensor")
     ap.add_argument("--init-truth", action="store_true",
                     help="start the chain from the generating labels instead of a burn-in from K=1 (profiling runs)")
     return ap.parse_args()
@@ -362,6 +365,7 @@ def main_batched(a):
         s = torch.cuda.Stream()
         g = P.DPMM(0, d, K_max, 10.0, prec=PREC[batch_prec(d)], init_K=1, burn_out=15, stream=s.cuda_stream,
                    kappa0=1.0, m0=np.zeros(d), nu0=float(d + 3), psi0=np.eye(d))
+        g.set_kernel(KERNEL[a.kernel or "auto"])
         g.set_data(X)
         g.set_problem(p)
         if a.init_truth:
@@ -440,6 +444,9 @@ def main_batched(a):
                       "K_max": K_max, "K_timed_mean": float(np.mean(Ks)), "burnin_sweeps": burn,
                       "init": "generating labels" if a.init_truth else "K=1", "parallelism": "1gpu, one stream per problem",
                       "device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
+                      "label_kernel": {"requested": a.kernel or "auto",
+                                       "tensor": sum(g.kernel()[0] == 0 for g in chains),
+                                       "cuda_core": sum(g.kernel()[0] == 1 for g in chains)},
                       "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
            "roofline": roof, "cpu_baseline": None, "e2e": None, "clocks": clk.summary(), "gpu_launches": None,
            "step_ms": step_ms}
@@ -487,6 +494,7 @@ def main():
     stream = torch.cuda.Stream()
     g = P.DPMM(kind, d, K_max, opt["alpha"], prec=PREC[a.prec], init_K=1, burn_out=15,
                stream=stream.cuda_stream, **kw)
+    g.set_kernel(KERNEL[a.kernel or "tensor"])
     Xd = None
     if csr:
         g.set_data_csr(*X[:3])
@@ -687,6 +695,7 @@ def main():
                "vs_baseline": None, "dtype": DTYPE[a.prec], "data": "synthetic",
                "config": {"workload": a.workload, "N": N, "d": d, "K_start": K0, "K_timed": Ks, "K_max": K_max,
                           "prec": a.prec, "burnin_sweeps": a.burnin, "init": "generating labels" if a.init_truth else "K=1", "parallelism": "replicas" if world > 1 else "1gpu",
+                          "label_kernel": ["tensor", "cuda_core"][g.kernel()[0]],
                           "l2": "flushed by a 256 MiB write between timed steps (untimed)"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                "gpu_launches": gpu_launches, "launch_floor": floor, "fp64_plain": fp64, "step_ms": step_ms,

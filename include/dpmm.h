@@ -236,6 +236,30 @@ dpmm_status dpmm_set_state(dpmm_ctx* ctx, int K, const int32_t* z, const uint8_t
  * step uses the parameters last drawn or set by dpmm_set_params. */
 dpmm_status dpmm_set_step_mask(dpmm_ctx* ctx, unsigned mask);
 
+/* Label-step kernel selection (Sec. 4.2, "Two kernels for optimization": the package
+ * picks at run time between a hand-written kernel and a library matrix product, from d,
+ * N and the GPU).  Here the two label-step kernels of a precision with tensor cores
+ * (TF32 and BF16X3 Gaussian, BF16 multinomial) are the tcgen05 kernel and the FP32
+ * CUDA-core kernel (the same Gumbel-max draws, scores in FP32 instead of TF32/BF16).
+ * choice: DPMM_KERNEL_TENSOR (the default) or DPMM_KERNEL_CUDA_CORE pins one;
+ * DPMM_KERNEL_AUTO times both at the next sweep that runs eagerly (the first after
+ * this call or after new data): each runs three times on the context's data and
+ * stream (CUDA events, the first run a warm-up), the faster is kept for the captured
+ * sweep graph, and the choice is cached for the process under (device, prior kind,
+ * precision, d, floor(log2 N), K_max), so a context with the same key takes it without
+ * timing.  The label step is deterministic given the parameters and the sweep counter,
+ * so the timing runs leave the chain as if the chosen kernel had run alone; which
+ * kernel wins may differ between GPUs and runs, so pin one where bit-reproducibility
+ * across machines matters.  Precisions without a tensor-core kernel keep their only
+ * kernel.  Drops the captured graph.  Errors: DPMM_EINVAL for an unknown choice.
+ * dpmm_get_kernel: *in_use = the kernel the label step runs (DPMM_KERNEL_TENSOR or
+ * DPMM_KERNEL_CUDA_CORE); *ms_tensor, *ms_cuda_core = the timed milliseconds per
+ * label step (the cached figures for a cache hit), or -1 when not timed; any output
+ * may be NULL. */
+typedef enum { DPMM_KERNEL_TENSOR = 0, DPMM_KERNEL_CUDA_CORE = 1, DPMM_KERNEL_AUTO = 2 } dpmm_kernel;
+dpmm_status dpmm_set_kernel(dpmm_ctx* ctx, int choice);
+dpmm_status dpmm_get_kernel(dpmm_ctx* ctx, int* in_use, float* ms_tensor, float* ms_cuda_core);
+
 /* Parameters of the 3K slots (host arrays), in the data's original coordinates.
  * Gaussian: log weight logw[3K], mean mu[3K x d], precision factor W[3K x d x d]
  * (upper-triangular, Lambda = W W^T) and logdetW[3K] = sum_j log W_jj.

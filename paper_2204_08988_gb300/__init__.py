@@ -24,6 +24,7 @@ DPMM_OK, DPMM_EINVAL, DPMM_ENOMEM, DPMM_ECUDA, DPMM_ESTATE, DPMM_ENUMERIC, DPMM_
 PRIOR_NIW, PRIOR_DIRICHLET = 0, 1
 F64, F32, BF16, I32 = 0, 1, 2, 3
 PREC_FP64_PLAIN, PREC_TF32, PREC_BF16, PREC_FP32, PREC_BF16X3 = 0, 1, 2, 3, 4
+KERNEL_TENSOR, KERNEL_CUDA_CORE, KERNEL_AUTO = 0, 1, 2
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENUMERIC", 6: "ETIMEOUT"}
 
 # every symbol include/dpmm.h declares
@@ -33,7 +34,8 @@ EXPORTS = [
     "dpmm_set_state", "dpmm_set_step_mask", "dpmm_set_params", "dpmm_get_params", "dpmm_set_iter",
     "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
     "dpmm_sweep_batch", "dpmm_check_wait_timeout", "dpmm_checkpoint_size", "dpmm_save_checkpoint",
-    "dpmm_load_checkpoint", "dpmm_set_data_csr", "dpmm_set_shard", "dpmm_sweep_sharded",
+    "dpmm_load_checkpoint", "dpmm_set_data_csr", "dpmm_set_shard", "dpmm_sweep_sharded", "dpmm_set_kernel",
+    "dpmm_get_kernel",
 ]
 
 
@@ -92,6 +94,8 @@ def load():
             "dpmm_set_data_csr": ([vp, vp, vp, vp, i64], i32),
             "dpmm_set_shard": ([vp, i64], i32),
             "dpmm_sweep_sharded": ([vp, i32, i32, u64], i32),
+            "dpmm_set_kernel": ([vp, i32], i32),
+            "dpmm_get_kernel": ([vp, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -203,6 +207,17 @@ def dpmm_set_state(h, K, z, zbar):
 
 def dpmm_set_step_mask(h, mask):
     _check(h, load().dpmm_set_step_mask(h, int(mask)))
+
+
+def dpmm_set_kernel(h, choice):
+    _check(h, load().dpmm_set_kernel(h, int(choice)))
+
+
+def dpmm_get_kernel(h):
+    """(kernel in use, timed ms on the tensor cores, timed ms on the CUDA cores); -1: not timed."""
+    use, mt, mc = C.c_int32(), C.c_float(), C.c_float()
+    _check(h, load().dpmm_get_kernel(h, C.byref(use), C.byref(mt), C.byref(mc)))
+    return use.value, mt.value, mc.value
 
 
 def dpmm_set_iter(h, it):
@@ -406,6 +421,12 @@ class DPMM:
 
     def set_mask(self, mask):
         dpmm_set_step_mask(self.h, mask)
+
+    def set_kernel(self, choice):
+        dpmm_set_kernel(self.h, choice)
+
+    def kernel(self):
+        return dpmm_get_kernel(self.h)
 
     def set_iter(self, it):
         dpmm_set_iter(self.h, it)

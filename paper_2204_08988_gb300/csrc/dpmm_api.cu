@@ -6,7 +6,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -231,12 +234,21 @@ static void drop_graph(dpmm_ctx* c) {
     c->graph = nullptr;
 }
 
+// new data: an automatic label-kernel choice is made again for the new size
+static void rearm_kernel_choice(dpmm_ctx* c) {
+    if (c->kchoice != DPMM_KERNEL_AUTO) return;
+    c->ktune = true;
+    c->kuse = 0;
+    c->kms[0] = c->kms[1] = -1.f;
+}
+
 // ------------------------------------------------------------------ compressed rows
 // what every data set of the compressed-row path has in common: labels, the row
 // pointer, the prior in storage coordinates (beta), the sweep counter reset
 static dpmm_status sparse_alloc(dpmm_ctx* c, int64_t N) {
     free_data(c);
     c->N = N;
+    rearm_kernel_choice(c);
     c->T_tiles = (int)((N + 255) / 256);
     c->Gr = 1;
     bool ok = true;
@@ -367,7 +379,9 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         delete c;
         return DPMM_EINVAL;
     }
-    c->G2 = 2 * c->num_sms;
+    // multinomial statistics are first moments only (small records): four ranges per SM,
+    // so that four CTAs per SM hide the latency of the gathered rows
+    c->G2 = (c->kind == DPMM_PRIOR_DIRICHLET ? 4 : 2) * c->num_sms;
     const size_t S = 3 * (size_t)K_max;
     bool ok = true;
     auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
@@ -494,6 +508,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     CK(c, cudaStreamSynchronize(c->stream));
     free_data(c);
     c->N = N;
+    rearm_kernel_choice(c);
     c->in_dt = dt;
     const int d = c->d;
     if (c->prec == DPMM_PREC_FP64_PLAIN) {
@@ -639,9 +654,78 @@ static dpmm_status init_chain(dpmm_ctx* c, uint64_t seed) {
 // context's points; (b) splits, merges, relabelling and the recount of the statistics
 // when anything changed; (c) the sweep index.  A point-sharded sweep exchanges the
 // statistics after (a) and after (b).
+// ---- label-step kernel selection (Sec. 4.2: two kernels, chosen at run time)
+static bool has_tc_labels(const dpmm_ctx* c) { return !c->sparse && (tc_supported(c) || x3_supported(c)); }
+
+// the label step on the tensor cores (which = 0) or the CUDA cores (which = 1)
+static cudaError_t label_step(dpmm_ctx* c, uint64_t seed, int which) {
+    if (which == 1 || !has_tc_labels(c)) return launch_labels_simt(c, seed);
+    return c->prec == DPMM_PREC_BF16X3 ? launch_labels_x3(c, seed) : launch_labels_tc(c, seed);
+}
+
+struct KernelKey {
+    int device, kind, prec, d, logn, K_max;
+    bool operator<(const KernelKey& o) const {
+        return std::tie(device, kind, prec, d, logn, K_max) < std::tie(o.device, o.kind, o.prec, o.d, o.logn, o.K_max);
+    }
+};
+struct KernelPick {
+    int use;
+    float ms[2];
+};
+static std::mutex g_kcache_mu;
+static std::map<KernelKey, KernelPick> g_kcache;
+
+static KernelKey kernel_key(const dpmm_ctx* c) {
+    int logn = 0;
+    while ((int64_t(2) << logn) <= c->N) ++logn;
+    return KernelKey{c->device, c->kind, c->prec, c->d, logn, c->K_max};
+}
+
+// Runs on an eager sweep only (it synchronises): both label kernels three times each on
+// this sweep's parameters, the first run of each a warm-up; keeps the faster.  The label
+// step is a deterministic function of the parameters and the sweep counter, and the
+// chosen kernel runs once more right after, so the chain is that of the chosen kernel.
+static cudaError_t tune_labels(dpmm_ctx* c, uint64_t seed) {
+    c->ktune = false;
+    if (!has_tc_labels(c)) return cudaSuccess;  // one kernel: nothing to choose
+    const KernelKey key = kernel_key(c);
+    {
+        std::lock_guard<std::mutex> lk(g_kcache_mu);
+        auto it = g_kcache.find(key);
+        if (it != g_kcache.end()) {
+            c->kuse = it->second.use;
+            c->kms[0] = it->second.ms[0];
+            c->kms[1] = it->second.ms[1];
+            return cudaSuccess;
+        }
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    float best[2] = {1e30f, 1e30f};
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v)
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(ev[0], c->stream);
+            if (e == cudaSuccess) e = label_step(c, seed, v);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (e == cudaSuccess && r > 0) best[v] = std::min(best[v], ms);
+        }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return e;
+    c->kms[0] = best[0];
+    c->kms[1] = best[1];
+    c->kuse = best[1] < best[0] ? 1 : 0;
+    std::lock_guard<std::mutex> lk(g_kcache_mu);
+    g_kcache[key] = KernelPick{c->kuse, {best[0], best[1]}};
+    return cudaSuccess;
+}
+
 static cudaError_t sweep_phase_a(dpmm_ctx* c, uint64_t seed) {
-    const bool tc = (c->prec == DPMM_PREC_TF32 || c->prec == DPMM_PREC_BF16);
-    const bool x3 = c->prec == DPMM_PREC_BF16X3;
     cudaError_t e = cudaSuccess;
     if (c->step_mask & 1u) {
         if ((e = launch_weights(c, seed)) != cudaSuccess) return e;
@@ -651,8 +735,12 @@ static cudaError_t sweep_phase_a(dpmm_ctx* c, uint64_t seed) {
     if ((c->step_mask & 2u) && c->sparse) {
         if ((e = launch_sparse(c, seed, 0, nullptr)) != cudaSuccess) return e;
     } else if (c->step_mask & 2u) {
-        e = x3 ? launch_labels_x3(c, seed) : tc ? launch_labels_tc(c, seed) : launch_labels_simt(c, seed);
-        if (e != cudaSuccess) return e;
+        if (c->ktune) {  // never pending during graph capture: set only by calls that drop the graph
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if ((e = cudaStreamIsCapturing(c->stream, &cs)) != cudaSuccess) return e;
+            if (cs == cudaStreamCaptureStatusNone && (e = tune_labels(c, seed)) != cudaSuccess) return e;
+        }
+        if ((e = label_step(c, seed, c->kuse)) != cudaSuccess) return e;
         if ((e = launch_sort(c)) != cudaSuccess) return e;
         if ((e = launch_substats(c, seed, 1)) != cudaSuccess) return e;
         if ((e = launch_combine(c)) != cudaSuccess) return e;
@@ -1052,6 +1140,27 @@ dpmm_status dpmm_set_state(dpmm_ctx* c, int K, const int32_t* z, const uint8_t* 
     CK(c, cudaStreamSynchronize(c->stream));
     c->initialized = true;
     return check_derr(c);
+}
+
+dpmm_status dpmm_set_kernel(dpmm_ctx* c, int choice) {
+    if (!c) return DPMM_EINVAL;
+    if (choice < DPMM_KERNEL_TENSOR || choice > DPMM_KERNEL_AUTO)
+        return fail(c, DPMM_EINVAL, "choice: DPMM_KERNEL_TENSOR, DPMM_KERNEL_CUDA_CORE or DPMM_KERNEL_AUTO");
+    drop_graph(c);
+    c->kchoice = choice;
+    c->kuse = choice == DPMM_KERNEL_CUDA_CORE ? 1 : 0;
+    c->ktune = choice == DPMM_KERNEL_AUTO;
+    c->kms[0] = c->kms[1] = -1.f;
+    return DPMM_OK;
+}
+
+dpmm_status dpmm_get_kernel(dpmm_ctx* c, int* in_use, float* ms_tensor, float* ms_cuda_core) {
+    if (!c) return DPMM_EINVAL;
+    const bool tc = has_tc_labels(c);
+    if (in_use) *in_use = (tc && c->kuse == 0) ? DPMM_KERNEL_TENSOR : DPMM_KERNEL_CUDA_CORE;
+    if (ms_tensor) *ms_tensor = c->kms[0];
+    if (ms_cuda_core) *ms_cuda_core = c->kms[1];
+    return DPMM_OK;
 }
 
 dpmm_status dpmm_set_step_mask(dpmm_ctx* c, unsigned mask) {

@@ -317,6 +317,13 @@ struct dpmm_ctx {
     bool use_graph = true;
     int64_t graph_kernels = 0;  // kernel nodes of the captured sweep
 
+    // label-step kernel choice (Sec. 4.2): requested choice (dpmm_kernel), kernel in
+    // force (0 tensor cores where the precision has them, 1 CUDA cores), a timing
+    // pending for the next eager sweep, and the timed ms (tensor, CUDA cores; -1: none)
+    int kchoice = 0, kuse = 0;
+    bool ktune = false;
+    float kms[2] = {-1.f, -1.f};
+
     // profiling: 0 off, 1 every kernel, 2 only the label kernel
     int profiling = 0;
     int64_t nlaunch = 0;  // kernels launched since the last dpmm_profile call

@@ -1237,8 +1237,9 @@ static cudaError_t substats_f32_t(dpmm_ctx* c, uint64_t seed, int draw, const in
 template <typename XT>
 static cudaError_t substats_mult_t(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
     const StatLayout& L = c->st;
-    int P = (int)((96 * 1024) / ((size_t)L.dp * 4));
-    P = std::max(32, std::min(256, P / 32 * 32));
+    // tiles of about 40 KB of rows: four CTAs per SM
+    int P = (int)((40 * 1024) / ((size_t)L.dp * 4));
+    P = std::max(32, std::min(256, P / 16 * 16));
     const int G = std::max(1, 256 / L.nblk);
     size_t head = (size_t)P * L.dp * 4 + (3 * (size_t)P + 2) * sizeof(int) + P;
     head = (head + 15) / 16 * 16;
