@@ -136,6 +136,20 @@ dpmm_status dpmm_set_data_csr(dpmm_ctx* ctx, const int64_t* indptr, const int32_
  * the next synchronising call (e.g. dpmm_get_labels). */
 dpmm_status dpmm_update_data(dpmm_ctx* ctx, const void* X, dpmm_dtype dt, int on_device);
 
+/* Stage the values of the next sweep's data (same N, d, dtype; host memory), for
+ * streaming inputs: Sec. 4.5 keeps the data on the device, and new values must cross
+ * the CPU-GPU link every step.  The copy runs on a copy-engine stream of the context's
+ * own, so it overlaps the sweep in flight; the next dpmm_sweep (or dpmm_sweep_sharded)
+ * waits for it and converts the staged values into the data before its first kernel,
+ * exactly as dpmm_update_data would have.  A second call before that sweep replaces the
+ * staged values; dpmm_update_data and dpmm_set_data discard them.  The device staging
+ * buffer (the input's size) stays with the context until dpmm_destroy.  Page-locked
+ * host memory is copied asynchronously and must keep its values until the next
+ * synchronising call; pageable memory is copied before the call returns.  Not for
+ * compressed rows.  Errors: DPMM_ESTATE without data, DPMM_EINVAL (NULL X, another
+ * dtype, compressed rows), DPMM_ENOMEM (staging buffer). */
+dpmm_status dpmm_stage_data(dpmm_ctx* ctx, const void* X, dpmm_dtype dt);
+
 /* Run `iters` sweeps (Sec. 4.1) with Philox key `seed`.  The sweep counter
  * persists across calls, so two calls of 5 equal one call of 10.  Asynchronous on
  * the context's stream. */

@@ -35,7 +35,7 @@ EXPORTS = [
     "dpmm_profile", "dpmm_get_profile", "dpmm_suffstats_noalloc", "dpmm_label_scores", "dpmm_set_problem",
     "dpmm_sweep_batch", "dpmm_check_wait_timeout", "dpmm_checkpoint_size", "dpmm_save_checkpoint",
     "dpmm_load_checkpoint", "dpmm_set_data_csr", "dpmm_set_shard", "dpmm_sweep_sharded", "dpmm_set_kernel",
-    "dpmm_get_kernel",
+    "dpmm_get_kernel", "dpmm_stage_data",
 ]
 
 
@@ -95,6 +95,7 @@ def load():
             "dpmm_set_shard": ([vp, i64], i32),
             "dpmm_sweep_sharded": ([vp, i32, i32, u64], i32),
             "dpmm_set_kernel": ([vp, i32], i32),
+            "dpmm_stage_data": ([vp, vp, i32], i32),
             "dpmm_get_kernel": ([vp, C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(C.c_float)], i32),
         }
         for name, (args, res) in sig.items():
@@ -162,6 +163,14 @@ def dpmm_set_data_csr(h, indptr, indices, counts):
 def dpmm_update_data(h, X):
     ptr, code, dev = _array_arg(X)
     _check(h, load().dpmm_update_data(h, ptr, code, dev))
+
+
+def dpmm_stage_data(h, X):
+    """Stage host values for the next sweep (copied while the current sweep runs)."""
+    ptr, code, dev = _array_arg(X)
+    if dev:
+        raise ValueError("dpmm_stage_data takes host memory")
+    _check(h, load().dpmm_stage_data(h, ptr, code))
 
 
 def dpmm_sweep(h, iters, seed):
@@ -388,6 +397,9 @@ class DPMM:
 
     def update_data(self, X):
         dpmm_update_data(self.h, X)
+
+    def stage_data(self, X):
+        dpmm_stage_data(self.h, X)
 
     def set_data_csr(self, indptr, indices, counts):
         dpmm_set_data_csr(self.h, indptr, indices, counts)

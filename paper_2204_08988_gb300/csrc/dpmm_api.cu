@@ -471,8 +471,13 @@ void dpmm_destroy(dpmm_ctx* c) {
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
                   c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg,
-                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch, c->p_b};
+                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch, c->p_b,
+                  c->stage};
+    if (c->cstream) cudaStreamSynchronize(c->cstream);
     for (void* p : ps) dfree(p);
+    if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+    if (c->ev_free) cudaEventDestroy(c->ev_free);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
     for (auto& p : c->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
     drop_graph(c);
@@ -501,6 +506,7 @@ dpmm_status dpmm_set_options(dpmm_ctx* c, dpmm_prec prec, int init_K, int burn_o
 
 dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, int on_device) {
     if (!c) return DPMM_EINVAL;
+    c->staged = false;
     drop_graph(c);
     if (!X || N < 1 || N > 0x7FFFFFFFLL) return fail(c, DPMM_EINVAL, "need 1 <= N < 2^31 and a non-NULL X");
     if (dt < DPMM_F64 || dt > DPMM_I32) return fail(c, DPMM_EINVAL, "unknown dtype");
@@ -572,6 +578,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
 
 dpmm_status dpmm_update_data(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_device) {
     if (!c) return DPMM_EINVAL;
+    c->staged = false;  // values staged before are superseded
     if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
     if (!X || dt != c->in_dt) return fail(c, DPMM_EINVAL, "same dtype as dpmm_set_data required");
     if (c->sparse) {  // new compressed rows (their length changes): the captured sweep refers to the old ones
@@ -579,6 +586,51 @@ dpmm_status dpmm_update_data(dpmm_ctx* c, const void* X, dpmm_dtype dt, int on_d
         return sparse_upload(c, X, dt, on_device);
     }
     return upload(c, X, dt, on_device, false);
+}
+
+// ---- staged input: the copy of the next sweep's values overlaps the current sweep
+dpmm_status dpmm_stage_data(dpmm_ctx* c, const void* X, dpmm_dtype dt) {
+    if (!c) return DPMM_EINVAL;
+    if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
+    if (c->sparse) return fail(c, DPMM_EINVAL, "compressed rows take new data through dpmm_set_data_csr");
+    if (!X || dt != c->in_dt) return fail(c, DPMM_EINVAL, "same dtype as dpmm_set_data required");
+    const size_t bytes = (size_t)c->N * c->d * dt_size(dt);
+    if (!c->cstream) CK(c, cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+    if (!c->ev_copied) CK(c, cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+    if (!c->ev_free) {
+        CK(c, cudaEventCreateWithFlags(&c->ev_free, cudaEventDisableTiming));
+        CK(c, cudaEventRecord(c->ev_free, c->stream));
+    }
+    if (c->stage_bytes < bytes) {
+        CK(c, cudaStreamSynchronize(c->cstream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        dfree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+        if (cudaMalloc(&c->stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->stage = nullptr;
+            return fail(c, DPMM_ENOMEM, "device allocation for the staging buffer failed");
+        }
+        c->stage_bytes = bytes;
+    }
+    // the values staged before must have been taken by the sweep that converts them
+    CK(c, cudaStreamWaitEvent(c->cstream, c->ev_free, 0));
+    CK(c, cudaMemcpyAsync(c->stage, X, bytes, cudaMemcpyHostToDevice, c->cstream));
+    CK(c, cudaEventRecord(c->ev_copied, c->cstream));
+    c->staged = true;
+    return DPMM_OK;
+}
+
+// At the start of a sweep: staged values replace the data (as dpmm_update_data would).
+static dpmm_status take_staged(dpmm_ctx* c) {
+    if (!c->staged) return DPMM_OK;
+    c->staged = false;
+    CK(c, cudaStreamWaitEvent(c->stream, c->ev_copied, 0));
+    const dpmm_status s = upload(c, c->stage, c->in_dt, 1, false);
+    if (s != DPMM_OK) return s;
+    CK(c, cudaEventRecord(c->ev_free, c->stream));
+    return DPMM_OK;
 }
 
 dpmm_status dpmm_set_data_csr(dpmm_ctx* c, const int64_t* indptr, const int32_t* indices, const int32_t* counts,
@@ -765,6 +817,10 @@ dpmm_status dpmm_sweep(dpmm_ctx* c, int iters, uint64_t seed) {
     if (!c) return DPMM_EINVAL;
     if (!c->X) return fail(c, DPMM_ESTATE, "dpmm_set_data first");
     if (iters < 0) return fail(c, DPMM_EINVAL, "iters must be >= 0");
+    {
+        const dpmm_status s = take_staged(c);
+        if (s != DPMM_OK) return s;
+    }
     if (!c->initialized) {
         dpmm_status s = init_chain(c, seed);
         if (s != DPMM_OK) return s;
@@ -1001,6 +1057,8 @@ dpmm_status dpmm_sweep_sharded(dpmm_ctx* const* sh, int G, int iters, uint64_t s
         if (!sh[s]) return DPMM_EINVAL;
     dpmm_status st = shard_check(sh, G);
     if (st != DPMM_OK) return st;
+    for (int s = 0; s < G; ++s)
+        if ((st = take_staged(sh[s])) != DPMM_OK) return st;
     dpmm_ctx* c0 = sh[0];
     auto phase = [&](auto&& f) -> dpmm_status {
         for (int s = 0; s < G; ++s) {

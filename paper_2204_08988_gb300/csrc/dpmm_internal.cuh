@@ -234,6 +234,13 @@ struct dpmm_ctx {
     double* center = nullptr;  // device, d: data were stored as x - center
     std::vector<double> h_center;
     dpmm_dtype in_dt = DPMM_F64;
+    // staged input (dpmm_stage_data): the next sweep's values, copied on a copy stream of
+    // their own while the current sweep runs, converted at the start of the next sweep
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_copied = nullptr, ev_free = nullptr;
+    bool staged = false;
 
     // chain state
     int32_t* z = nullptr;

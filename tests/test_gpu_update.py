@@ -68,3 +68,46 @@ def test_update_data_sources_agree(prec, d):
     scale2 = np.abs(sxx).max() + 1.0
     assert np.abs(sx0 - sx).max() <= rtol * scale1
     assert np.abs(sxx0 - sxx).max() <= rtol * scale2
+
+
+@pytest.mark.parametrize("prec,d", [("tf32", 32), ("fp64", 5), ("bf16x3", 64)])
+def test_staged_data_give_the_chain_of_updated_data(prec, d):
+    """dpmm_stage_data (the copy overlaps the sweep in flight; the next sweep takes the
+    values) gives, sweep for sweep, the chain of dpmm_update_data called right before that
+    sweep: same labels, sub-labels, K and statistics, from page-locked and pageable
+    sources, with a second staging call replacing the first."""
+    import torch
+
+    import synth
+
+    pr = {"tf32": P.PREC_TF32, "fp64": P.PREC_FP64_PLAIN, "bf16x3": P.PREC_BF16X3}[prec]
+    dt = np.float64 if prec == "fp64" else np.float32
+    N, K = 40_001, 4
+    Xs = [synth.gaussian_mixture(N, d, K, 6.0, seed=10 + t, dtype=dt)[0] for t in range(4)]
+    y = synth.gaussian_mixture(N, d, K, 6.0, seed=10, dtype=dt)[1]
+    zb = (np.arange(N) % 2).astype(np.uint8)
+    pinned = [torch.from_numpy(x).pin_memory() for x in Xs]
+
+    def chain(staged):
+        g = P.DPMM(0, d, 16, 3.0, prec=pr, burn_out=2, **_prior(d))
+        g.set_data(Xs[0])
+        g.set_state(K, y, zb)
+        g.sweep(2, 9)
+        out = []
+        for t in (1, 2, 3):
+            src = pinned[t] if t != 2 else Xs[t]  # page-locked and pageable sources
+            if staged:
+                if t == 3:
+                    g.stage_data(pinned[1])  # replaced by the next call
+                g.stage_data(src)
+            else:
+                g.update_data(src)
+            g.sweep(2, 9)
+            out.append((g.K, *g.labels(), *[s.copy() for s in g.stats()[:2]]))
+        g.close()
+        return out
+
+    for a, b in zip(chain(False), chain(True)):
+        assert a[0] == b[0]
+        for u, v in zip(a[1:], b[1:]):
+            assert np.array_equal(u, v)
