@@ -436,6 +436,9 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
                 for (int q = 0; q < SP_LGT; ++q) t[q] = std::lgamma(b + q) - std::lgamma(b);
                 ok = cudaMemcpy(c->sp_lgt, t.data(), sizeof(double) * SP_LGT, cudaMemcpyHostToDevice) == cudaSuccess;
             }
+            // a copy from pageable memory may return before its transfer lands, and the
+            // context's stream (set later) need not be ordered after the legacy stream
+            ok = ok && cudaDeviceSynchronize() == cudaSuccess;
         }
     }
     A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1 + 6 * (size_t)K_max));
