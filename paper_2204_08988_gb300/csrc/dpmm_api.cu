@@ -416,6 +416,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     // counts straight into the table)
     c->records_bytes = c->sparse ? 0 : sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
     A(&c->records, c->records_bytes);
+    if (c->kind == DPMM_PRIOR_DIRICHLET && !c->sparse) A(&c->mcnt, sizeof(unsigned) * 2 * (size_t)K_max * (d + 1));
     if (c->sparse) {
         const size_t ks = (size_t)(K_max + 31) / 32 * 32;
         A(&c->sp_cc, sizeof(float) * 2 * (size_t)K_max * d);
@@ -474,7 +475,7 @@ void dpmm_destroy(dpmm_ctx* c) {
                   c->shift32, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c, c->p_logtheta, c->q_mu,
                   c->q_W, c->q_c, c->q_b, c->q_logtheta, c->cweights, c->tot, c->records, c->Ltab,
                   c->relabel, c->acc, c->center, c->tc_img, c->tcs_img, c->tc_flag, c->dbg_scores, c->eps, c->bart, c->lgs, c->retry, c->x3_fimg,
-                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch, c->p_b,
+                  c->sp_cc, c->sp_ltT, c->sp_ct, c->sp_lgt, c->sp_lgb, c->sp_part, c->shard_scratch, c->p_b, c->mcnt,
                   c->stage};
     if (c->cstream) cudaStreamSynchronize(c->cstream);
     for (void* p : ps) dfree(p);

@@ -307,6 +307,7 @@ struct dpmm_ctx {
     void* sp_ltT = nullptr;        // d x round_up(K_max, 32) cluster log theta (FP64 or FP32)
     void* sp_ct = nullptr;         // K_max cluster log weights (FP64 or FP32)
     float* sp_cc = nullptr;        // 2 K_max x d compact sub-cluster counts
+    unsigned* mcnt = nullptr;      // dense multinomial data: 2 K_max x (d + 1) sub-cluster counts
     double* sp_lgt = nullptr;      // lgamma(beta + c) - lgamma(beta), c < SP_LGT (uniform beta)
     double* sp_lgb = nullptr;      // lgamma(beta_j)
     void* sp_part = nullptr;       // 3 K_max x ceil(d / 2048) (max, sum exp) of the FP32 theta draws
@@ -347,6 +348,7 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed);
 cudaError_t launch_sort(dpmm_ctx* c);
 cudaError_t launch_substats(dpmm_ctx* c, uint64_t seed, int draw_zbar);
 cudaError_t launch_combine(dpmm_ctx* c);
+bool mult_direct(const dpmm_ctx* c);
 cudaError_t launch_init_labels(dpmm_ctx* c, uint64_t seed);
 cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm_enabled);
 cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed);

@@ -1024,6 +1024,206 @@ __global__ void __launch_bounds__(256) substats_mult_kernel(SubArgs<float> a) {
     if (cur >= 0) flush(cur);
 }
 
+// Multinomial sub-labels and statistics (first moments only), one warp per range of sorted
+// positions, that is, of points in cluster order.  Lane l holds categories 8l .. 8l + 7 (d <= 256)
+// of a point's counts and of the two sub-cluster log theta rows of the current cluster; the
+// two sub-cluster scores are dot products reduced across the warp; the z-bar draws of 32
+// points are made at once, one point per lane; the counts of a cluster's run stay in registers
+// and are added at the run's end to the compact table cnt (2 K_max x (d + 1) integers, column
+// d: the points) with atomic adds, exact in any order.  No block-wide barrier.
+struct MwArgs {
+    int64_t N, R;  // points; sorted positions per warp
+    int d, xs;
+    const void* X;
+    const int* idx;     // sorted position -> point
+    const int* starts;  // K + 1 cluster offsets in sorted order
+    const int* dK;
+    const float* lt;    // slots x d log theta (FP32)
+    const float* lc;    // slots: log weights
+    const uint32_t* diter;
+    uint64_t seed;
+    const int* gate;
+    int draw;
+    uint8_t* zbar;
+    unsigned* cnt;
+};
+
+constexpr int MW_DEPTH = 16;  // rows in flight per warp (a ring in shared memory)
+constexpr int MW_ROWB = 512;  // bytes per ring slot: d <= 256 BF16 counts
+
+__device__ __forceinline__ void mw_cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// BF16 counts (rows 16-byte aligned).  Dynamic shared memory: 8 warps x MW_DEPTH x MW_ROWB.
+__global__ void __launch_bounds__(256, 3) mult_warp_kernel(MwArgs a) {
+    if (a.gate && *a.gate == 0) return;
+    extern __shared__ __align__(16) unsigned char mw_sm[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* ring = mw_sm + (threadIdx.x >> 5) * (MW_DEPTH * MW_ROWB);
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t p0 = w * a.R, p1 = min(a.N, p0 + a.R);
+    if (p0 >= p1) return;
+    const int K = *a.dK, d = a.d, j0 = 8 * lane, nch = (d + 7) >> 3;
+    int k = 0;  // the cluster of position p0: the last k with starts[k] <= p0
+    for (int lo = 0, hi = K; hi - lo > 1;) {
+        const int mid = (lo + hi) >> 1;
+        if (a.starts[mid] <= p0) lo = mid;
+        else hi = mid;
+        k = lo;
+    }
+    int64_t kend = a.starts[k + 1];
+    float lt0[8], lt1[8], c0 = 0.f, c1 = 0.f;
+    auto stage = [&](int kk) {
+        const float* r0 = a.lt + (size_t)(3 * kk + 1) * d + j0;
+        const float* r1 = r0 + d;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            lt0[u] = j0 + u < d ? r0[u] : 0.f;
+            lt1[u] = j0 + u < d ? r1[u] : 0.f;
+        }
+        c0 = a.lc[3 * kk + 1];
+        c1 = a.lc[3 * kk + 2];
+    };
+    unsigned acc0[8], acc1[8], n0 = 0, n1 = 0;  // integer counts: exact
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc0[u] = acc1[u] = 0u;
+    auto flush = [&](int kk) {
+        unsigned* r0 = a.cnt + (size_t)(2 * kk) * (d + 1);
+        unsigned* r1 = r0 + (d + 1);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (j0 + u < d) {
+                if (acc0[u]) atomicAdd(r0 + j0 + u, acc0[u]);
+                if (acc1[u]) atomicAdd(r1 + j0 + u, acc1[u]);
+            }
+            acc0[u] = acc1[u] = 0u;
+        }
+        if (lane == 0) {
+            if (n0) atomicAdd(r0 + d, n0);
+            if (n1) atomicAdd(r1 + d, n1);
+        }
+        n0 = n1 = 0;
+    };
+    if (a.draw) stage(k);
+    const Key key{a.seed, a.diter[0], a.diter[1], a.diter[2]};
+    // point indices of positions in batches of 32 (lane l: position batch start + l); the
+    // next batch's are loaded one batch ahead
+    int64_t bstart = p0;
+    int cur = p0 + lane < p1 ? a.idx[p0 + lane] : 0;
+    int nxt = p0 + 32 + lane < p1 ? a.idx[p0 + 32 + lane] : 0;
+    auto pick = [&](int64_t pos) {
+        const int r = (int)(pos - bstart);
+        const int vc = __shfl_sync(0xffffffffu, cur, r & 31), vn = __shfl_sync(0xffffffffu, nxt, r & 31);
+        return r < 32 ? vc : vn;
+    };
+    auto issue = [&](int slot, int64_t pos) {  // the row of position pos into a ring slot
+        if (pos < p1) {
+            const int i = pick(pos);
+            if (lane < nch)
+                mw_cp16(ring + slot * MW_ROWB + lane * 16, (const char*)a.X + (int64_t)i * a.xs * 2 + lane * 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int t = 0; t < MW_DEPTH; ++t) issue(t, p0 + t);
+    float gl = 0.f, gr = 0.f;
+    int hz = 0;
+    auto draws = [&]() {  // this batch's z-bar Gumbel values (or kept z-bar), one point per lane
+        if (bstart + lane < p1) {
+            if (a.draw) {
+                uint32_t wq[4];
+                key.block((uint32_t)cur, TAG_ZBAR, 0, wq);
+                gl = gumbel_of<float>(wq[0], wq[1]);
+                gr = gumbel_of<float>(wq[2], wq[3]);
+            } else {
+                hz = a.zbar[cur];
+            }
+        }
+    };
+    draws();
+    for (int64_t p = p0; p < p1; ++p) {
+        if (p - bstart == 32) {  // the next batch
+            bstart += 32;
+            cur = nxt;
+            nxt = bstart + 32 + lane < p1 ? a.idx[bstart + 32 + lane] : 0;
+            draws();
+        }
+        const int slot = (int)((p - p0) % MW_DEPTH);
+        asm volatile("cp.async.wait_group %0;" ::"n"(MW_DEPTH - 1) : "memory");
+        __syncwarp();
+        float x[8];
+        if (lane < nch) {
+            const uint4 q = *(const uint4*)(ring + slot * MW_ROWB + lane * 16);
+            const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[2 * u] = j0 + 2 * u < d ? __uint_as_float(wv[u] << 16) : 0.f;
+                x[2 * u + 1] = j0 + 2 * u + 1 < d ? __uint_as_float(wv[u] & 0xFFFF0000u) : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = 0.f;
+        }
+        __syncwarp();  // every lane has read the slot: it may be refilled
+        issue(slot, p + MW_DEPTH);
+        while (p >= kend) {  // the next cluster's run begins
+            flush(k);
+            ++k;
+            kend = a.starts[k + 1];
+            if (a.draw) stage(k);
+        }
+        const int q = (int)(p - bstart);
+        int h;
+        if (a.draw) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s0 = fmaf(x[u], lt0[u], s0);
+                s1 = fmaf(x[u], lt1[u], s1);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            const float vl = c0 + s0 + __shfl_sync(0xffffffffu, gl, q);
+            const float vr = c1 + s1 + __shfl_sync(0xffffffffu, gr, q);
+            h = vr > vl ? 1 : 0;
+            if (lane == q) a.zbar[cur] = (uint8_t)h;
+        } else {
+            h = __shfl_sync(0xffffffffu, hz, q);
+        }
+        if (h) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc1[u] += (unsigned)x[u];
+            ++n1;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc0[u] += (unsigned)x[u];
+            ++n0;
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    flush(k);
+}
+
+// the compact counts of the 2K sub-clusters: cleared before, copied into the FP64
+// statistics table after (grid: y = sub-cluster slot, x strides over the d + 1 columns)
+__global__ void mcnt_zero_kernel(const int* dK, const int* gate, int d, unsigned* cnt) {
+    if (gate && *gate == 0) return;
+    const int s = blockIdx.y;
+    if (s >= 2 * *dK) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= d; j += gridDim.x * blockDim.x) cnt[(size_t)s * (d + 1) + j] = 0u;
+}
+
+__global__ void mcnt_fill_kernel(const int* dK, const int* gate, StatLayout L, const unsigned* cnt, double* S) {
+    if (gate && *gate == 0) return;
+    const int s = blockIdx.y, d = L.d;
+    if (s >= 2 * *dK) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= d; j += gridDim.x * blockDim.x)
+        S[(size_t)s * L.E + L.ent(j, d)] = (double)cnt[(size_t)s * (d + 1) + j];
+}
+
 // stats[(2k + h) E + e] = sum over the CTAs g covering cluster k's run of rec[g + k]
 __global__ void combine_kernel(const double* rec, const int* starts, const int* dK, int64_t R, int E,
                                const double* shift_new, double* shift_stats, int d, const int* gate,
@@ -1307,9 +1507,51 @@ static cudaError_t substats_wide_t(dpmm_ctx* c, uint64_t seed, int draw, const i
     return cudaGetLastError();
 }
 
+// dense multinomial data on the reduced-precision paths: mult_warp_kernel and its compact counts
+bool mult_direct(const dpmm_ctx* c) {
+    return c->kind == DPMM_PRIOR_DIRICHLET && !c->sparse && c->prec != DPMM_PREC_FP64_PLAIN && c->d <= 256 && c->mcnt &&
+           c->xdt == 2 && (c->xs & 7) == 0;
+}
+
+static cudaError_t mult_direct_t(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
+    const dim3 sg((unsigned)std::min(8, (c->d + 1 + 255) / 256), (unsigned)(2 * c->K_max));
+    mcnt_zero_kernel<<<sg, 256, 0, c->stream>>>(c->dK, gate, c->d, c->mcnt);
+    MwArgs a;
+    a.N = c->N;
+    a.d = c->d;
+    a.xs = c->xs;
+    a.X = c->X;
+    a.idx = c->idx;
+    a.starts = c->tot;
+    a.dK = c->dK;
+    a.lt = c->q_logtheta;
+    a.lc = c->q_c;
+    a.diter = c->diter;
+    a.seed = seed;
+    a.gate = gate;
+    a.draw = draw;
+    a.zbar = c->zbar;
+    a.cnt = c->mcnt;
+    const int64_t warps = 24 * (int64_t)c->num_sms;  // three 256-thread blocks per SM
+    a.R = std::max<int64_t>(1, (c->N + warps - 1) / warps);
+    const unsigned grid = (unsigned)((((c->N + a.R - 1) / a.R) + 7) / 8);
+    const int smem = 8 * MW_DEPTH * MW_ROWB;
+    cudaError_t e = cudaFuncSetAttribute(mult_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    mult_warp_kernel<<<grid, 256, smem, c->stream>>>(a);
+    mcnt_fill_kernel<<<sg, 256, 0, c->stream>>>(c->dK, gate, c->st, c->mcnt, c->stats);
+    return cudaGetLastError();
+}
+
 static cudaError_t substats_dispatch(dpmm_ctx* c, uint64_t seed, int draw, const int* gate) {
     prof_begin(c, draw ? "substats" : "restats");
     cudaError_t e;
+    if (mult_direct(c)) {
+        e = mult_direct_t(c, seed, draw, gate);
+        prof_end(c, draw ? "substats" : "restats");
+        c->nlaunch += 3;
+        return e;
+    }
     const bool mult_fast = c->prec != DPMM_PREC_FP64_PLAIN && c->kind == DPMM_PRIOR_DIRICHLET && c->st.nblk <= 256;
     if (mult_fast) {
         e = c->xdt == 2 ? substats_mult_t<__nv_bfloat16>(c, seed, draw, gate) : substats_mult_t<float>(c, seed, draw, gate);
@@ -1338,6 +1580,7 @@ cudaError_t launch_substats(dpmm_ctx* c, uint64_t seed, int draw_zbar) {
 }
 
 cudaError_t launch_combine(dpmm_ctx* c) {
+    if (mult_direct(c)) return cudaSuccess;  // the counts went straight to the table
     prof_begin(c, "combine");
     cudaError_t e = combine_impl(c, nullptr);
     prof_end(c, "combine");
@@ -1350,7 +1593,7 @@ cudaError_t launch_restats_gated(dpmm_ctx* c, const int* gate) {
     if (c->sparse) return launch_sparse(c, 0, 2, gate);
     cudaError_t e = sort_impl(c, gate);
     if (e == cudaSuccess) e = substats_dispatch(c, 0, 0, gate);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !mult_direct(c)) {
         prof_begin(c, "combine");
         e = combine_impl(c, gate);
         prof_end(c, "combine");

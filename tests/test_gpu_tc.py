@@ -225,3 +225,31 @@ def test_mult_chain_finds_topics():
     purity = sum(Counter(z[y == k]).most_common(1)[0][1] for k in range(K) if (y == k).any()) / N
     assert purity > 0.95, (purity, g.K)
     g.close()
+
+
+@pytest.mark.parametrize("N,d,K", [(120_001, 200, 50), (30_000, 100, 7), (20_000, 256, 12), (5_003, 3, 4)])
+def test_mult_statistics_are_exact_counts(N, d, K):
+    """The multinomial statistics of the reduced-precision path (one warp per run of points
+    in cluster order, integer counts added atomically): after whole sweeps, each
+    sub-cluster's count vector and point count equal an exact integer recount of the data by
+    the GPU's own labels, at d divisible by 8 or not (lanes holding a partial or no block of
+    eight categories)."""
+    import synth
+
+    X, y = synth.multinomial_mixture(N, d, K, 60, seed=70 + d)
+    g = P.DPMM(1, d, 64, 10.0, prec=P.PREC_BF16, burn_out=2, beta=np.ones(d))
+    g.set_data(X)
+    g.set_state(K, y.astype(np.int32), (np.arange(N) % 2).astype(np.uint8))
+    g.sweep(3, 4)
+    z, zb = g.labels()
+    n, sx, _ = g.stats()
+    Kg = g.K
+    slot = 2 * z.astype(np.int64) + zb
+    ref = np.zeros((2 * Kg, d), dtype=np.int64)
+    np.add.at(ref, slot, X.astype(np.int64))
+    cnt = np.bincount(slot, minlength=2 * Kg)
+    for k in range(Kg):
+        for h in range(2):
+            assert n[3 * k + 1 + h] == cnt[2 * k + h]
+            assert np.array_equal(sx[3 * k + 1 + h], ref[2 * k + h].astype(np.float64))
+    g.close()
