@@ -189,13 +189,15 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     }
 }
 
-// The Dirichlet-multinomial log marginals of compressed-row data (many categories):
-// the counts come from the compact sub-cluster count table, and only categories with a
-// nonzero count contribute (for c = 0, lgamma(beta_j + c) - lgamma(beta_j) = 0).  The term
-// for count c is read from a table of lgamma(beta + c) - lgamma(beta) made on the host when
-// every beta_j is equal and c is below its length, and computed otherwise.  Same outputs
-// as marginal_kernel (Ltab), one CTA per cluster, sub-cluster and pair.
-__global__ void marginal_sparse_kernel(SMArgs a, const float* cc, const double* lgt, int nlgt, const double* lgb,
+// The Dirichlet-multinomial log marginals from a compact sub-cluster count table (row
+// stride cs): FP32 counts of compressed-row data, or the integer counts of the dense
+// reduced-precision path.  Only categories with a nonzero count contribute (for c = 0,
+// lgamma(beta_j + c) - lgamma(beta_j) = 0).  The term for count c is read from a table of
+// lgamma(beta + c) - lgamma(beta) made on the host when every beta_j is equal and c is below
+// its length, and computed otherwise.  Same outputs as marginal_kernel (Ltab), one CTA per
+// cluster, sub-cluster and pair.
+template <typename CT>
+__global__ void marginal_counts_kernel(SMArgs a, const CT* cc, int cs, const double* lgt, int nlgt, const double* lgb,
                                        double* Ltab) {
     __shared__ double shc[32], sha[32];
     const int K = *a.dK;
@@ -217,18 +219,18 @@ __global__ void marginal_sparse_kernel(SMArgs a, const float* cc, const double* 
         const double ns = smv(a, k1, h, d, d);
         Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
     }
-    const float* a0 = cc + (size_t)(2 * k1 + (h < 0 ? 0 : h)) * d;
-    const float* a1 = h < 0 ? cc + (size_t)(2 * k1 + 1) * d : nullptr;
-    const float* b0 = k2 >= 0 ? cc + (size_t)(2 * k2) * d : nullptr;
-    const float* b1 = k2 >= 0 ? cc + (size_t)(2 * k2 + 1) * d : nullptr;
+    const CT* a0 = cc + (size_t)(2 * k1 + (h < 0 ? 0 : h)) * cs;
+    const CT* a1 = h < 0 ? cc + (size_t)(2 * k1 + 1) * cs : nullptr;
+    const CT* b0 = k2 >= 0 ? cc + (size_t)(2 * k2) * cs : nullptr;
+    const CT* b1 = k2 >= 0 ? cc + (size_t)(2 * k2 + 1) * cs : nullptr;
     double sc = 0.0, acc = 0.0;
     for (int j = tid; j < d; j += nt) {
-        float c = a0[j];
+        CT c = a0[j];
         if (a1) c += a1[j];
-        if (b0) c += b0[j] + b1[j];  // integers below 2^24: exact
-        if (c > 0.f) {
+        if (b0) c += b0[j] + b1[j];  // integer counts (FP32: below 2^24): exact
+        if (c > CT(0)) {
             sc += (double)c;
-            acc += (lgt && c < (float)nlgt) ? lgt[(int)c] : lgamma(a.beta[j] + (double)c) - lgb[j];
+            acc += (lgt && c < (CT)nlgt) ? lgt[(int)c] : lgamma(a.beta[j] + (double)c) - lgb[j];
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -558,8 +560,11 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
         }
         prof_begin(c, "marginal");
         if (c->sparse)
-            marginal_sparse_kernel<<<items, 256, 0, c->stream>>>(s, c->sp_cc, c->sp_lgt, c->sp_lgt ? SP_LGT : 0,
-                                                                c->sp_lgb, c->Ltab);
+            marginal_counts_kernel<float><<<items, 256, 0, c->stream>>>(s, c->sp_cc, c->d, c->sp_lgt,
+                                                                       c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
+        else if (mult_direct(c))  // the compact integer counts of the dense multinomial path
+            marginal_counts_kernel<unsigned><<<items, 256, 0, c->stream>>>(s, c->mcnt, c->d + 1, c->sp_lgt,
+                                                                          c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
         else
             marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);
         prof_end(c, "marginal");
