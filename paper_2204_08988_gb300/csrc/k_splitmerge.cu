@@ -62,15 +62,12 @@ __device__ inline void pair_of(int p, int K, int& k1, int& k2) {
     k2 = r + 1 + (p - off);
 }
 
-// Dynamic shared memory: d (d | 1) + 10 d doubles (+ 2 E when the statistics are staged).
-__global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
+// One item (slot or merge pair) of marginal_kernel.  Dynamic shared memory: d (d | 1) + 10 d
+// doubles (+ 2 E when the statistics are staged).
+__device__ __forceinline__ void marginal_item(const SMArgs& a, double* Ltab, int* derr, int K, int e) {
     extern __shared__ double smem[];
     __shared__ double sh[32];
     __shared__ double s_n, s_n1, s_n2;
-    const int K = *a.dK;
-    const int e = blockIdx.x;
-    const int npairs = K * (K - 1) / 2;
-    if (e >= 3 * K + npairs) return;
     const int d = a.L.d, tid = threadIdx.x, nt = blockDim.x;
     int k1, k2, h;
     if (e < 3 * K) {
@@ -189,6 +186,18 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     }
 }
 
+// Log marginal likelihoods of every slot (cluster and sub-clusters) and merge pair: the
+// resident blocks take the items in turn, so that no block is launched for the slots and
+// pairs beyond the current K.
+__global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
+    const int K = *a.dK;
+    const int total = 3 * K + K * (K - 1) / 2;
+    for (int e = blockIdx.x; e < total; e += gridDim.x) {
+        marginal_item(a, Ltab, derr, K, e);
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
 // The Dirichlet-multinomial log marginals from a compact sub-cluster count table (row
 // stride cs): FP32 counts of compressed-row data, or the integer counts of the dense
 // reduced-precision path.  Only categories with a nonzero count contribute (for c = 0,
@@ -197,13 +206,9 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
 // its length, and computed otherwise.  Same outputs as marginal_kernel (Ltab), one CTA per
 // cluster, sub-cluster and pair.
 template <typename CT>
-__global__ void marginal_counts_kernel(SMArgs a, const CT* cc, int cs, const double* lgt, int nlgt, const double* lgb,
-                                       double* Ltab) {
+__device__ __forceinline__ void marginal_counts_item(const SMArgs& a, const CT* cc, int cs, const double* lgt, int nlgt,
+                                                     const double* lgb, double* Ltab, int K, int e) {
     __shared__ double shc[32], sha[32];
-    const int K = *a.dK;
-    const int e = blockIdx.x;
-    const int npairs = K * (K - 1) / 2;
-    if (e >= 3 * K + npairs) return;
     const int d = a.L.d, tid = threadIdx.x, nt = blockDim.x;
     int k1, k2, h;
     if (e < 3 * K) {
@@ -249,6 +254,17 @@ __global__ void marginal_counts_kernel(SMArgs a, const CT* cc, int cs, const dou
             l += sha[w];
         }
         *out = l + a.lg_sum_beta - lgamma(a.sum_beta + c);
+    }
+}
+
+template <typename CT>
+__global__ void marginal_counts_kernel(SMArgs a, const CT* cc, int cs, const double* lgt, int nlgt, const double* lgb,
+                                       double* Ltab) {
+    const int K = *a.dK;
+    const int total = 3 * K + K * (K - 1) / 2;
+    for (int e = blockIdx.x; e < total; e += gridDim.x) {
+        marginal_counts_item<CT>(a, cc, cs, lgt, nlgt, lgb, Ltab, K, e);
+        __syncthreads();  // shared memory is reused by the next item
     }
 }
 
@@ -558,15 +574,26 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
             cudaError_t e = cudaFuncSetAttribute(marginal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
+        // one wave of resident blocks, each taking items in turn (the items beyond the
+        // current K launch no block)
+        auto waves = [&](const void* fn, int threads, size_t smem) {
+            int per = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) {
+                cudaGetLastError();
+                per = 1;
+            }
+            return (unsigned)std::min<int64_t>(items, (int64_t)per * c->num_sms);
+        };
         prof_begin(c, "marginal");
         if (c->sparse)
-            marginal_counts_kernel<float><<<items, 256, 0, c->stream>>>(s, c->sp_cc, c->d, c->sp_lgt,
-                                                                       c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
+            marginal_counts_kernel<float><<<waves((const void*)marginal_counts_kernel<float>, 256, 0), 256, 0, c->stream>>>(
+                s, c->sp_cc, c->d, c->sp_lgt, c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
         else if (mult_direct(c))  // the compact integer counts of the dense multinomial path
-            marginal_counts_kernel<unsigned><<<items, 256, 0, c->stream>>>(s, c->mcnt, c->d + 1, c->sp_lgt,
-                                                                          c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
+            marginal_counts_kernel<unsigned>
+                <<<waves((const void*)marginal_counts_kernel<unsigned>, 256, 0), 256, 0, c->stream>>>(
+                    s, c->mcnt, c->d + 1, c->sp_lgt, c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
         else
-            marginal_kernel<<<items, 128, sm, c->stream>>>(s, c->Ltab, c->derr);
+            marginal_kernel<<<waves((const void*)marginal_kernel, 128, sm), 128, sm, c->stream>>>(s, c->Ltab, c->derr);
         prof_end(c, "marginal");
         c->nlaunch += 1;
     }
