@@ -63,11 +63,62 @@ struct VarArgs {
     uint64_t seed;
     double alpha, nu0;
     int kind, Kmax, niw;
+    int f32;       // the slots' variates in FP32 arithmetic (NIW, reduced-precision paths)
+    int f32w;      // the weights' Gamma draws in FP32 arithmetic (reduced-precision paths)
     double* W;     // p_W
     double* eps;   // 3 K_max x d
     double* bart;  // 3 K_max x d
     double* lgs;   // 3 K_max + 1
 };
+
+// Element q of the variates of slot s's NIW draw (Sec. 4.1 steps (c), (d)): for q < npair a
+// pair of normals (the entries above W's diagonal, then eps), for npair <= q < npair + d the
+// Bartlett diagonal B_jj = sqrt(chi^2(nu_n - d + j + 1)).  W, eps, bart: the slot's rows.
+// f32: FP32 arithmetic on the leading bits of the same Philox words (the reduced-precision
+// paths; an FP64 retry of the slot draws them again in FP64).
+__device__ inline void slot_variate(const Key& key, int s, int d, double nun, int q, bool f32, double* W, double* eps,
+                                    double* bart) {
+    const int npair = (d * d + d + 1) / 2;
+    const uint32_t NB = 64u * d;
+    if (q < npair) {
+        uint32_t w[4];
+        key.block((uint32_t)s, TAG_PARAM, NB + (uint32_t)q, w);
+        double nv2[2];
+        if (f32) {
+            const float rr = sqrtf(-2.f * logf(u01_f32(w[0])));
+            float sn, cs;
+            sincospif(2.f * u01_f32(w[2]), &sn, &cs);
+            nv2[0] = rr * cs;
+            nv2[1] = rr * sn;
+        } else {
+            const double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
+            const double rr = sqrt(-2.0 * log(u1));
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);  // sin and cos of 2 pi u2
+            nv2[0] = rr * cs;
+            nv2[1] = rr * sn;
+        }
+        for (int o = 0; o < 2; ++o) {
+            const int qq = 2 * q + o;
+            if (qq < d * d) {
+                const int r = qq / d, c = qq % d;
+                W[qq] = r < c ? nv2[o] : 0.0;
+            } else if (qq < d * d + d) {
+                eps[qq - d * d] = nv2[o];
+            }
+        }
+    } else if (q < npair + d) {
+        const int j = q - npair;
+        const double df = nun - d + (j + 1);
+        if (f32) {
+            const float lg = f_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, (float)(0.5 * df));
+            bart[j] = (double)sqrtf(2.f * expf(lg));
+        } else {
+            const double lg = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, 0.5 * df);
+            bart[j] = sqrt(2.0 * exp(lg));
+        }
+    }
+}
 
 __global__ void variates_kernel(VarArgs a) {
     const int K = *a.dK;
@@ -77,54 +128,54 @@ __global__ void variates_kernel(VarArgs a) {
     if ((int)blockIdx.y == 3 * a.Kmax) {
         const int T = 3 * K + 1;
         if (q >= T) return;
+        // Gamma draws of the weights: FP32 arithmetic on the reduced-precision paths
+        auto lg = [&](uint32_t c0, uint32_t tag, uint32_t base, double shape) -> double {
+            return a.f32w ? (double)f_log_gamma(key, c0, tag, base, (float)shape) : d_log_gamma(key, c0, tag, base, shape);
+        };
         double v;
-        if (q < K) v = d_log_gamma(key, (uint32_t)q, TAG_WEIGHT, 0, a.sv.count(q, -1));
-        else if (q == K) v = d_log_gamma(key, 0xFFFFFFFFu, TAG_WEIGHT, 0, a.alpha);
+        if (q < K) v = lg((uint32_t)q, TAG_WEIGHT, 0, a.sv.count(q, -1));
+        else if (q == K) v = lg(0xFFFFFFFFu, TAG_WEIGHT, 0, a.alpha);
         else {
             const int k = (q - K - 1) >> 1, h = (q - K - 1) & 1;
-            v = d_log_gamma(key, (uint32_t)k, TAG_SUBW, 64u * h, a.sv.count(k, h) + 0.5 * a.alpha);
+            v = lg((uint32_t)k, TAG_SUBW, 64u * h, a.sv.count(k, h) + 0.5 * a.alpha);
         }
         a.lgs[q] = v;
         return;
     }
     const int s = blockIdx.y;
     if (!a.niw || s >= 3 * K) return;
-    const int npair = (d * d + d + 1) / 2;
-    const uint32_t NB = 64u * d;
-    if (q < npair) {
-        uint32_t w[4];
-        key.block((uint32_t)s, TAG_PARAM, NB + (uint32_t)q, w);
-        const double u1 = u01_f64(w[0], w[1]), u2 = u01_f64(w[2], w[3]);
-        const double rr = sqrt(-2.0 * log(u1));
-        double sn, cs;
-        sincospi(2.0 * u2, &sn, &cs);  // sin and cos of 2 pi u2
-        double* W = a.W + (size_t)s * d * d;
-        for (int o = 0; o < 2; ++o) {
-            const int qq = 2 * q + o;
-            const double nv = o ? rr * sn : rr * cs;
-            if (qq < d * d) {
-                const int r = qq / d, c = qq % d;
-                W[qq] = r < c ? nv : 0.0;
-            } else if (qq < d * d + d) {
-                a.eps[(size_t)s * d + (qq - d * d)] = nv;
-            }
-        }
-    } else if (q < npair + d) {
-        const int j = q - npair;
-        const int k = s / 3, h = s % 3 - 1;
-        const double nun = a.nu0 + a.sv.count(k, h);
-        const double df = nun - d + (j + 1);
-        const double lg = d_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, 0.5 * df);
-        a.bart[(size_t)s * d + j] = sqrt(2.0 * exp(lg));
-    }
+    const int k = s / 3, h = s % 3 - 1;
+    slot_variate(key, s, d, a.nu0 + a.sv.count(k, h), q, a.f32 != 0, a.W + (size_t)s * d * d, a.eps + (size_t)s * d,
+                 a.bart + (size_t)s * d);
 }
 
 // (a) (pi_1..pi_K, pi~) ~ Dir(N_1..N_K, alpha); (b) pibar_k ~ Dir(N_kl + a/2, N_kr + a/2):
 // normalisation of the Gamma draws made by variates_kernel.  One warp: a wider block
 // would only multiply the FP64 reduction work on GB300's narrow FP64 pipe.
+template <typename T>
 __global__ void __launch_bounds__(32) weights_kernel(const int* dK, const double* lgs, double* logw,
                                                      double* cweights) {
     const int K = *dK, lane = threadIdx.x;
+    if constexpr (sizeof(T) == 4) {  // the reduced-precision paths: FP32 arithmetic
+        float lmax = -INFINITY;
+        for (int k = lane; k <= K; k += 32) lmax = fmaxf(lmax, (float)lgs[k]);
+        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        float s = 0.f;
+        for (int k = lane; k <= K; k += 32) s += expf((float)lgs[k] - lmax);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float lse = lmax + logf(s);
+        for (int k = lane; k < K; k += 32) {
+            const float lw = (float)lgs[k] - lse;
+            logw[3 * k] = lw;
+            cweights[k] = expf(lw);
+            const float gl = (float)lgs[K + 1 + 2 * k], gr = (float)lgs[K + 2 + 2 * k];
+            const float m = fmaxf(gl, gr);
+            const float l2 = m + log1pf(expf(-fabsf(gl - gr)));
+            logw[3 * k + 1] = gl - l2;
+            logw[3 * k + 2] = gr - l2;
+        }
+        return;
+    }
     double lmax = -INFINITY;
     for (int k = lane; k <= K; k += 32) lmax = fmax(lmax, lgs[k]);
     for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -172,9 +223,9 @@ __device__ inline double log_t(double x) { return log(x); }
 
 template <typename T>
 __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPrior pr, const int* dK,
-                                  const double* eps, const double* bart, const double* logw, double* p_mu,
+                                  double* eps, double* bart, const double* logw, double* p_mu,
                                   double* p_W, double* p_logdetW, double* p_c, int* derr, int w_in_smem,
-                                  int staged, int* retry) {
+                                  int staged, int* retry, const uint32_t* diter, uint64_t seed) {
     extern __shared__ double smem[];
     const int d = sv.L.d, E = sv.L.E;
     const int K = *dK;
@@ -216,6 +267,14 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
     }
     __syncthreads();
     const double n = s_n, rn = s_rn, kn = s_kn, rkn = s_rkn;
+    if (retry_pass) {  // the slot's variates again, in FP64 (the FP32 pass drew them in FP32)
+        const Key key{seed, diter[0], diter[1], diter[2]};
+        const int npair = (d * d + d + 1) / 2;
+        for (int q = tid; q < npair + d; q += nt)
+            slot_variate(key, s, d, pr.nu0 + n, q, false, p_W + (size_t)s * d * d, eps + (size_t)s * d,
+                         bart + (size_t)s * d);
+        __syncthreads();
+    }
     const double* sh_k = shift_stats + (size_t)k * d;
     for (int j = tid; j < d; j += nt) {
         const double xbar = n > 0 ? sh_k[j] + M(j, d) * rn : 0.0;
@@ -449,7 +508,8 @@ static StatView make_sv(dpmm_ctx* c) { return StatView{c->stats, c->st}; }
 
 cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
     VarArgs a{make_sv(c), c->dK, c->diter, seed, c->alpha, c->nu0, c->kind, c->K_max, c->kind == DPMM_PRIOR_NIW,
-              c->p_W, c->eps, c->bart, c->lgs};
+              c->kind == DPMM_PRIOR_NIW && c->prec != DPMM_PREC_FP64_PLAIN, c->prec != DPMM_PREC_FP64_PLAIN, c->p_W,
+              c->eps, c->bart, c->lgs};
     const int d = c->d;
     const int per_slot = c->kind == DPMM_PRIOR_NIW ? (d * d + d + 1) / 2 + d : 0;
     const int per = std::max(per_slot, 3 * c->K_max + 1);
@@ -458,7 +518,8 @@ cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed) {
     variates_kernel<<<grid, 128, 0, c->stream>>>(a);
     prof_end(c, "variates");
     prof_begin(c, "weights");
-    weights_kernel<<<1, 32, 0, c->stream>>>(c->dK, c->lgs, c->p_logw, c->cweights);
+    if (c->prec == DPMM_PREC_FP64_PLAIN) weights_kernel<double><<<1, 32, 0, c->stream>>>(c->dK, c->lgs, c->p_logw, c->cweights);
+    else weights_kernel<float><<<1, 32, 0, c->stream>>>(c->dK, c->lgs, c->p_logw, c->cweights);
     prof_end(c, "weights");
     c->nlaunch += 2;
     return cudaGetLastError();
@@ -494,13 +555,13 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         if (fp32) {
             niw_params_kernel<float><<<3 * c->K_max, 128, sm32, c->stream>>>(
                 make_sv(c), c->shift_stats, pr, c->dK, c->eps, c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW,
-                c->p_c, c->derr, w32, st32, c->retry);
+                c->p_c, c->derr, w32, st32, c->retry, c->diter, seed);
             c->nlaunch += 1;
         }
         // the FP64 path, or the FP64 retry of slots whose FP32 factorisation failed
         niw_params_kernel<double><<<3 * c->K_max, 128, sm64, c->stream>>>(
             make_sv(c), c->shift_stats, pr, c->dK, c->eps, c->bart, c->p_logw, c->p_mu, c->p_W, c->p_logdetW, c->p_c,
-            c->derr, w64, st64, fp32 ? c->retry : nullptr);
+            c->derr, w64, st64, fp32 ? c->retry : nullptr, c->diter, seed);
         prof_end(c, "niw_params");
         c->nlaunch += 1;
     } else {
