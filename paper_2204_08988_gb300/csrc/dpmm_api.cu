@@ -422,9 +422,9 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
         A(&c->sp_cc, sizeof(float) * 2 * (size_t)K_max * d);
         A(&c->sp_ltT, sizeof(double) * ks * d);
         A(&c->sp_ct, sizeof(double) * K_max);
-        A(&c->sp_part, sizeof(float) * 2 * S * ((d + 2047) / 2048));
     }
-    if (c->kind == DPMM_PRIOR_DIRICHLET) {  // the marginals of counts kept in compact tables
+    if (c->kind == DPMM_PRIOR_DIRICHLET) {  // FP32 theta draws; the marginals' lgamma tables
+        A(&c->sp_part, sizeof(float) * 2 * S * ((d + 2047) / 2048));
         A(&c->sp_lgb, sizeof(double) * d);
         bool uniform = true;
         for (int j = 1; j < d; ++j) uniform = uniform && prior->beta[j] == prior->beta[0];

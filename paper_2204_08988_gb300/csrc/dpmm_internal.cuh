@@ -339,6 +339,20 @@ struct dpmm_ctx {
 };
 
 namespace dpmm {
+// Sub-cluster count sources of the multinomial model (slot 2k + h, category j): the FP32
+// compact table of compressed-row data, or the FP64 statistics table of dense data (the one
+// table a point-sharded chain exchanges).
+struct CountsF32 {  // integer counts below 2^24: sums of a few stay exact in FP32
+    const float* cc;
+    int d;
+    __device__ float operator()(int slot, int j) const { return cc[(size_t)slot * d + j]; }
+};
+struct CountsStats {
+    const double* S;
+    StatLayout L;
+    __device__ double operator()(int slot, int j) const { return S[(size_t)slot * L.E + L.ent(j, L.d)]; }
+};
+
 // kernel launchers, one per .cu file group; each returns cudaGetLastError().
 cudaError_t launch_weights(dpmm_ctx* c, uint64_t seed);
 cudaError_t launch_params(dpmm_ctx* c, uint64_t seed);

@@ -415,15 +415,16 @@ __global__ void dirichlet_params_kernel(StatView sv, const double* beta, const i
     if (threadIdx.x == 0) p_c[s] = logw[s];
 }
 
-// The same draw in FP32 (reduced-precision path of compressed-row data): f_log_gamma,
-// FP32 normalisation; log theta stored in the FP64 table and its FP32 mirror.  A slot's
+// The same draw in FP32 (the reduced-precision paths): f_log_gamma, FP32 normalisation; log
+// theta stored in the FP64 table and its FP32 mirror.  A slot's
 // d categories (20,000 for document data) are spread over blockIdx.y chunks of
 // DP_CHUNK; the first kernel draws and leaves each chunk's maximum and sum of
 // exp(v - maximum), the second combines a slot's chunks in a fixed order and normalises.
 constexpr int DP_CHUNK = 2048;
 
+template <typename Src>
 __global__ void dirichlet_draw_f32_kernel(int d, const double* beta, const int* dK, const uint32_t* diter,
-                                          uint64_t seed, const float* cc, float* q_logtheta, float2* part) {
+                                          uint64_t seed, Src cnt, float* q_logtheta, float2* part) {
     __shared__ double sh[32];
     const int K = *dK;
     const int s = blockIdx.x;
@@ -434,9 +435,8 @@ __global__ void dirichlet_draw_f32_kernel(int d, const double* beta, const int* 
     float* qt = q_logtheta + (size_t)s * d;
     float mx = -INFINITY;
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const float cnt = h < 0 ? cc[(size_t)(2 * k) * d + j] + cc[(size_t)(2 * k + 1) * d + j]
-                                : cc[(size_t)(2 * k + h) * d + j];
-        const float v = f_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, (float)beta[j] + cnt);
+        const auto c = h < 0 ? cnt(2 * k, j) + cnt(2 * k + 1, j) : cnt(2 * k + h, j);
+        const float v = f_log_gamma(key, (uint32_t)s, TAG_PARAM, 64u * j, (float)beta[j] + (float)c);
         qt[j] = v;
         mx = fmaxf(mx, v);
     }
@@ -566,10 +566,16 @@ cudaError_t launch_params(dpmm_ctx* c, uint64_t seed) {
         c->nlaunch += 1;
     } else {
         prof_begin(c, "dirichlet_params");
-        if (c->sparse && c->prec != DPMM_PREC_FP64_PLAIN) {
+        if (c->prec != DPMM_PREC_FP64_PLAIN) {  // the reduced-precision paths: FP32 draws
             const dim3 grid(3 * c->K_max, (c->d + DP_CHUNK - 1) / DP_CHUNK);
-            dirichlet_draw_f32_kernel<<<grid, 256, 0, c->stream>>>(c->d, c->center + c->d, c->dK, c->diter, seed,
-                                                                  c->sp_cc, c->q_logtheta, (float2*)c->sp_part);
+            if (c->sparse)
+                dirichlet_draw_f32_kernel<CountsF32><<<grid, 256, 0, c->stream>>>(
+                    c->d, c->center + c->d, c->dK, c->diter, seed, CountsF32{c->sp_cc, c->d}, c->q_logtheta,
+                    (float2*)c->sp_part);
+            else
+                dirichlet_draw_f32_kernel<CountsStats><<<grid, 256, 0, c->stream>>>(
+                    c->d, c->center + c->d, c->dK, c->diter, seed, CountsStats{c->stats, c->st}, c->q_logtheta,
+                    (float2*)c->sp_part);
             dirichlet_norm_f32_kernel<<<grid, 256, 0, c->stream>>>(c->d, c->dK, c->p_logw, (const float2*)c->sp_part,
                                                                   c->q_logtheta, c->p_logtheta, c->p_c);
             c->nlaunch += 1;

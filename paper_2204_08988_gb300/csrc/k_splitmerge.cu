@@ -198,15 +198,15 @@ __global__ void marginal_kernel(SMArgs a, double* Ltab, int* derr) {
     }
 }
 
-// The Dirichlet-multinomial log marginals from a compact sub-cluster count table (row
-// stride cs): FP32 counts of compressed-row data, or the integer counts of the dense
-// reduced-precision path.  Only categories with a nonzero count contribute (for c = 0,
+// The Dirichlet-multinomial log marginals from the sub-cluster counts (Src: the FP32 compact
+// table of compressed-row data, or the statistics table of dense data on the reduced-precision
+// paths).  Only categories with a nonzero count contribute (for c = 0,
 // lgamma(beta_j + c) - lgamma(beta_j) = 0).  The term for count c is read from a table of
 // lgamma(beta + c) - lgamma(beta) made on the host when every beta_j is equal and c is below
 // its length, and computed otherwise.  Same outputs as marginal_kernel (Ltab), one CTA per
 // cluster, sub-cluster and pair.
-template <typename CT>
-__device__ __forceinline__ void marginal_counts_item(const SMArgs& a, const CT* cc, int cs, const double* lgt, int nlgt,
+template <typename Src>
+__device__ __forceinline__ void marginal_counts_item(const SMArgs& a, const Src& cnt, const double* lgt, int nlgt,
                                                      const double* lgb, double* Ltab, int K, int e) {
     __shared__ double shc[32], sha[32];
     const int d = a.L.d, tid = threadIdx.x, nt = blockDim.x;
@@ -224,18 +224,16 @@ __device__ __forceinline__ void marginal_counts_item(const SMArgs& a, const CT* 
         const double ns = smv(a, k1, h, d, d);
         Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
     }
-    const CT* a0 = cc + (size_t)(2 * k1 + (h < 0 ? 0 : h)) * cs;
-    const CT* a1 = h < 0 ? cc + (size_t)(2 * k1 + 1) * cs : nullptr;
-    const CT* b0 = k2 >= 0 ? cc + (size_t)(2 * k2) * cs : nullptr;
-    const CT* b1 = k2 >= 0 ? cc + (size_t)(2 * k2 + 1) * cs : nullptr;
+    using V = decltype(cnt(0, 0));  // the source's own type: FP32 sums stay off the FP64 pipe
+    const int s0 = 2 * k1 + (h < 0 ? 0 : h);
     double sc = 0.0, acc = 0.0;
     for (int j = tid; j < d; j += nt) {
-        CT c = a0[j];
-        if (a1) c += a1[j];
-        if (b0) c += b0[j] + b1[j];  // integer counts (FP32: below 2^24): exact
-        if (c > CT(0)) {
+        V c = cnt(s0, j);
+        if (h < 0) c += cnt(2 * k1 + 1, j);
+        if (k2 >= 0) c += cnt(2 * k2, j) + cnt(2 * k2 + 1, j);  // integer counts: exact
+        if (c > V(0)) {
             sc += (double)c;
-            acc += (lgt && c < (CT)nlgt) ? lgt[(int)c] : lgamma(a.beta[j] + (double)c) - lgb[j];
+            acc += (lgt && c < (V)nlgt) ? lgt[(int)c] : lgamma(a.beta[j] + (double)c) - lgb[j];
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -257,13 +255,12 @@ __device__ __forceinline__ void marginal_counts_item(const SMArgs& a, const CT* 
     }
 }
 
-template <typename CT>
-__global__ void marginal_counts_kernel(SMArgs a, const CT* cc, int cs, const double* lgt, int nlgt, const double* lgb,
-                                       double* Ltab) {
+template <typename Src>
+__global__ void marginal_counts_kernel(SMArgs a, Src cnt, const double* lgt, int nlgt, const double* lgb, double* Ltab) {
     const int K = *a.dK;
     const int total = 3 * K + K * (K - 1) / 2;
     for (int e = blockIdx.x; e < total; e += gridDim.x) {
-        marginal_counts_item<CT>(a, cc, cs, lgt, nlgt, lgb, Ltab, K, e);
+        marginal_counts_item<Src>(a, cnt, lgt, nlgt, lgb, Ltab, K, e);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
@@ -586,12 +583,13 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
         };
         prof_begin(c, "marginal");
         if (c->sparse)
-            marginal_counts_kernel<float><<<waves((const void*)marginal_counts_kernel<float>, 256, 0), 256, 0, c->stream>>>(
-                s, c->sp_cc, c->d, c->sp_lgt, c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
-        else if (mult_direct(c))  // the compact integer counts of the dense multinomial path
-            marginal_counts_kernel<unsigned>
-                <<<waves((const void*)marginal_counts_kernel<unsigned>, 256, 0), 256, 0, c->stream>>>(
-                    s, c->mcnt, c->d + 1, c->sp_lgt, c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
+            marginal_counts_kernel<CountsF32>
+                <<<waves((const void*)marginal_counts_kernel<CountsF32>, 256, 0), 256, 0, c->stream>>>(
+                    s, CountsF32{c->sp_cc, c->d}, c->sp_lgt, c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
+        else if (c->kind == DPMM_PRIOR_DIRICHLET && c->prec != DPMM_PREC_FP64_PLAIN)  // dense counts
+            marginal_counts_kernel<CountsStats>
+                <<<waves((const void*)marginal_counts_kernel<CountsStats>, 256, 0), 256, 0, c->stream>>>(
+                    s, CountsStats{c->stats, c->st}, c->sp_lgt, c->sp_lgt ? SP_LGT : 0, c->sp_lgb, c->Ltab);
         else
             marginal_kernel<<<waves((const void*)marginal_kernel, 128, sm), 128, sm, c->stream>>>(s, c->Ltab, c->derr);
         prof_end(c, "marginal");

@@ -163,3 +163,32 @@ def test_compressed_rows_fp32_three_shards_equal_unsharded_chain():
     assert one.K >= 3
     for g in gs + [one]:
         g.close()
+
+
+def test_dense_multinomial_bf16_two_shards_equal_unsharded_chain():
+    """Dense multinomial counts on the BF16 tensor-core path: the statistics are integer
+    counts (exact in any order) and every later step reads the exchanged statistics table,
+    so two shards give the very chain of one context."""
+    import synth
+
+    N, d = 30_001, 120
+    X, y = synth.multinomial_mixture(N, d, 6, 60, seed=66)
+    cut = 12_345
+    beta = np.ones(d)
+    gs = _shards(1, d, 16, 5.0, [X[:cut], X[cut:]], P.PREC_BF16, beta=beta)
+    one = P.DPMM(1, d, 16, 5.0, prec=P.PREC_BF16, burn_out=2, beta=beta)
+    one.set_data(X)
+    for t in range(12):
+        one.sweep(1, 77)
+        P.dpmm_sweep_sharded([g.h for g in gs], 1, 77)
+        assert all(g.K == one.K for g in gs), t
+        z1, zb1 = one.labels()
+        assert np.array_equal(z1, np.concatenate([g.labels()[0] for g in gs])), t
+        assert np.array_equal(zb1, np.concatenate([g.labels()[1] for g in gs])), t
+        n1, sx1, _ = one.stats()
+        for g in gs:
+            ng, sxg, _ = g.stats()
+            assert np.array_equal(n1, ng) and np.array_equal(sx1, sxg), t
+    assert one.K >= 3
+    for g in gs + [one]:
+        g.close()
