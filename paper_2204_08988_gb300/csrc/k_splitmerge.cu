@@ -268,20 +268,33 @@ __global__ void marginal_counts_kernel(SMArgs a, Src cnt, const double* lgt, int
 // Every split and merge ratio with its Philox uniform, in parallel: acc[k] for the
 // split of cluster k, acc[K_max + p] for merge pair p; 1 = accepted if proposed.
 // Indices in the Philox counters are those after removing emptied clusters.
-__global__ void hastings_kernel(SMArgs a, const double* Ltab, const uint32_t* diter, uint64_t seed, int labels_ran,
-                                int* acc) {
+constexpr int DEC_KMAX_SM = 1024;  // K_max <= 1000
+
+// One warp per block: the warp first finds which clusters hold points and their indices
+// after removing the empty ones (a prefix count in shared memory), then each lane takes a
+// proposal.
+__global__ void __launch_bounds__(32) hastings_kernel(SMArgs a, const double* Ltab, const uint32_t* diter, uint64_t seed,
+                                                      int labels_ran, int* acc) {
+    __shared__ int s_live[DEC_KMAX_SM], s_cid[DEC_KMAX_SM];
     const int K = *a.dK;
+    const int d = a.L.d, lane = threadIdx.x;
+    for (int q0 = 0, base = 0; q0 < K; q0 += 32) {
+        const int q = q0 + lane;
+        const int lv = q < K ? (labels_ran ? (smv(a, q, -1, d, d) > 0 ? 1 : 0) : 1) : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, lv);
+        if (q < K) {
+            s_live[q] = lv;
+            s_cid[q] = base + __popc(m & ((1u << lane) - 1u));
+        }
+        base += __popc(m);
+    }
+    __syncwarp();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int npairs = K * (K - 1) / 2;
     if (e >= K + npairs) return;
-    const int d = a.L.d;
     Key key{seed, diter[0], diter[1], diter[2]};
-    auto live = [&](int k) { return labels_ran ? smv(a, k, -1, d, d) > 0 : true; };
-    auto cid = [&](int k) {
-        int c = 0;
-        for (int q = 0; q < k; ++q) c += live(q);
-        return c;
-    };
+    auto live = [&](int k) { return s_live[k] != 0; };
+    auto cid = [&](int k) { return s_cid[k]; };
     const double la = a.log_alpha, al = a.alpha;
     const double* lg = Ltab + lg_offset(a.K_max);
     if (e < K) {
