@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
     unsigned char* SB = SA + 2 * SA_BUF;                  // 2 x SB_BUF
     float* F = (float*)(SB + 2 * SB_BUF);                 // FR x FS accumulators (row = D row)
     uint8_t* hq = (uint8_t*)(F + FR * FS);                // 2 x BM sub-labels (2: padding row)
-    __shared__ uint64_t bars[2 * XST + 15];
+    __shared__ uint64_t bars[2 * XST + 17];
     uint64_t* xfull = bars;           // XST (64 cp.async arrivals: two producer warps)
     uint64_t* xempty = bars + XST;    // XST (operand threads)
     uint64_t* pfull = bars + 2 * XST; // 2
