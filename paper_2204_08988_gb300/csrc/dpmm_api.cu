@@ -249,7 +249,7 @@ static dpmm_status sparse_alloc(dpmm_ctx* c, int64_t N) {
     free_data(c);
     c->N = N;
     rearm_kernel_choice(c);
-    c->T_tiles = (int)((N + 255) / 256);
+    c->T_tiles = (int)((N + SORT_TILE - 1) / SORT_TILE);
     c->Gr = 1;
     bool ok = true;
     auto A = [&](auto** p, size_t bytes) { ok = ok && dalloc(p, bytes) == cudaSuccess; };
@@ -411,7 +411,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
     A(&c->bart, sizeof(double) * S * d);
     A(&c->lgs, sizeof(double) * (S + 1));
     A(&c->retry, sizeof(int) * S);
-    A(&c->tot, sizeof(int) * (K_max + 1));
+    A(&c->tot, sizeof(int) * (K_max + 2));  // starts, then the sort's completion counter
     // range records of the dense statistics kernels (the compressed-row path adds its
     // counts straight into the table)
     c->records_bytes = c->sparse ? 0 : sizeof(double) * (size_t)(c->G2 + K_max) * 2 * c->st.E;
@@ -537,7 +537,7 @@ dpmm_status dpmm_set_data(dpmm_ctx* c, const void* X, int64_t N, dpmm_dtype dt, 
     }
     if (c->sparse) return set_data_sparse(c, X, N, dt, on_device);
     const size_t esz = c->xdt == 0 ? 8 : (c->xdt == 1 ? 4 : 2);
-    c->T_tiles = (int)((N + 255) / 256);
+    c->T_tiles = (int)((N + SORT_TILE - 1) / SORT_TILE);
     // ranges of the statistics step: about one per 512 points, at most 2 x SMs (the CUDA-core
     // kernels run two CTAs per SM) or 1 x SMs for the tensor-core kernel (one CTA per SM: one
     // long range per CTA fills its pipeline once)

@@ -39,6 +39,7 @@ constexpr float GUMBEL_MAX_F32 = 17.5f;
 constexpr int SPARSE_MIN_D = 256;
 constexpr int DIRICHLET_MAX_D = 65536;
 constexpr int SP_LGT = 1 << 16;  // entries of the lgamma-difference table (counts below it)
+constexpr int SORT_TILE = 1024;  // points per tile of the counting sort (four rounds of 256 threads)
 
 __host__ __device__ inline void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                        uint32_t k1, uint32_t out[4]) {
@@ -278,7 +279,7 @@ struct dpmm_ctx {
     int* retry = nullptr;        // 3 K_max: slots whose FP32 parameter draw is redone in FP64
 
     // sort / reduction scratch
-    int T_tiles = 0;         // sort tiles of 256 points
+    int T_tiles = 0;         // sort tiles of SORT_TILE points
     int* hist = nullptr;     // K_max x T_tiles
     int* tot = nullptr;      // K_max + 1: totals, then starts
     int* idx = nullptr;      // N: points sorted by cluster

@@ -485,11 +485,30 @@ __global__ void derive_kernel(int kind, int d, int tf32, const int* dK, const do
     if (kind == DPMM_PRIOR_NIW) {
         const double* W = p_W + (size_t)s * d * d;
         const double* mu = p_mu + (size_t)s * d;
-        for (int e = tid; e < d * d; e += nt) q_W[(size_t)s * d * d + e] = (float)W[e];
+        for (int e0 = 0; e0 < d * d; e0 += 8 * nt) {  // eight loads in flight per thread
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * nt + tid;
+                v[u] = e < d * d ? W[e] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * nt + tid;
+                if (e < d * d) q_W[(size_t)s * d * d + e] = (float)v[u];
+            }
+        }
         for (int j = tid; j < d; j += nt) {
             q_mu[(size_t)s * d + j] = (float)mu[j];
-            double b = 0.0;  // b_j = sum_l mu_l W_lj, with W as the tensor cores see it
-            for (int l = 0; l <= j; ++l) b += mu[l] * (tf32 ? (double)round_tf32((float)W[l * d + j]) : W[l * d + j]);
+            // b_j = sum_l mu_l W_lj (l <= j: W is upper triangular), with W as the tensor
+            // cores see it, in the order l = 0, 1, ...; a fixed trip count lets the loads of
+            // several rows be in flight at once (the FMA chain is the only serial part)
+            double b = 0.0;
+#pragma unroll 8
+            for (int l = 0; l < d; ++l) {
+                const double w = W[l * d + j], m = mu[l];
+                if (l <= j) b = fma(m, tf32 ? (double)round_tf32((float)w) : w, b);
+            }
             q_b[(size_t)s * d + j] = (float)b;
             p_b[(size_t)s * d + j] = b;  // read by the tensor-core image builds
             if (s % 3 == 0) {

@@ -342,21 +342,28 @@ struct DecArgs {
 #define DEC_KMAX 1024
 
 // Dynamic shared memory: the accept flags (one byte per proposal) when they fit in
-// dyn_flags bytes, so that the sequential walk reads shared memory only.
+// dyn_flags bytes, so that the sequential walk reads shared memory only.  The
+// bookkeeping (live clusters, split targets, new ids, ages, relabel maps) is done by
+// ballot prefix counts over chunks of 32 clusters in cluster order, which gives the ids
+// a sequential walk gives; only the merge walk is sequential (on bit masks for K <= 64).
 __global__ void decision_kernel(DecArgs a, int dyn_flags) {
-    __shared__ int live[DEC_KMAX], cid[DEC_KMAX], split_to[DEC_KMAX], merged_into[DEC_KMAX], head[DEC_KMAX];
-    __shared__ int newid[DEC_KMAX], newid_split[DEC_KMAX], src[DEC_KMAX], nage[DEC_KMAX];
-    __shared__ int s_K, s_Knew;
-    __shared__ double cnt[DEC_KMAX];
+    __shared__ int live[DEC_KMAX], split_to[DEC_KMAX], merged_into[DEC_KMAX], head[DEC_KMAX];
+    __shared__ int newid[DEC_KMAX], newid_split[DEC_KMAX], src[DEC_KMAX], nage[DEC_KMAX], cid[DEC_KMAX];
+    __shared__ unsigned long long rowm[64];
+    __shared__ int s_Kc, s_nsplit, s_nrej, s_nmerge, s_nid;
     extern __shared__ unsigned char flg[];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned below = (1u << lane) - 1u;
     const int K = *a.s.dK;
     const int d = a.s.L.d;
     const int nflags = K + K * (K - 1) / 2;
     const bool staged = a.sm_enabled && nflags <= dyn_flags;
     for (int k = tid; k < K; k += blockDim.x) {
-        cnt[k] = smv(a.s, k, -1, d, d);
+        live[k] = a.labels_ran ? (smv(a.s, k, -1, d, d) > 0) : 1;
         nage[k] = a.age[k];
+        split_to[k] = -1;
+        merged_into[k] = -1;
+        head[k] = 0;
     }
     if (staged) {
         for (int q = tid; q < nflags; q += blockDim.x) flg[q] = (unsigned char)(q < K ? a.acc[q] : a.acc[a.s.K_max + q - K]);
@@ -364,130 +371,163 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
     __syncthreads();
     auto acc_split = [&](int k) { return staged ? (int)flg[k] : a.acc[k]; };
     auto acc_merge = [&](int p) { return staged ? (int)flg[K + p] : a.acc[a.s.K_max + p]; };
-    if (tid == 0) {
+    // splits: the accepted proposals of live clusters past burn-out, in cluster order, take
+    // the ids Kc, Kc + 1, ... below K_max; the ones beyond K_max are rejected
+    if (tid < 32) {
         int Kc = 0;
-        for (int k = 0; k < K; ++k) {
-            double nk = cnt[k];
-            live[k] = a.labels_ran ? (nk > 0) : 1;
-            cid[k] = live[k] ? Kc++ : -1;
-            split_to[k] = -1;
-            merged_into[k] = -1;
-            head[k] = 0;
-        }
-        int nsplit = 0, nrej = 0;
+        for (int k0 = 0; k0 < K; k0 += 32) Kc += __popc(__ballot_sync(0xffffffffu, k0 + lane < K && live[k0 + lane]));
+        int want = 0, ns = 0;
         if (a.sm_enabled) {
-            int S = Kc;
-            for (int k = 0; k < K; ++k) {
-                if (!live[k]) continue;
-                if (nage[k] < a.burn_out) continue;
-                if (acc_split(k)) {
-                    if (S >= a.s.K_max) {
-                        ++nrej;
-                        continue;
-                    }
-                    split_to[k] = S++;
-                    ++nsplit;
-                }
+            const int room = a.s.K_max - Kc;
+            for (int k0 = 0; k0 < K; k0 += 32) {
+                const int k = k0 + lane;
+                const bool w = k < K && live[k] && nage[k] >= a.burn_out && acc_split(k);
+                const unsigned m = __ballot_sync(0xffffffffu, w);
+                const int r = want + __popc(m & below);
+                if (w && r < room) split_to[k] = Kc + r;
+                want += __popc(m);
             }
+            ns = min(want, max(room, 0));
         }
-        s_K = nsplit;  // carried to the merge walk below
-        s_Knew = nrej;
+        if (lane == 0) {
+            s_Kc = Kc;
+            s_nsplit = ns;
+            s_nrej = want - ns;
+        }
     }
     __syncthreads();
     // merges: for k1 in order, the first eligible k2 > k1 whose proposal is accepted
-    // (found 32 candidates at a time by warp 0; same outcome as the plain double loop)
-    __shared__ int s_nmerge;
+    // (eligible: live, not split, not merged, not already a merge's head)
     if (tid < 32) {
         int nm = 0;
         if (a.sm_enabled) {
-            auto elig = [&](int k) { return live[k] && split_to[k] < 0 && merged_into[k] < 0 && !head[k]; };
-            for (int k1 = 0; k1 < K; ++k1) {
-                if (!elig(k1)) continue;
-                int found = -1;
-                for (int b0 = k1 + 1; b0 < K && found < 0; b0 += 32) {
-                    const int k2 = b0 + tid;
-                    const bool ok = k2 < K && elig(k2) && acc_merge(k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1));
-                    const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    if (m) found = b0 + __ffs(m) - 1;
+            if (K <= 64) {
+                for (int k1 = lane; k1 < K; k1 += 32) {  // bit k2 of row k1: pair (k1, k2) accepted
+                    unsigned long long row = 0;
+                    const int p0 = k1 * (2 * K - k1 - 1) / 2 - k1 - 1;
+                    for (int k2 = k1 + 1; k2 < K; ++k2)
+                        if (acc_merge(p0 + k2)) row |= 1ull << k2;
+                    rowm[k1] = row;
                 }
-                if (found >= 0) {
-                    if (tid == 0) {
-                        merged_into[found] = k1;
-                        head[k1] = 1;
-                    }
-                    ++nm;
+                unsigned long long el = 0;
+                for (int k0 = 0; k0 < K; k0 += 32) {
+                    const int k = k0 + lane;
+                    el |= (unsigned long long)__ballot_sync(0xffffffffu, k < K && live[k] && split_to[k] < 0) << k0;
                 }
                 __syncwarp();
+                if (lane == 0) {
+                    for (int k1 = 0; k1 < K; ++k1) {
+                        if (!((el >> k1) & 1ull)) continue;
+                        const unsigned long long cand = el & rowm[k1];
+                        if (cand) {
+                            const int k2 = __ffsll((long long)cand) - 1;
+                            merged_into[k2] = k1;
+                            head[k1] = 1;
+                            el &= ~((1ull << k1) | (1ull << k2));
+                            ++nm;
+                        }
+                    }
+                }
+            } else {  // 32 candidates at a time by the warp; same outcome as the plain double loop
+                auto elig = [&](int k) { return live[k] && split_to[k] < 0 && merged_into[k] < 0 && !head[k]; };
+                for (int k1 = 0; k1 < K; ++k1) {
+                    if (!elig(k1)) continue;
+                    int found = -1;
+                    for (int b0 = k1 + 1; b0 < K && found < 0; b0 += 32) {
+                        const int k2 = b0 + lane;
+                        const bool ok = k2 < K && elig(k2) && acc_merge(k1 * (2 * K - k1 - 1) / 2 + (k2 - k1 - 1));
+                        const unsigned m = __ballot_sync(0xffffffffu, ok);
+                        if (m) found = b0 + __ffs(m) - 1;
+                    }
+                    if (found >= 0) {
+                        if (lane == 0) {
+                            merged_into[found] = k1;
+                            head[k1] = 1;
+                        }
+                        ++nm;
+                    }
+                    __syncwarp();
+                }
             }
         }
-        if (tid == 0) s_nmerge = nm;
+        if (lane == 0) s_nmerge = nm;
     }
     __syncthreads();
+    // new ids: the clusters that stay (live, not merged away) keep their order, then the
+    // second halves of the splits in cluster order; src[new id] = old cluster
+    if (tid < 32) {
+        int base = 0;
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int k = k0 + lane;
+            const bool sv = k < K && live[k] && merged_into[k] < 0;
+            const unsigned m = __ballot_sync(0xffffffffu, sv);
+            const int q = base + __popc(m & below);
+            if (k < K) newid[k] = sv ? q : -1;
+            if (sv) src[q] = k;
+            base += __popc(m);
+        }
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int k = k0 + lane;
+            const bool sp = k < K && split_to[k] >= 0;
+            const unsigned m = __ballot_sync(0xffffffffu, sp);
+            const int q = base + __popc(m & below);
+            if (sp) {
+                newid_split[k] = q;
+                src[q] = k;
+            }
+            base += __popc(m);
+        }
+        if (lane == 0) {
+            if (base == 0) {  // no cluster holds a point: the statistics disagree with the labels
+                atomicExch(a.derr, (int)DPMM_ENUMERIC);
+                newid[0] = 0;
+                src[0] = 0;
+                live[0] = 1;
+                base = 1;
+            }
+            s_nid = base;
+        }
+    }
+    __syncthreads();
+    const int nid = s_nid;
+    // ages: survivors one sweep older, clusters created by a split or merge start at 0
+    for (int q = tid; q < nid; q += blockDim.x) {
+        const int k = src[q];
+        const bool fresh = split_to[k] >= 0 || head[k];  // both halves of a split, and a merge
+        cid[q] = fresh ? 0 : nage[k] + (a.init_mode ? 0 : 1);
+    }
+    int* map_l = a.relabel;
+    int* map_r = a.relabel + a.s.K_max;
+    int* zmode = a.relabel + 2 * a.s.K_max;
+    for (int k = tid; k < K; k += blockDim.x) {
+        if (!live[k]) {
+            map_l[k] = map_r[k] = -1;
+            zmode[k] = 0;
+        } else if (split_to[k] >= 0) {
+            map_l[k] = newid[k];
+            map_r[k] = newid_split[k];
+            zmode[k] = 3;
+        } else if (merged_into[k] >= 0) {
+            map_l[k] = map_r[k] = newid[merged_into[k]];
+            zmode[k] = 2;
+        } else if (head[k]) {
+            map_l[k] = map_r[k] = newid[k];
+            zmode[k] = 1;
+        } else {
+            map_l[k] = map_r[k] = newid[k];
+            zmode[k] = 0;
+        }
+    }
     if (tid == 0) {
-        const int nsplit = s_K, nrej = s_Knew, nmerge = s_nmerge;
-        int Kc = 0;
-        for (int k = 0; k < K; ++k) Kc += live[k];
-        // nage holds the old ages; the new ones go to cid (free after the proposals)
-        int nid = 0;
-        for (int k = 0; k < K; ++k)
-            if (live[k] && merged_into[k] < 0) {
-                newid[k] = nid;
-                src[nid] = k;
-                ++nid;
-            } else {
-                newid[k] = -1;
-            }
-        for (int k = 0; k < K; ++k)
-            if (split_to[k] >= 0) {
-                newid_split[k] = nid;
-                src[nid] = k;
-                ++nid;
-            }
-        if (nid == 0) {  // no cluster holds a point: the statistics disagree with the labels
-            atomicExch(a.derr, (int)DPMM_ENUMERIC);
-            newid[0] = 0;
-            src[0] = 0;
-            live[0] = 1;
-            nid = 1;
-        }
-        // ages: survivors one sweep older, clusters created by a split or merge start at 0
-        for (int q = 0; q < nid; ++q) {
-            const int k = src[q];
-            const bool fresh = split_to[k] >= 0 || head[k];  // both halves of a split, and a merge
-            cid[q] = fresh ? 0 : nage[k] + (a.init_mode ? 0 : 1);
-        }
-        int* map_l = a.relabel;
-        int* map_r = a.relabel + a.s.K_max;
-        int* zmode = a.relabel + 2 * a.s.K_max;
-        for (int k = 0; k < K; ++k) {
-            if (!live[k]) {
-                map_l[k] = map_r[k] = -1;
-                zmode[k] = 0;
-            } else if (split_to[k] >= 0) {
-                map_l[k] = newid[k];
-                map_r[k] = newid_split[k];
-                zmode[k] = 3;
-            } else if (merged_into[k] >= 0) {
-                map_l[k] = map_r[k] = newid[merged_into[k]];
-                zmode[k] = 2;
-            } else if (head[k]) {
-                map_l[k] = map_r[k] = newid[k];
-                zmode[k] = 1;
-            } else {
-                map_l[k] = map_r[k] = newid[k];
-                zmode[k] = 0;
-            }
-        }
+        const int nsplit = s_nsplit, nmerge = s_nmerge;
         a.counters[0] = nsplit;
         a.counters[1] = nmerge;
-        a.counters[2] = nrej;
-        a.counters[3] = K - Kc;
+        a.counters[2] = s_nrej;
+        a.counters[3] = K - s_Kc;
         a.counters[4] = (nid != K || nsplit || nmerge) ? 1 : 0;
-        s_K = K;
-        s_Knew = nid;
     }
     __syncthreads();
-    const int Kn = s_Knew;
+    const int Kn = nid;
     // the statistics shifts follow their clusters (Gaussian only: the multinomial
     // statistics are not shifted, and d x K can be 20,000 x 100 there)
     if (a.s.kind == DPMM_PRIOR_NIW)

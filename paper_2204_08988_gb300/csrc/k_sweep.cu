@@ -135,97 +135,141 @@ __global__ void __launch_bounds__(256) labels_simt_kernel(int kind, int d, int x
 }
 
 // ------------------------------------------------------------------ counting sort
+// Stable counting sort of the points by cluster (the order the statistics step visits
+// them in), in tiles of SORT_TILE points: four rounds of 256, one point per thread per
+// round, so that a tile's points are ranked in index order (round, warp, lane).
 __global__ void hist_kernel(const int32_t* z, int64_t N, int T_tiles, int Kmax, const int* gate, int* hist) {
     if (gate && *gate == 0) return;
     extern __shared__ int cnt[];
     const int t = blockIdx.x;
     for (int k = threadIdx.x; k < Kmax; k += blockDim.x) cnt[k] = 0;
-    __syncthreads();
-    int64_t i = (int64_t)t * 256 + threadIdx.x;
-    if (i < N) {
-        const int k = z[i];
-        if ((unsigned)k < (unsigned)Kmax) atomicAdd(&cnt[k], 1);  // labels are always in range
+    int zq[SORT_TILE / 256];
+#pragma unroll
+    for (int q = 0; q < SORT_TILE / 256; ++q) {
+        const int64_t i = (int64_t)t * SORT_TILE + q * 256 + threadIdx.x;
+        zq[q] = i < N ? z[i] : -1;
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < SORT_TILE / 256; ++q)
+        if ((unsigned)zq[q] < (unsigned)Kmax) atomicAdd(&cnt[zq[q]], 1);  // labels are always in range
     __syncthreads();
     for (int k = threadIdx.x; k < Kmax; k += blockDim.x) hist[(size_t)k * T_tiles + t] = cnt[k];
 }
 
-// exclusive scan of each cluster's row of tile counts; row total into tot[k]
-__global__ void scan_kernel(int* hist, int T_tiles, const int* dK, const int* gate, int* tot) {
+// Exclusive scan of each cluster's row of tile counts (block k), row total into tot[k];
+// the last block to finish turns the totals into the clusters' starts (exclusive prefix,
+// tot[K] = N) and re-arms the counter *done for the next launch.
+__global__ void scan_kernel(int* hist, int T_tiles, const int* dK, const int* gate, int* tot, int* done) {
     if (gate && *gate == 0) return;
-    const int k = blockIdx.x;
-    if (k >= *dK) {
-        if (threadIdx.x == 0) tot[k] = 0;
-        return;
-    }
+    const int k = blockIdx.x, K = *dK;
     __shared__ int wsum[32];
-    int* row = hist + (size_t)k * T_tiles;
-    const int per = (T_tiles + blockDim.x - 1) / blockDim.x;
-    const int a = threadIdx.x * per, b = min(T_tiles, a + per);
-    int s = 0;
-    for (int t = a; t < b; ++t) s += row[t];
-    // block exclusive scan of s
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        int v = lane < nw ? wsum[lane] : 0;
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (k < K) {
+        int* row = hist + (size_t)k * T_tiles;
+        const int per = (T_tiles + blockDim.x - 1) / blockDim.x;
+        const int a = threadIdx.x * per, b = min(T_tiles, a + per);
+        int s = 0;
+        for (int t = a; t < b; ++t) s += row[t];
+        // block exclusive scan of s
+        int x = s;
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (lane < nw) wsum[lane] = v;
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int nw = blockDim.x >> 5;
+            int v = lane < nw ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (lane < nw) wsum[lane] = v;
+        }
+        __syncthreads();
+        int excl = x - s + (w > 0 ? wsum[w - 1] : 0);
+        for (int t = a; t < b; ++t) {
+            int v = row[t];
+            row[t] = excl;
+            excl += v;
+        }
+        if (threadIdx.x == blockDim.x - 1) {
+            tot[k] = excl;
+            __threadfence();
+        }
+    } else if (threadIdx.x == 0) {
+        tot[k] = 0;
+        __threadfence();
     }
     __syncthreads();
-    int excl = x - s + (w > 0 ? wsum[w - 1] : 0);
-    for (int t = a; t < b; ++t) {
-        int v = row[t];
-        row[t] = excl;
-        excl += v;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(done, 1) == (int)gridDim.x - 1;
     }
-    if (threadIdx.x == blockDim.x - 1) tot[k] = excl;
-}
-
-// totals -> starts (exclusive prefix), starts[K] = N
-__global__ void starts_kernel(const int* dK, const int* gate, int* tot) {
-    if (gate && *gate == 0) return;
-    if (threadIdx.x != 0) return;
-    int K = *dK, acc = 0;
-    for (int k = 0; k < K; ++k) {
-        int v = tot[k];
-        tot[k] = acc;
-        acc += v;
+    __syncthreads();
+    if (!s_last || w != 0) return;
+    __threadfence();
+    int acc = 0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int v = k0 + lane < K ? __ldcg(tot + k0 + lane) : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (k0 + lane < K) tot[k0 + lane] = acc + x - v;
+        acc += __shfl_sync(0xffffffffu, x, 31);
     }
-    tot[K] = acc;
+    if (lane == 0) {
+        tot[K] = acc;
+        *done = 0;
+    }
 }
 
 __global__ void scatter_kernel(const int32_t* z, int64_t N, int T_tiles, const int* hist, const int* starts,
                                const int* gate, int Kmax, int* idx) {
     if (gate && *gate == 0) return;
-    extern __shared__ int wc[];  // 8 warps x Kmax
+    extern __shared__ int wc[];  // 8 warps x Kmax counts of the round, then Kmax running bases
+    int* base = wc + 8 * Kmax;
     const int t = blockIdx.x;
     for (int e = threadIdx.x; e < 8 * Kmax; e += blockDim.x) wc[e] = 0;
-    __syncthreads();
-    const int64_t i = (int64_t)t * 256 + threadIdx.x;
+    for (int k = threadIdx.x; k < Kmax; k += blockDim.x) base[k] = starts[k] + hist[(size_t)k * T_tiles + t];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int zi = i < N ? z[i] : -1;
-    const bool live = (unsigned)zi < (unsigned)Kmax;  // labels are always in range
-    const int k = live ? zi : -1 - lane;  // dead lanes never match live ones
-    unsigned m = __match_any_sync(0xffffffffu, k);
-    int r = __popc(m & ((1u << lane) - 1u));
-    if (live && r == 0) wc[w * Kmax + k] = __popc(m);
+    int zq[SORT_TILE / 256];
+#pragma unroll
+    for (int q = 0; q < SORT_TILE / 256; ++q) {
+        const int64_t i = (int64_t)t * SORT_TILE + q * 256 + threadIdx.x;
+        zq[q] = i < N ? z[i] : -1;
+    }
     __syncthreads();
-    if (live) {
-        int before = 0;
-        for (int v = 0; v < w; ++v) before += wc[v * Kmax + k];
-        int pos = starts[k] + hist[(size_t)k * T_tiles + t] + before + r;
-        idx[pos] = (int)i;
+#pragma unroll
+    for (int q = 0; q < SORT_TILE / 256; ++q) {
+        const int64_t i = (int64_t)t * SORT_TILE + q * 256 + threadIdx.x;
+        const bool live = (unsigned)zq[q] < (unsigned)Kmax;  // labels are always in range
+        const int k = live ? zq[q] : -1 - lane;             // dead lanes never match live ones
+        const unsigned m = __match_any_sync(0xffffffffu, k);
+        const int r = __popc(m & ((1u << lane) - 1u));
+        if (live && r == 0) wc[w * Kmax + k] = __popc(m);
+        __syncthreads();
+        if (live) {
+            int before = 0;
+            for (int v = 0; v < w; ++v) before += wc[v * Kmax + k];
+            idx[base[k] + before + r] = (int)i;
+        }
+        __syncthreads();
+        // the bases move past this round's points; the counts are cleared for the next
+        for (int kk = threadIdx.x; kk < Kmax; kk += blockDim.x) {
+            int s = 0;
+            for (int v = 0; v < 8; ++v) {
+                s += wc[v * Kmax + kk];
+                wc[v * Kmax + kk] = 0;
+            }
+            base[kk] += s;
+        }
+        __syncthreads();
     }
 }
 
@@ -1307,12 +1351,12 @@ static cudaError_t sort_impl(dpmm_ctx* c, const int* gate) {
     prof_begin(c, "sort");
     hist_kernel<<<c->T_tiles, 256, sizeof(int) * c->K_max, c->stream>>>(c->z, c->N, c->T_tiles, c->K_max, gate,
                                                                          c->hist);
-    scan_kernel<<<c->K_max, 1024, 0, c->stream>>>(c->hist, c->T_tiles, c->dK, gate, c->tot);
-    starts_kernel<<<1, 32, 0, c->stream>>>(c->dK, gate, c->tot);
-    scatter_kernel<<<c->T_tiles, 256, sizeof(int) * 8 * c->K_max, c->stream>>>(c->z, c->N, c->T_tiles, c->hist, c->tot,
+    // tot holds K_max + 1 starts, then the scan's completion counter
+    scan_kernel<<<c->K_max, 1024, 0, c->stream>>>(c->hist, c->T_tiles, c->dK, gate, c->tot, c->tot + c->K_max + 1);
+    scatter_kernel<<<c->T_tiles, 256, sizeof(int) * 9 * c->K_max, c->stream>>>(c->z, c->N, c->T_tiles, c->hist, c->tot,
                                                                                gate, c->K_max, c->idx);
     prof_end(c, "sort");
-    c->nlaunch += 4;
+    c->nlaunch += 3;
     return cudaGetLastError();
 }
 
