@@ -444,7 +444,7 @@ dpmm_status dpmm_create(const dpmm_prior* prior, double alpha, int d, int K_max,
             ok = ok && cudaDeviceSynchronize() == cudaSuccess;
         }
     }
-    A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1 + 6 * (size_t)K_max));
+    A(&c->Ltab, sizeof(double) * (3 * (size_t)K_max + 3 * ((size_t)K_max * (K_max - 1) / 2) + 1 + 6 * (size_t)K_max));
     A(&c->relabel, sizeof(int) * 4 * K_max);
     A(&c->acc, sizeof(int) * ((size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1));
     A(&c->center, sizeof(double) * (2 * (size_t)d + (size_t)d * d));

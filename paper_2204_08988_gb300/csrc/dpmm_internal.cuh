@@ -290,7 +290,8 @@ struct dpmm_ctx {
 
     // split/merge scratch
     double* Ltab = nullptr;  // 3 K_max + K_max (K_max - 1)/2 log marginals, 1 spare, then per slot
-                             // lgamma(n_s) and lgamma(alpha/2 + n_s) (6 K_max)
+                             // lgamma(n_s) and lgamma(alpha/2 + n_s) (6 K_max), then per merge
+                             // pair lgamma(n) and lgamma(alpha + n) (K_max (K_max - 1))
     int* relabel = nullptr;  // 4 K_max
     int* acc = nullptr;      // K_max + K_max (K_max - 1)/2 accept flags of the split/merge proposals
     double* canon = nullptr; // canonical (n, xbar, C) per cluster and sub-cluster: 3 K_max x (1 + d + d d)

@@ -51,6 +51,8 @@ __device__ inline double lmvgamma(double x, int d) {
 // per-slot lgamma table after the log marginals: lg[2 s] = lgamma(n_s),
 // lg[2 s + 1] = lgamma(alpha / 2 + n_s)
 __host__ __device__ inline size_t lg_offset(int K_max) { return 3 * (size_t)K_max + (size_t)K_max * (K_max - 1) / 2 + 1; }
+// then lgamma(n) and lgamma(alpha + n) of every merge pair's n = n_k1 + n_k2 (two per pair)
+__host__ __device__ inline size_t lg_pair_offset(int K_max) { return lg_offset(K_max) + 6 * (size_t)K_max; }
 
 __device__ inline void pair_of(int p, int K, int& k1, int& k2) {
     int r = 0, off = 0;
@@ -79,9 +81,14 @@ __device__ __forceinline__ void marginal_item(const SMArgs& a, double* Ltab, int
         h = -1;
     }
     double* out = Ltab + (e < 3 * K ? e : 3 * a.K_max + (e - 3 * K));
-    if (e < 3 * K && (tid == 32 || tid == 33)) {  // the slot's lgamma terms for the Hastings ratios
-        const double ns = smv(a, k1, h, d, d);
-        Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
+    if (tid == 32 || tid == 33) {  // the slot's or the pair's lgamma terms for the Hastings ratios
+        if (e < 3 * K) {
+            const double ns = smv(a, k1, h, d, d);
+            Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
+        } else {
+            const double nm = smv(a, k1, -1, d, d) + smv(a, k2, -1, d, d);
+            Ltab[lg_pair_offset(a.K_max) + 2 * (e - 3 * K) + (tid - 32)] = lgamma(tid == 32 ? nm : a.alpha + nm);
+        }
     }
     if (a.kind == DPMM_PRIOR_DIRICHLET) {
         // the prior's terms (sum beta, lgamma(sum beta), sum lgamma(beta_j)) come from the host
@@ -220,9 +227,14 @@ __device__ __forceinline__ void marginal_counts_item(const SMArgs& a, const Src&
         h = -1;
     }
     double* out = Ltab + (e < 3 * K ? e : 3 * a.K_max + (e - 3 * K));
-    if (e < 3 * K && (tid == 32 || tid == 33)) {  // the slot's lgamma terms for the Hastings ratios
-        const double ns = smv(a, k1, h, d, d);
-        Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
+    if (tid == 32 || tid == 33) {  // the slot's or the pair's lgamma terms for the Hastings ratios
+        if (e < 3 * K) {
+            const double ns = smv(a, k1, h, d, d);
+            Ltab[lg_offset(a.K_max) + 2 * e + (tid - 32)] = lgamma(tid == 32 ? ns : 0.5 * a.alpha + ns);
+        } else {
+            const double nm = smv(a, k1, -1, d, d) + smv(a, k2, -1, d, d);
+            Ltab[lg_pair_offset(a.K_max) + 2 * (e - 3 * K) + (tid - 32)] = lgamma(tid == 32 ? nm : a.alpha + nm);
+        }
     }
     using V = decltype(cnt(0, 0));  // the source's own type: FP32 sums stay off the FP64 pipe
     const int s0 = 2 * k1 + (h < 0 ? 0 : h);
@@ -313,9 +325,10 @@ __global__ void __launch_bounds__(32) hastings_kernel(SMArgs a, const double* Lt
         pair_of(p, K, k1, k2);
         int ok = 0;
         if (live(k1) && live(k2)) {
-            const double n1 = smv(a, k1, -1, d, d), n2 = smv(a, k2, -1, d, d), nm = n1 + n2;
-            const double lH = lgamma(nm) - la - lg[2 * (3 * k1)] - lg[2 * (3 * k2)] + Ltab[3 * a.K_max + p] -
-                              Ltab[3 * k1] - Ltab[3 * k2] + a.lg_alpha - lgamma(al + nm) + lg[2 * (3 * k1) + 1] +
+            // lgamma(n_k1 + n_k2) and lgamma(alpha + n_k1 + n_k2), formed by the marginal kernel
+            const double* lgp = Ltab + lg_pair_offset(a.K_max) + 2 * (size_t)p;
+            const double lH = lgp[0] - la - lg[2 * (3 * k1)] - lg[2 * (3 * k2)] + Ltab[3 * a.K_max + p] -
+                              Ltab[3 * k1] - Ltab[3 * k2] + a.lg_alpha - lgp[1] + lg[2 * (3 * k1) + 1] +
                               lg[2 * (3 * k2) + 1] - 2.0 * a.lg_half_alpha;
             ok = log(d_uniform(key, (uint32_t)cid(k1), TAG_MERGE, (uint32_t)cid(k2))) < lH;
         }

@@ -1282,9 +1282,16 @@ __global__ void combine_kernel(const double* rec, const int* starts, const int* 
         for (int j = threadIdx.x; j < d; j += blockDim.x) shift_stats[(size_t)k * d + j] = shift_new[(size_t)k * d + j];
     if (e >= E) return;
     double v = 0.0;
-    if (cnt > 0) {
+    if (cnt > 0) {  // the ranges' records in order; four loads in flight at a time
         const int64_t g0 = st / R, g1 = (st + cnt - 1) / R;
-        for (int64_t g = g0; g <= g1; ++g) v += rec[((size_t)(g + k) * 2 + h) * E + e];
+        for (int64_t g = g0; g <= g1; g += 4) {
+            double r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) r[u] = g + u <= g1 ? rec[((size_t)(g + u + k) * 2 + h) * E + e] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (g + u <= g1) v += r[u];
+        }
     }
     stats[(size_t)kh * E + e] = v;
 }
@@ -1325,9 +1332,10 @@ static cudaError_t labels_simt_t(dpmm_ctx* c, uint64_t seed, const int* gate) {
     auto kern = c->dbg_scores ? labels_simt_kernel<T, XT, true> : labels_simt_kernel<T, XT, false>;
     cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (ea != cudaSuccess) return ea;
-    // a gated launch usually exits at once: keep its grid small and let CTAs stride
+    // a gated launch usually exits at once: one wave of CTAs (one per SM at this shared
+    // memory size) that stride over the tiles
     int64_t tiles = (c->N + TB - 1) / TB;
-    int grid = (int)(gate ? std::min<int64_t>(tiles, 4 * (int64_t)c->num_sms) : tiles);
+    int grid = (int)(gate ? std::min<int64_t>(tiles, (int64_t)c->num_sms) : tiles);
     kern<<<grid, TB, sm, c->stream>>>(c->kind, d, c->xs, c->N, (const XT*)c->X, pview<T>(c), c->dK, c->diter, seed,
                                       CB, gate, c->dbg_scores, c->z);
     return cudaGetLastError();

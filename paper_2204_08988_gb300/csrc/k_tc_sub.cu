@@ -489,17 +489,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) substats_tc_kernel(Args a) {
                     *(float4*)(Ac + 32 * 128) = make_float4(lo[0], lo[1], lo[2], lo[3]);
                     *(float4*)Bc = make_float4(b0[0], b0[1], b0[2], b0[3]);
                     *(float4*)(Bc + 40 * 128) = make_float4(b1[0], b1[1], b1[2], b1[3]);
-                    if (j == 0) {
-                        float m0[4], m1[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const uint32_t he = (hw >> (8 * e)) & 0xFFu;
-                            m0[e] = he == 0 ? 1.f : 0.f;
-                            m1[e] = he == 1 ? 1.f : 0.f;
-                        }
-                        unsigned char* Bm = SB + hf * SB_BUF + u * (SB_ROWS * 128) + (wb << 4);
-                        *(float4*)(Bm + 32 * 128) = make_float4(m0[0], m0[1], m0[2], m0[3]);
-                        *(float4*)(Bm + 72 * 128) = make_float4(m1[0], m1[1], m1[2], m1[3]);
+                    {  // the mask rows (m_1 at row 32, m_2 at row 72) of the quad: lanes 0-7, one value each
+                        const uint32_t he = (hw >> (8 * (j & 3))) & 0xFFu;
+                        const float mv = he == (uint32_t)((j >> 2) & 1) ? 1.f : 0.f;
+                        if (j < 8)
+                            *(float*)(SB + hf * SB_BUF + u * (SB_ROWS * 128) + ((j >> 2) ? 72 : 32) * 128 + (wb << 4) +
+                                      (j & 3) * 4) = mv;
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
