@@ -13,7 +13,19 @@ namespace dpmm {
 __device__ inline void stage_slot(const double* S, int E, int k, int h, double* out) {
     const double* s0 = S + (size_t)(2 * k + (h < 0 ? 0 : h)) * E;
     const double* s1 = S + (size_t)(2 * k + 1) * E;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) out[e] = h < 0 ? s0[e] + s1[e] : s0[e];
+    const int nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < E; e0 += 4 * nt) {  // four entries' loads in flight per thread
+        double a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * nt;
+            a[u] = e < E ? s0[e] : 0.0;
+            b[u] = e < E && h < 0 ? s1[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e0 + u * nt < E) out[e0 + u * nt] = h < 0 ? a[u] + b[u] : a[u];
+    }
 }
 
 // Row i0 and column l0 (l0 <= i0) of entry e of a lower triangle enumerated row by row.

@@ -276,28 +276,50 @@ __global__ void niw_params_kernel(StatView sv, const double* shift_stats, NiwPri
         __syncthreads();
     }
     const double* sh_k = shift_stats + (size_t)k * d;
+    // xbar - m0 per coordinate (FP64), for the Psi_n build below; in the factorisation's
+    // scratch columns, which it overwrites only after that build
+    double* dxm = (double*)(((uintptr_t)cols + 7) & ~(uintptr_t)7);
     for (int j = tid; j < d; j += nt) {
         const double xbar = n > 0 ? sh_k[j] + M(j, d) * rn : 0.0;
         mn[j] = (T)((pr.kappa0 * pr.m0s[j] + n * xbar) * rkn);
+        dxm[j] = xbar - pr.m0s[j];
         Bd[j] = (T)bart[(size_t)s * d + j];
         acc[j] = (T)eps[(size_t)s * d + j];
     }
     if (w_in_smem)  // the normals above the diagonal (zero below), drawn by variates_kernel
-        for (int e = tid; e < d * d; e += nt) W[e] = (T)Wg[e];
+        for (int e0 = tid; e0 < d * d; e0 += 8 * nt) {  // eight loads in flight per thread
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = e0 + u * nt < d * d ? Wg[e0 + u * nt] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (e0 + u * nt < d * d) W[e0 + u * nt] = (T)v[u];
+        }
     __syncthreads();
     // Psi_n = Psi0 + C + (kappa0 n / kappa_n)(xbar - m0)(xbar - m0)^T, C = S2 - S1 S1^T / n
     // (in FP64: the subtraction cancels); lower triangle only: the factorisation reads
     // nothing else
     const double f = n > 0 ? pr.kappa0 * n * rkn : 0.0;
-    for (int e = tid; e < d * (d + 1) / 2; e += nt) {
-        int j, l;
-        tri_index(e, j, l);  // l <= j
-        double C = 0.0;
-        if (n > 0) C = M(l, j) - M(l, d) * M(j, d) * rn;
-        const double xj = n > 0 ? sh_k[j] + M(j, d) * rn : 0.0, xl = n > 0 ? sh_k[l] + M(l, d) * rn : 0.0;
-        const T a = (T)(pr.psi0[j * d + l] + C + f * (xj - pr.m0s[j]) * (xl - pr.m0s[l]));
-        A[j * ld + l] = a;
-        if (l == j) dg[j] = a;
+    const int ntri = d * (d + 1) / 2;
+    for (int e0 = tid; e0 < ntri; e0 += 4 * nt) {  // the Psi0 entries of four entries loaded first
+        int jj[4], ll[4];
+        double p0[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = min(e0 + u * nt, ntri - 1);
+            tri_index(e, jj[u], ll[u]);  // l <= j
+            p0[u] = pr.psi0[jj[u] * d + ll[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (e0 + u * nt >= ntri) break;
+            const int j = jj[u], l = ll[u];
+            double C = 0.0;
+            if (n > 0) C = M(l, j) - M(l, d) * M(j, d) * rn;
+            const T a = (T)(p0[u] + C + f * dxm[j] * dxm[l]);
+            A[j * ld + l] = a;
+            if (l == j) dg[j] = a;
+        }
     }
     __syncthreads();
     chol_ldl_t<T>(A, d, ld, piv, rd, cols, dg, sizeof(T) == 4 ? T(1.0 / 1024) : T(0), &s_fail);

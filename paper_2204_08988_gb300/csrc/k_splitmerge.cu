@@ -129,7 +129,8 @@ __device__ __forceinline__ void marginal_item(const SMArgs& a, double* Ltab, int
     double* piv = x2 + d;      // pivots of the factorisation
     double* rs = piv + d;
     double* cols = rs + d;     // 4 d: the factorisation's scaled panel columns
-    double* S1 = cols + 4 * d; // staged statistics of (k1, h) and of cluster k2 (E each)
+    double* dxb = cols + 4 * d;  // merged mean - m0
+    double* S1 = dxb + d;      // staged statistics of (k1, h) and of cluster k2 (E each)
     double* S2 = S1 + a.L.E;
     const bool staged = a.stage != 0;
     if (staged) {
@@ -159,21 +160,33 @@ __device__ __forceinline__ void marginal_item(const SMArgs& a, double* Ltab, int
         x1[j] = m1;
         x2[j] = m2;
         xb[j] = n > 0 ? (n1 * m1 + n2 * m2) * rn : 0.0;
+        dxb[j] = xb[j] - a.m0s[j];
     }
     __syncthreads();
     const double kn = a.kappa0 + n, nun = a.nu0 + n;
     const double f = n > 0 ? a.kappa0 * n / kn : 0.0;
-    for (int q0 = tid; q0 < d * (d + 1) / 2; q0 += nt) {
-        int j, l;
-        tri_index(q0, j, l);  // l <= j: the factorisation reads nothing else
-        const int q = j * ld + l;
-        double C = 0.0;
-        if (n1 > 0) C += M1(l, j) - M1(l, d) * M1(j, d) * r1;
-        if (k2 >= 0 && n2 > 0) {
-            C += M2(l, j) - M2(l, d) * M2(j, d) * r2;
-            if (n1 > 0) C += w12 * (x1[j] - x2[j]) * (x1[l] - x2[l]);
+    const int ntri = d * (d + 1) / 2;
+    for (int e0 = tid; e0 < ntri; e0 += 4 * nt) {  // the Psi0 entries of four entries loaded first
+        int jj[4], ll[4];
+        double p0[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            tri_index(min(e0 + u * nt, ntri - 1), jj[u], ll[u]);  // l <= j: the factorisation reads nothing else
+            p0[u] = a.psi0[jj[u] * d + ll[u]];
         }
-        A[q] = a.psi0[j * d + l] + C + f * (xb[j] - a.m0s[j]) * (xb[l] - a.m0s[l]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (e0 + u * nt >= ntri) break;
+            const int j = jj[u], l = ll[u];
+            const int q = j * ld + l;
+            double C = 0.0;
+            if (n1 > 0) C += M1(l, j) - M1(l, d) * M1(j, d) * r1;
+            if (k2 >= 0 && n2 > 0) {
+                C += M2(l, j) - M2(l, d) * M2(j, d) * r2;
+                if (n1 > 0) C += w12 * (x1[j] - x2[j]) * (x1[l] - x2[l]);
+            }
+            A[q] = p0[u] + C + f * dxb[j] * dxb[l];
+        }
     }
     __syncthreads();
     chol_ldl(A, d, ld, piv, rs, cols, derr);
@@ -558,26 +571,25 @@ __global__ void decision_kernel(DecArgs a, int dyn_flags) {
 __global__ void relabel_kernel(int64_t N, const int* relabel, int Kmax, const int* gate, const uint32_t* diter,
                                uint64_t seed, int32_t* z, uint8_t* zbar, int* derr) {
     if (*gate == 0) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int k = z[i];
-    const int h = zbar[i];
-    if ((unsigned)k >= (unsigned)Kmax) {  // never for consistent state: keep memory safe, report
-        atomicExch(derr, (int)DPMM_ENUMERIC);
-        k = 0;
-    }
-    const int mode = relabel[2 * Kmax + k];
-    int nz = h ? relabel[Kmax + k] : relabel[k];
-    if (nz < 0) {  // a point in a cluster counted as empty
-        atomicExch(derr, (int)DPMM_ENUMERIC);
-        nz = 0;
-    }
-    z[i] = nz;
-    if (mode == 1) zbar[i] = 0;
-    else if (mode == 2) zbar[i] = 1;
-    else if (mode == 3) {
-        Key key{seed, diter[0], diter[1], diter[2]};
-        zbar[i] = d_uniform(key, (uint32_t)i, TAG_RESUB, 0) < 0.5 ? 0 : 1;
+    const Key key{seed, diter[0], diter[1], diter[2]};
+    // grid-stride: the launch is one wave, so that the usual gated-off launch is cheap
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        int k = z[i];
+        const int h = zbar[i];
+        if ((unsigned)k >= (unsigned)Kmax) {  // never for consistent state: keep memory safe, report
+            atomicExch(derr, (int)DPMM_ENUMERIC);
+            k = 0;
+        }
+        const int mode = relabel[2 * Kmax + k];
+        int nz = h ? relabel[Kmax + k] : relabel[k];
+        if (nz < 0) {  // a point in a cluster counted as empty
+            atomicExch(derr, (int)DPMM_ENUMERIC);
+            nz = 0;
+        }
+        z[i] = nz;
+        if (mode == 1) zbar[i] = 0;
+        else if (mode == 2) zbar[i] = 1;
+        else if (mode == 3) zbar[i] = d_uniform(key, (uint32_t)i, TAG_RESUB, 0) < 0.5 ? 0 : 1;
     }
 }
 
@@ -699,7 +711,8 @@ cudaError_t launch_splitmerge(dpmm_ctx* c, uint64_t seed, int labels_ran, int sm
 
 cudaError_t launch_relabel(dpmm_ctx* c, uint64_t seed) {
     prof_begin(c, "relabel");
-    relabel_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->N, c->relabel, c->K_max, c->counters + 4,
+    const unsigned grid = (unsigned)std::min<int64_t>((c->N + 255) / 256, 8 * (int64_t)c->num_sms);
+    relabel_kernel<<<grid, 256, 0, c->stream>>>(c->N, c->relabel, c->K_max, c->counters + 4,
                                                                          c->diter, seed, c->z, c->zbar, c->derr);
     prof_end(c, "relabel");
     c->nlaunch += 1;
