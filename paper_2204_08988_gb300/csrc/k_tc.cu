@@ -24,12 +24,14 @@
 // cluster skipped in an earlier group was outside an earlier (lower) best's window and so
 // is outside the final one.  The result is the same argmax as one pass over all clusters.
 //
-// CTA roles (576 threads, one CTA per SM, persistent over 128-point tiles):
+// CTA roles (608 threads, one CTA per SM, persistent over 128-point tiles):
 //   warp 0     : TMA producer (X tiles, 128 rows x 128 B, SWIZZLE_128B, 3 stages)
 //   warp 1     : TMEM allocation (512 columns) and the single-thread MMA issue
 //   warps 2-17 : epilogue, four warps (parts) per TMEM lane quarter, part p taking
-//                clusters p, p + 4, ... of a chunk; the parts exchange their running
-//                maxima before drawing and then merge their argmax per point.
+//                clusters p, p + 4, ... of a chunk; per tile each part publishes its two
+//                best scores and every score in one of two slots and moves on
+//   warp 18    : merge: per tile and point, the best over the parts, the Gumbel draws
+//                when needed, and the label (or the carried state).
 // The factor image of all clusters is copied once into shared memory (pre-swizzled
 // by tc_prepare).  Accumulators are double-buffered in TMEM (NBUF = 2 buffers of 256
 // columns; four buffers of 128 columns were slower: the cost per chunk is mostly fixed).
@@ -52,7 +54,8 @@ constexpr int XBYTES = BM * 128; // one X tile: 128 rows x 128 B
 constexpr int NPART = 4;         // epilogue warps per TMEM lane quarter
 constexpr int EPI0 = 2;          // first epilogue warp
 constexpr int NEPI = 4 * NPART;  // epilogue warps
-constexpr int NTHREADS = 32 * (EPI0 + NEPI);
+constexpr int MRG = EPI0 + NEPI; // the merge warp
+constexpr int NTHREADS = 32 * (MRG + 1);
 // A cluster can win the Gumbel-max only if its score is within G_MAX - G_MIN of the
 // best score (FP32 uniforms: 16.64 + 2.82), plus one nat for rounding.
 constexpr float WINDOW = 20.5f;
@@ -101,8 +104,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     unsigned char* bs = xs + XST * XBYTES;                      // cap_rows x 128
     unsigned char* bb = bs + (size_t)a.cap_rows * 128;          // cap_rows x 32
     float* ones = (float*)(bb + (size_t)a.cap_rows * 32);       // BM rows x 8, no swizzle
-    float* sbuf = ones + BM * 8;                                // (cap_rows / dn) clusters x BM
-    float* ct = sbuf + (size_t)(a.cap_rows / a.dn) * BM;         // 2 x Kmax: c_k of a group, by group parity
+    float* sbuf = ones + BM * 8;                                // 2 slots x capc clusters x BM
+    float* ct = sbuf + (size_t)2 * a.capc * BM;                  // 2 x Kmax: c_k of a group, by group parity
     uint64_t* bars = (uint64_t*)(((uintptr_t)(ct + 2 * a.Kmax) + 7) & ~(uintptr_t)7);
     uint64_t* full = bars;            // XST
     uint64_t* empty = full + XST;     // XST
@@ -110,14 +113,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
     uint64_t* tempty = tfull + NBUF;  // NBUF
     uint64_t* bload = tempty + NBUF;  // 1: the group's factor image has landed (phase g & 1)
     uint64_t* facfree = bload + 1;    // 1: the group's last MMAs are complete (phase g & 1)
-    uint64_t* sfull = facfree + 1;    // 2 x 4 (slot, lane quarter): the parts published their two best
-    uint64_t* qbar = sfull + 8;       // 4: the parts of a lane quarter published their draws
+    uint64_t* sfull = facfree + 1;    // 2 (slot): every part has published its tile
+    uint64_t* sfree = sfull + 2;      // 2 (slot): the merge warp has read it
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float xm1[2][NPART][BM], xm2[2][NPART][BM];  // per part: best and second score
     __shared__ int xk1[2][NPART][BM];                         // per part: cluster of the best
-    __shared__ float mbest[2][NPART][BM];                     // per part: best perturbed score
-    __shared__ int mz[2][NPART][BM];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = *a.dK;
@@ -143,8 +144,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
         }
         mbar_init(bload, 1);
         mbar_init(facfree, 1);
-        for (int b = 0; b < 8; ++b) mbar_init(&sfull[b], NPART * 32);
-        for (int q = 0; q < 4; ++q) mbar_init(&qbar[q], NPART * 32);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sfull[b], NEPI * 32);
+            mbar_init(&sfree[b], 32);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -253,34 +256,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
             }
         }
         __syncwarp();
-    } else {
-        // epilogue: thread <-> TMEM lane (point row); NPART warps per lane quarter, part p
-        // takes clusters cc = p, p + NPART, ... of every chunk
+    } else if (warp < MRG) {
+        // parts: thread <-> TMEM lane (point row); NPART warps per lane quarter, part p
+        // takes clusters cc = p, p + NPART, ... of every chunk.  Per tile a part publishes
+        // its two best scores (and every score, for the rare draws) in slot it & 1 and goes
+        // on to the next tile; the merge warp reads the slot.
         const int ew = warp - EPI0;
         const int quarter = warp & 3, part = ew >> 2;
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t iter = *a.diter;
-        Key key{a.seed, iter, a.diter[1], a.diter[2]};
         int64_t ch = 0, it = 0;
-        uint32_t nq = 0;  // uses of this quarter's draw barrier (the same in its four parts)
         bool ok = true;
         for (int g = 0; g < ngroups && ok; ++g) {
         const int kb = g * a.capc, Kg = group_size(g), nch = (Kg + a.NC - 1) / a.NC;
-        const bool first = g == 0, final = g == ngroups - 1;
         // the group's c_k table (written before the factor copies' arrival)
         if (!mbar_wait(bload, (uint32_t)(g & 1), abort)) { ok = false; break; }
         const float* ctg = ct + (g & 1) * a.capc;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
             const int64_t i = t * BM + r;
-            // Exact Gumbel-max.  Every part scores its clusters (kept in shared memory)
-            // and tracks its two best scores.  A cluster can win only if its score is
-            // within WINDOW of the row's best; when no other cluster is, the best one
-            // wins whatever the Gumbel values, and no draw is needed.  Otherwise each
-            // part draws for its clusters within the window and part 0 merges.
+            const int sl = (int)(it & 1);
+            // slot sl was last used two tiles ago: wait until the merge warp has read it
+            if (it >= 2 && !mbar_wait(&sfree[sl], (uint32_t)(((it >> 1) - 1) & 1), abort)) { ok = false; break; }
             float m1 = -INFINITY, m2 = -INFINITY;
             int k1 = 0;
-            float* sr = sbuf + r;  // score of the group's cluster kk at sr[kk * BM]
+            float* sr = sbuf + (size_t)sl * a.capc * BM + r;  // score of the group's cluster kk at sr[kk * BM]
             auto score = [&](int kk, float q) {
                 const float sc = ctg[kk] - 0.5f * q;
                 if constexpr (SCORES) {  // test hook only: no FP64 in the production kernel
@@ -324,100 +323,92 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                 mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
-            // Slot sl is reused two tiles later; every reader of it has arrived on the
-            // other slot's barrier in between, so no second barrier is needed.
-            const int sl = (int)(it & 1);
-            const uint32_t use = (uint32_t)((it >> 1) & 1);
             xm1[sl][part][r] = m1;
             xm2[sl][part][r] = m2;
             xk1[sl][part][r] = k1;
-            mbar_arrive(&sfull[sl * 4 + quarter]);
-            if (!mbar_wait(&sfull[sl * 4 + quarter], use, abort)) { ok = false; break; }
-            // the row's best and second-best scores (every part computes the same)
-            float g1 = xm1[sl][0][r], g2 = xm2[sl][0][r];
-            int gk = xk1[sl][0][r];
+            mbar_arrive(&sfull[sl]);
+        }
+        }
+        if (!ok) {
+            atomicExch(a.derr, (int)DPMM_ETIMEOUT);
+            *abort = 1;
+        }
+    } else {
+        // merge warp: per tile and row (lane + 32 q), the best and second-best score over the
+        // four parts and the earlier groups; Gumbel draws only when another cluster is
+        // within the window (the best one wins whatever the Gumbel values otherwise); then
+        // the label, or the state carried to the next group
+        const uint32_t iter = *a.diter;
+        Key key{a.seed, iter, a.diter[1], a.diter[2]};
+        int64_t it = 0;
+        bool ok = true;
+        for (int g = 0; g < ngroups && ok; ++g) {
+        const int kb = g * a.capc, Kg = group_size(g);
+        const bool first = g == 0, final = g == ngroups - 1;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+            const int sl = (int)(it & 1);
+            if (!mbar_wait(&sfull[sl], (uint32_t)((it >> 1) & 1), abort)) { ok = false; break; }
+            const float* sb = sbuf + (size_t)sl * a.capc * BM;
+            for (int qr = 0; qr < 4; ++qr) {
+                const int r = qr * 32 + lane;
+                const int64_t i = t * BM + r;
+                float g1 = xm1[sl][0][r], g2 = xm2[sl][0][r];
+                int gk = xk1[sl][0][r];
 #pragma unroll
-            for (int p2 = 1; p2 < NPART; ++p2) {
-                const float o1 = xm1[sl][p2][r], o2 = xm2[sl][p2][r];
-                const int ok1 = xk1[sl][p2][r];
-                if (o1 > g1 || (o1 == g1 && ok1 < gk)) {
-                    g2 = fmaxf(g1, o2);
-                    g1 = o1;
-                    gk = ok1;
-                } else {
-                    g2 = fmaxf(g2, o1);
-                }
-            }
-            // the state carried from the earlier groups (their clusters have lower ids)
-            float cg1 = -INFINITY, cg2 = -INFINITY, cv = -INFINITY;
-            int ck1 = 0, cz = 0;
-            if (!first && i < a.N) {
-                cg1 = a.carry.g1[i];
-                cg2 = a.carry.g2[i];
-                cv = a.carry.v[i];
-                ck1 = a.carry.k1[i];
-                cz = a.carry.zv[i];
-            }
-            if (!first) {
-                if (cg1 >= g1) {
-                    g2 = fmaxf(g1, cg2);
-                    g1 = cg1;
-                    gk = ck1;
-                } else {
-                    g2 = fmaxf(g2, cg1);
-                }
-            }
-            const float lim = g1 - WINDOW;
-            const bool need = !(g2 <= lim);  // another cluster might win: draw
-            float vbest = cv;  // best perturbed score among all clusters drawn so far
-            int zbest = cz;
-            if (__any_sync(0xffffffffu, need)) {  // the same answer in the four parts
-                float best = -INFINITY;
-                int zb = 0;
-                auto draw = [&](int k, float sc) {
-                    uint32_t w[4];
-                    key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
-                    const float u = u01_f32((k & 1) ? w[2] : w[0]);
-                    const float v = sc - __logf(-logf(u));
-                    if (v > best || (v == best && k < zb)) {
-                        best = v;
-                        zb = k;
+                for (int p2 = 1; p2 < NPART; ++p2) {
+                    const float o1 = xm1[sl][p2][r], o2 = xm2[sl][p2][r];
+                    const int ok1 = xk1[sl][p2][r];
+                    if (o1 > g1 || (o1 == g1 && ok1 < gk)) {
+                        g2 = fmaxf(g1, o2);
+                        g1 = o1;
+                        gk = ok1;
+                    } else {
+                        g2 = fmaxf(g2, o1);
                     }
-                };
+                }
+                // the state carried from the earlier groups (their clusters have lower ids)
+                float cg1 = -INFINITY, cg2 = -INFINITY, cv = -INFINITY;
+                int ck1 = 0, cz = 0;
+                if (!first && i < a.N) {
+                    cg1 = a.carry.g1[i];
+                    cg2 = a.carry.g2[i];
+                    cv = a.carry.v[i];
+                    ck1 = a.carry.k1[i];
+                    cz = a.carry.zv[i];
+                }
+                if (!first) {
+                    if (cg1 >= g1) {
+                        g2 = fmaxf(g1, cg2);
+                        g1 = cg1;
+                        gk = ck1;
+                    } else {
+                        g2 = fmaxf(g2, cg1);
+                    }
+                }
+                const float lim = g1 - WINDOW;
+                const bool need = !(g2 <= lim);  // another cluster might win: draw
+                float vbest = cv;  // best perturbed score among all clusters drawn so far
+                int zbest = cz;
                 if (need) {
-                    // the first two candidates are drawn below together with the other
-                    // lanes', any further one at once
-                    int c0 = -1, c1 = -1;
-                    float s0 = 0.f, s1 = 0.f;
-                    for (int kk = part; kk < Kg; kk += NPART) {
-                        const float sc = sr[kk * BM];
-                        if (sc > lim) {
-                            if (c0 < 0) { c0 = kb + kk; s0 = sc; }
-                            else if (c1 < 0) { c1 = kb + kk; s1 = sc; }
-                            else draw(kb + kk, sc);
+                    float best = -INFINITY;
+                    int zb = 0;
+                    auto draw = [&](int k, float sc) {
+                        uint32_t w[4];
+                        key.block((uint32_t)i, TAG_Z, (uint32_t)(k >> 1), w);
+                        const float u = u01_f32((k & 1) ? w[2] : w[0]);
+                        const float v = sc - __logf(-logf(u));
+                        if (v > best || (v == best && k < zb)) {
+                            best = v;
+                            zb = k;
                         }
+                    };
+                    for (int kk = 0; kk < Kg; ++kk) {
+                        const float sc = sb[(size_t)kk * BM + r];
+                        if (sc > lim) draw(kb + kk, sc);
                     }
-                    if (c0 >= 0) draw(c0, s0);
-                    if (c1 >= 0) draw(c1, s1);
-                    // the carried best cluster: its draw is deferred until a rival appears
+                    // the carried best cluster: its draw was deferred until a rival appeared
                     // (drawing it again later gives the same value)
-                    if (part == 0 && !first && cg1 > lim) draw(ck1, cg1);
-                }
-                mbest[sl][part][r] = best;
-                mz[sl][part][r] = zb;
-                mbar_arrive(&qbar[quarter]);
-                if (!mbar_wait(&qbar[quarter], (uint32_t)(nq & 1), abort)) { ok = false; break; }
-                ++nq;
-                if (part == 0 && need) {
-#pragma unroll
-                    for (int p2 = 1; p2 < NPART; ++p2) {
-                        const float ob = mbest[sl][p2][r];
-                        const int oz = mz[sl][p2][r];
-                        if (ob > best || (ob == best && oz < zb)) {
-                            best = ob;
-                            zb = oz;
-                        }
-                    }
+                    if (!first && cg1 > lim) draw(ck1, cg1);
                     if (cv > best || (cv == best && cz < zb)) {
                         best = cv;
                         zb = cz;
@@ -425,20 +416,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) labels_tc_kernel(const __grid_con
                     vbest = best;
                     zbest = zb;
                 }
-            }
-            if (part == 0 && i < a.N) {
-                if (final) {
-                    a.z[i] = need ? zbest : gk;
-                } else {
-                    // read back by every part of this row in the next group, after barriers
-                    // this warp arrives on after these stores
-                    a.carry.g1[i] = g1;
-                    a.carry.g2[i] = g2;
-                    a.carry.v[i] = vbest;
-                    a.carry.k1[i] = gk;
-                    a.carry.zv[i] = zbest;
+                if (i < a.N) {
+                    if (final) {
+                        a.z[i] = need ? zbest : gk;
+                    } else {
+                        // read back by this lane in the next group
+                        a.carry.g1[i] = g1;
+                        a.carry.g2[i] = g2;
+                        a.carry.v[i] = vbest;
+                        a.carry.k1[i] = gk;
+                        a.carry.zv[i] = zbest;
+                    }
                 }
             }
+            mbar_arrive(&sfree[sl]);
         }
         }
         if (!ok) {
@@ -522,9 +513,9 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     q.NC = tc::BUFCOLS / q.dn;
     while ((q.NC * q.dn) % 16) --q.NC;
     const size_t fixed = 1024 + tc::XST * tc::XBYTES + (size_t)tc::BM * 8 * 4 + (size_t)c->K_max * 8 + 32 * 8 + 64;
-    const size_t limit = 227 * 1024 - 24576;  // leave room for the kernel's static shared memory (22 KB)
-    // factor row, -b row, and each cluster's 128 scores spread over its dn rows
-    const size_t per_row = 128 + 32 + (tc::BM * 4 + q.dn - 1) / q.dn;
+    const size_t limit = 227 * 1024 - 16384;  // leave room for the kernel's static shared memory (13 KB)
+    // factor row, -b row, and each cluster's two slots of 128 scores spread over its dn rows
+    const size_t per_row = 128 + 32 + (2 * tc::BM * 4 + q.dn - 1) / q.dn;
     size_t want = (size_t)((c->K_max * q.dn + 15) / 16 * 16) * per_row;
     size_t cap = std::min(want, limit - fixed);
     q.cap_rows = (int)(cap / per_row / 16 * 16);
@@ -534,7 +525,7 @@ static TcCfg tc_cfg(const dpmm_ctx* c) {
     // image's 8-row groups line up) and is read padded to 16 rows, which can pass the last
     // cluster's rows by 8: 16 zero rows of slack
     q.img_rows = (c->K_max * q.dn + 15) / 16 * 16 + 16;
-    q.smem = fixed + (size_t)q.cap_rows * (128 + 32) + (size_t)(q.cap_rows / q.dn) * tc::BM * 4;
+    q.smem = fixed + (size_t)q.cap_rows * (128 + 32) + (size_t)2 * (q.cap_rows / q.dn) * tc::BM * 4;
     if (q.smem < 120 * 1024) q.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     return q;
 }
