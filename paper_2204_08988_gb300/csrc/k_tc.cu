@@ -15,7 +15,7 @@
 // so far is skipped, which leaves the argmax unchanged.
 //
 // Cluster groups: the factors of the clusters being scored are held in shared memory (up
-// to capc clusters: 27 at d = 32).  More clusters are scored in groups of capc: each CTA
+// to capc clusters: 26 at d = 32).  More clusters are scored in groups of capc: each CTA
 // passes over its tiles once per group, reloading the factor slice in between.  Between groups each point carries its best and
 // second-best scores so far (and the cluster of the best), and the best perturbed score
 // among the clusters drawn so far (and its cluster).  A group draws for its clusters within

@@ -64,9 +64,10 @@ def _fp64_scores(X, p, K):
 @pytest.mark.parametrize("N,d,K", [(5000, 32, 4), (3001, 32, 20), (2000, 8, 6), (1500, 20, 9), (3001, 32, 28),
                                    (9000, 32, 45), (12800, 32, 64), (8000, 8, 61)])
 def test_tc_scores_within_budget(N, d, K):
-    """Every score of every point against FP64.  Above 27 clusters at d = 32 the factors
-    no longer fit one launch's shared memory and the clusters are scored in groups, one
-    launch per group (K = 28: a group of one cluster; 45: two groups; 64 = K_max: three)."""
+    """Every score of every point against FP64.  Above 26 clusters at d = 32 the factors
+    no longer fit the kernel's shared memory at once and the clusters are scored in groups
+    of 26 within the launch (K = 28: a second group of two; 45: two groups; 64 = K_max:
+    three)."""
     X, y, zb, o, g, p = _setup(N, d, K, seed=N + d)
     s_tc = g.label_scores()
     s_64 = _fp64_scores(X, p, K)
@@ -84,9 +85,9 @@ def test_tc_scores_within_budget(N, d, K):
 
 @pytest.mark.parametrize("K", [20, 28, 45, 64])
 def test_tc_labels_agree_with_fp64(K):
-    """Above 27 clusters at d = 32 the tensor-core kernel scores the clusters in groups
-    (one launch each) and carries each point's best scores and best perturbed score from
-    group to group; the labels must agree with FP64 as for one group."""
+    """Above 26 clusters at d = 32 the tensor-core kernel scores the clusters in groups
+    (passes of one launch) and carries each point's best scores and best perturbed score
+    from group to group; the labels must agree with FP64 as for one group."""
     N, d = 20000, 32
     X, y, zb, o, g, p = _setup(N, d, K, seed=7 + K)
     g.set_mask(2)

@@ -82,10 +82,10 @@ def _compare_sampled(o, g, seed, n_sample, rng_seed):
     return dz, dzb, len(idx)
 
 
-@pytest.mark.parametrize("K", [20, 27])
+@pytest.mark.parametrize("K", [20, 26, 27])
 def test_tc_labels_wrap(K):
-    """TF32 at d = 32: K = 20 (the benchmark's cluster count) and K = 27, the most
-    clusters whose factors fit the kernel's shared memory at K_max = 64."""
+    """TF32 at d = 32: K = 20 (the benchmark's cluster count), K = 26, the most clusters
+    whose factors fit the kernel's shared memory at K_max = 64, and K = 27 (two groups)."""
     X, o, g, p = _gauss_pair(N_WRAP, 32, K, seed=400 + K, prec=P.PREC_TF32)
     dz, dzb, n = _compare_sampled(o, g, 77, 40_000, K)
     assert dz < 1e-3, dz
@@ -94,9 +94,10 @@ def test_tc_labels_wrap(K):
 
 
 def test_tc_scores_wrap():
-    """Every score of every point at N = 160,001 (K = 27) against FP64: the budgets of
-    the small-size test, and empty-cluster scores (-inf) exactly where FP64 has them."""
-    K = 27
+    """Every score of every point at N = 160,001 (K = 26, one full group of factors)
+    against FP64: the budgets of the small-size test, and empty-cluster scores (-inf)
+    exactly where FP64 has them."""
+    K = 26
     X, o, g, p = _gauss_pair(N_WRAP, 32, K, seed=427, prec=P.PREC_TF32)
     s_tc = g.label_scores()
     s_64 = np.empty_like(s_tc)
