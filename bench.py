@@ -38,8 +38,8 @@ METRIC = "point-sweeps/s (N*iters/s) d=32 N=1e6, BF16/TF32-TC vs FP64-plain, one
 # per cluster): the point part scales with N, the factor part with K.  Must be re-taken (or
 # removed) whenever that kernel changes.
 TRAFFIC_BYTES = {
-    # 2 M points, K = 20: 256.170240 MB read + 8.826368 MB written
-    ("labels_tc", "gauss_d32"): ((256.170240e6 + 8.826368e6) / 2e6, 0.0),
+    # 2 M points, K = 20: 256.227840 MB read + 8.569088 MB written
+    ("labels_tc", "gauss_d32"): ((256.227840e6 + 8.569088e6) / 2e6, 0.0),
     # 262,144 points, K = 56: 143.424256 MB read + written, of which the 56 factor images
     # (69,632 B each, read once from DRAM, then from L2) are the cluster part
     ("labels_x3", "gauss_d128"): ((143.424256e6 - 56 * 69632) / 262144, 69632.0),
