@@ -620,7 +620,9 @@ cudaError_t launch_labels_tc(dpmm_ctx* c, uint64_t seed) {
     prof_end(c, "labels_tc");
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // K beyond the shared-memory capacity: the CUDA-core kernel does the step
+    // K beyond the groups' capacity: the CUDA-core kernel does the step (launched only
+    // when K_max can exceed it)
+    if ((int64_t)q.gmax * q.capc >= c->K_max) return cudaSuccess;
     return launch_labels_simt_gated(c, seed, c->tc_flag);
 }
 

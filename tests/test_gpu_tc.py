@@ -101,6 +101,23 @@ def test_tc_labels_agree_with_fp64(K):
     g.close()
 
 
+def test_tc_overflow_falls_back_to_cuda_cores():
+    """K = 110 clusters at d = 32 with K_max = 128: more than the tensor-core kernel's four
+    groups of 26, so it raises its overflow flag and the CUDA-core kernel draws the labels
+    in the same step; they must agree with FP64 as the tensor-core ones do."""
+    N, d, K = 6000, 32, 110
+    X, y, zb, o, g, p = _setup(N, d, K, seed=5, K_max=128)
+    g.set_mask(2)
+    g.sweep(1, 321)
+    o.sweep(1, 321, mask=O.MASK_LABELS)
+    zo, zbo = o.labels()
+    zg, zbg = g.labels()
+    assert o.K == g.K
+    assert (zo != zg).mean() < 1e-3
+    assert (zbo != zbg).mean() < 1e-2
+    g.close()
+
+
 def test_tc_chain_finds_clusters():
     import synth
 
