@@ -145,11 +145,11 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(bar)) : "memory");
 }
-// FP32 -> TF32, round to nearest (ties away from zero)
+// FP32 -> TF32, round to nearest (ties away from zero), for the finite values the operands
+// hold: half a TF32 unit added to the magnitude bits, the 13 low bits cleared (a carry
+// into the exponent is the correct rounding).  Two integer operations.
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 template <bool DRAW>
