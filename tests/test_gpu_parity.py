@@ -198,6 +198,31 @@ def test_full_sweeps_fp64_match_oracle(kind):
     assert splits >= 2 and g.K >= 3
 
 
+def test_many_clusters_split_merge_fp64_match_oracle():
+    """Whole FP64 sweeps from 40 random clusters (K_max = 64): the split and merge
+    bookkeeping runs over two chunks of 32 clusters (prefix counts carried from one chunk
+    to the next), and the merge walk over the bit masks of 40 clusters; K, labels,
+    statistics and counters must match the oracle at every sweep."""
+    import synth
+
+    d = 2
+    X, _ = synth.gaussian_mixture(6000, d, 5, 6.0, seed=71, dtype=np.float64)
+    o, g = _pair(0, d, 64, 5.0, X, init_K=40, burn_out=0, **_niw_prior(d))
+    merges = 0
+    for t in range(6):
+        o.sweep(1, 57)
+        g.sweep(1, 57)
+        assert o.K == g.K, t
+        zo, zbo = o.labels()
+        zg, zbg = g.labels()
+        assert np.array_equal(zo, zg) and np.array_equal(zbo, zbg), t
+        _check_stats(o, g)
+        co, cg = o.counters(), g.counters()
+        assert co == cg, (t, co, cg)
+        merges += co["merges"]
+    assert merges >= 1
+
+
 def test_k_max_saturation_counts_rejections():
     import synth
 
